@@ -1,0 +1,311 @@
+"""Benchmark: FGMRES solves of 2D Stokes (Taylor-Hood P2/P1, 16x16 -> 128x128, 4 levels) on one GB300.
+
+One step = one FGMRES solve to 1e-8 relative residual (zero initial guess, V(1,1) cycles with
+Chebyshev-accelerated matrix-full Vanka smoothing) of a seeded N(0,1) right-hand side already resident
+in HBM.  The hierarchy (assembly, patch inverses, coarse inverse, eigenvalue estimates) is built once
+before timing and kept resident, as a solver service would.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vk|reference] [--config cfg2]
+
+N > 1 runs under torch.distributed.run as independent replicas (the path does not shard).
+--impl reference times the CPU oracle (the plain FP64 NumPy restatement of the method) on the host.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "V-cycle DoF/s; FGMRES solves/s to 1e-8 rel. residual; p50/p99 solve latency"
+
+CONFIGS = {
+    # name: (N_coarse, nlevels, k, sweeps, rtol, description)
+    "cfg1": (4, 2, 2, 1, 1e-10, "2D Stokes TH P2/P1, 4x4 -> 8x8 (2 levels), FGMRES to 1e-10"),
+    "cfg2": (16, 4, 2, 1, 1e-8, "2D Stokes TH P2/P1, 16x16 -> 128x128 (4 levels), FGMRES to 1e-8"),
+    "cfg3p3": (16, 3, 3, 1, 1e-8, "2D Stokes TH P3/P2, 16x16 -> 64x64 (3 levels), FGMRES to 1e-8"),
+    "cfg3p4": (16, 3, 4, 1, 1e-8, "2D Stokes TH P4/P3, 16x16 -> 64x64 (3 levels), FGMRES to 1e-8"),
+    "cfg4": (32, 5, 2, 1, 1e-8, "2D Stokes TH P2/P1, 32x32 -> 512x512 (5 levels), FGMRES to 1e-8"),
+}
+
+HBM_FALLBACK = 6800.0
+FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 (vector and tensor) nominal rate
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": HBM_FALLBACK}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.index = index
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if os.environ.get("VK_BENCH_GLOO") != "1" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_cpu_baseline(cfg, seed=0):
+    """The oracle timed as it stands on the host cores: one full FGMRES solve of the workload
+    (hierarchy built before timing, like the GPU arm)."""
+    from oracle import solver
+    import synthetic_inputs as si
+    Nc, L, k, sweeps, rtol, _ = cfg
+    t0 = time.perf_counter()
+    H = solver.Hierarchy(Nc, L, k, sweeps=sweeps)
+    t_setup = time.perf_counter() - t0
+    b = si.rhs_normal(H.finest.space.ndof, seed)
+    t0 = time.perf_counter()
+    res = solver.solve(H, b, rtol, 100)
+    t = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": 1.0 / t, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"1 full FGMRES solve (seed {seed}, {res.iters} iterations, {t:.1f} s; hierarchy setup "
+                      f"{t_setup:.1f} s excluded); NumPy/SciPy FP64, BLAS threads "
+                      f"{os.environ.get('OPENBLAS_NUM_THREADS', 'default')}",
+            "iterations": res.iters, "seconds": t}
+
+
+def run_reference(args, cfg):
+    """--impl reference: the oracle on the host cores, same metric and config."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from oracle import solver
+    import synthetic_inputs as si
+    Nc, L, k, sweeps, rtol, desc = cfg
+    H = solver.Hierarchy(Nc, L, k, sweeps=sweeps)
+    ndof = H.finest.space.ndof
+    # one full solve (untimed warm-up) fixes the iteration count of the workload; each timed step is
+    # a bounded sample: the first `sample_iters` FGMRES iterations of a solve, scaled to a full solve
+    full = solver.solve(H, si.rhs_normal(ndof, 0), rtol, 100)
+    sample_iters = min(3, full.iters)
+    for w in range(max(0, args.warmup - 1)):
+        solver.solve(H, si.rhs_normal(ndof, 100 + w), rtol, sample_iters)
+    times = []
+    for s in range(args.steps):
+        b = si.rhs_normal(ndof, 1000 + s)
+        t0 = time.perf_counter()
+        solver.solve(H, b, rtol, sample_iters)
+        times.append((time.perf_counter() - t0) * full.iters / sample_iters)
+    total = sum(times)
+    value = args.steps / total
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = (f"each step: first {sample_iters} FGMRES iterations of a solve, scaled by "
+              f"{full.iters}/{sample_iters} (full solve iteration count); hierarchy built before timing")
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": desc, "ndof": ndof, "iterations": full.iters},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "vcycle_dof_per_s": ndof * full.iters * args.steps / total,
+        "latency_ms": {"p50": 1e3 * float(np.percentile(times, 50)), "p99": 1e3 * float(np.percentile(times, 99))},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_vk(args, cfg):
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    from __graft_entry__ import build
+    build()
+    import paper_2409_14222_gb300 as vk
+    import synthetic_inputs as si
+    Nc, L, k, sweeps, rtol, desc = cfg
+    opts = vk.default_options(sweeps=sweeps)
+    if args.prec == "f32":
+        opts.factor_prec = vk.VK_PREC_F32
+    stream = torch.cuda.current_stream()
+    G = vk.Hierarchy(Nc, L, k, options=opts)
+    ndof = G.ndof()
+    # inputs resident in HBM before timing: one RHS per step
+    seeds = [rank * 100000 + s for s in range(args.warmup + args.steps)]
+    B = [torch.from_numpy(si.rhs_normal(ndof, s)).cuda() for s in seeds]
+    x = torch.zeros(ndof, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for w in range(args.warmup):
+        G.solve(B[w], x, rtol=rtol, history=False)
+    torch.cuda.synchronize()
+    G.stats_reset(time_kernels=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters = []
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        torch.cuda.profiler.start()          # a profiler started with --profile-from-start off sees only this
+        for s in range(args.steps):
+            flush.fill_(float(s))            # overwrite L2 (256 MiB > 129 MB) between timed solves
+            ev[s][0].record(stream)
+            out = G.solve(B[args.warmup + s], x, rtol=rtol, history=False)
+            ev[s][1].record(stream)
+            iters.append(out["iterations"])
+            if not out["converged"]:
+                raise RuntimeError(f"solve {s} did not converge: {out}")
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    barrier(world)
+    st = G.stats()
+    times_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = max_over_ranks(sum(times_ms) / 1e3, world)
+    value = world * args.steps / total_s
+    vcycles = st["vcycles"]
+    # end to end through the C ABI with host buffers (pinned): H2D copy + solve + D2H copy per step
+    bh = [torch.from_numpy(si.rhs_normal(ndof, 7777 + s)).pin_memory() for s in range(args.steps)]
+    xh = torch.zeros(ndof, dtype=torch.float64).pin_memory()
+    G.solve_host(bh[0].numpy(), xh.numpy(), rtol=rtol)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        G.solve_host(bh[s].numpy(), xh.numpy(), rtol=rtol)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    if rank != 0:
+        return
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK))
+    apply_avg_s = st["apply_ms"] / max(st["apply_launches"], 1) / 1e3
+    gbs = st["apply_bytes"] / apply_avg_s / 1e9
+    gflops = st["apply_flops"] / apply_avg_s / 1e9
+    frac_hbm, frac_alu = gbs / hbm, gflops / FP64_NOMINAL_GFLOPS
+    if args.prec == "f64" and frac_alu > frac_hbm:
+        roof = {"bound": "alu", "achieved": gflops / 1e3, "peak": FP64_NOMINAL_GFLOPS / 1e3, "unit": "TFLOP/s",
+                "frac": frac_alu, "traffic": None, "kernel": "k_patch_apply (finest level, FP64 inverses)",
+                "peak_source": "GB300 nominal FP64 rate 1.25 TFLOP/s (fp64 FMA pipe)",
+                "hbm_view": {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": frac_hbm, "peak_source": peak_kind}}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": frac_hbm, "traffic": None,
+                "kernel": f"k_patch_apply (finest level, {args.prec.upper()} inverses)",
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+    roof["launch_avg_us"] = apply_avg_s * 1e6
+    roof["bytes_per_launch"] = st["apply_bytes"]
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = oracle_cpu_baseline(cfg)
+    clocks = clk.summary()
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "f64" else "f64 vectors, f32 patch inverses",
+        "data": "synthetic",
+        "config": {"workload": desc, "ndof": ndof, "levels": L, "k": k, "sweeps": sweeps, "rtol": rtol,
+                   "factor_prec": args.prec, "rhs": "N(0,1), numpy default_rng(seed)",
+                   "l2": "256 MiB buffer overwritten between timed solves (outside the per-solve events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "vcycle_dof_per_s": world * ndof * vcycles / total_s,
+        "iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)), "max": int(max(iters))},
+        "latency_ms": {"p50": float(np.percentile(times_ms, 50)), "p99": float(np.percentile(times_ms, 99))},
+        "e2e": {"value": world * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * ndof,
+                "d2h_bytes_per_step": 8 * ndof},
+        "gpu_launches": int(st["launches"]),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="vk", choices=["vk", "reference"])
+    ap.add_argument("--config", default="cfg2", choices=sorted(CONFIGS))
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "vk":
+        ap.error("--warmup must be >= 3")
+    cfg = CONFIGS[args.config]
+    if args.impl == "reference":
+        run_reference(args, cfg)
+    else:
+        run_vk(args, cfg)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * vk.h -- C ABI of a single-GPU (GB300, sm_103a) matrix-full Vanka multigrid solver for the
+ * Taylor-Hood (P_k, P_{k-1}) discretization of the Stokes equations on triangles.
+ *
+ * Method: Rafiei and MacLachlan, "Achieving h- and p-robust monolithic multigrid solvers for the
+ * Stokes equations", arXiv 2409.14222.
+ *   - Stokes problem and weak form:            Sec. 2, Eqs. (Stokes1), (VariationalStokesa/b)
+ *   - Taylor-Hood on triangles (Case 1):       Sec. 3
+ *   - saddle-point system per level, nested hierarchy, canonical transfers, R = P^T,
+ *     Chebyshev-accelerated additive relaxation on [lambda/4, 1.1 lambda]:  Sec. 3
+ *   - additive subspace correction:            Algorithm 1 (Sec. 3.1)
+ *   - vertex / edge / cell composite patches:  Sec. 3.1
+ *   - matrix-full patch extraction (ASMPatchPC-style): Sec. 3.1, last paragraph
+ *   - FGMRES outer solver, zero initial guess, relative reduction, at most 100 iterations: Sec. 3, Sec. 4
+ *
+ * Conventions (all calls):
+ *   - Vectors are FP64, length ndof of the level, in the canonical DoF order: velocity node-major
+ *     (DoF 2*node + component, node = b*(kN+1) + a for the lattice point (a/(kN), b/(kN))), then the
+ *     pressure lattice ((k-1)N+1)^2 at offset 2*(kN+1)^2.
+ *   - Pointers named *_dev are device pointers owned by the caller; they must stay valid until the
+ *     work queued on `stream` has finished.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   - Every call returns a status code (VK_OK = 0).  On error, vk_last_error() gives a message for
+ *     the calling thread.  A hierarchy is not thread-safe; distinct hierarchies are independent.
+ *   - Level 0 is the coarsest mesh; level nlevels-1 the finest.
+ */
+#ifndef VK_H
+#define VK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VK_ABI_VERSION 1
+
+/* ---- status codes ---------------------------------------------------------------------------- */
+#define VK_OK 0
+#define VK_ERR_ARG 1            /* invalid argument or call not valid for this hierarchy        */
+#define VK_ERR_NO_MEMORY 2      /* device allocation failed (allocator returned NULL)           */
+#define VK_ERR_SINGULAR 3       /* zero pivot in a patch matrix or in the coarse bordered matrix */
+#define VK_ERR_NONFINITE 4      /* NaN or Inf in a right-hand side or residual                  */
+#define VK_ERR_NOT_CONVERGED 5  /* FGMRES reached maxit; x and info are still valid             */
+#define VK_ERR_TIMEOUT 6        /* a bounded device-side wait expired                           */
+#define VK_ERR_CUDA 7           /* CUDA runtime error                                           */
+#define VK_ERR_INTERNAL 8
+
+/* ---- options ----------------------------------------------------------------------------------- */
+#define VK_WEIGHTS_PLAIN 0         /* Algorithm 1 with w_i = gamma_i = identity (a plain sum)       */
+#define VK_WEIGHTS_MULTIPLICITY 1  /* each DoF's correction divided by the number of its patches    */
+
+#define VK_PREC_F64 0  /* patch inverses stored and applied in FP64                                  */
+#define VK_PREC_F32 1  /* patch inverses stored in FP32, applied with FP32 products, FP64 vectors    */
+
+#define VK_CSR_A 0  /* level matrix script-A_l with Dirichlet identity rows and zeroed columns      */
+#define VK_CSR_P 1  /* prolongation from level l-1 to level l (ndof_l x ndof_{l-1})                 */
+#define VK_CSR_R 2  /* restriction R = P^T (ndof_{l-1} x ndof_l)                                     */
+
+/* Mesh hierarchy: the unit square cut into N_coarse x N_coarse squares, each split from its top-left
+ * to its bottom-right corner (Sec. 4), refined uniformly nlevels-1 times (Sec. 3).  Velocity is
+ * continuous P_k, pressure continuous P_{k-1} (Case 1 of Sec. 3), 2 <= k <= 4.  No-slip Dirichlet
+ * rows on the whole boundary (Eq. StokesDirichletNoSlip); nu is the viscosity of Eq. (Stokes1). */
+typedef struct vk_problem {
+  int32_t N_coarse;
+  int32_t nlevels;
+  int32_t k;
+  double nu;
+} vk_problem;
+
+typedef struct vk_options {
+  int32_t sweeps;      /* Chebyshev steps per pre- and post-smoothing (nu in Sec. 4), >= 1          */
+  int32_t weights;     /* VK_WEIGHTS_*                                                               */
+  double cheb_lo;      /* Chebyshev interval [cheb_lo*lambda, cheb_hi*lambda]; 0.25 and 1.1 (Sec. 3) */
+  double cheb_hi;
+  int32_t eig_steps;   /* Arnoldi steps of the largest-eigenvalue estimate (10)                     */
+  uint64_t eig_seed;   /* SplitMix64 seed of the Arnoldi start vector; level l uses eig_seed + l    */
+  const double* lambdas; /* optional host array of nlevels values (index 0 unused); NULL = estimate */
+  int32_t factor_prec; /* VK_PREC_*                                                                  */
+  int32_t use_graph;   /* 1: replay each FGMRES iteration as a captured CUDA graph                  */
+  int32_t host_threads;/* threads for host assembly (0 = hardware concurrency)                      */
+  int32_t host_only;   /* 1: build and keep the host-side hierarchy only (export calls, no solves)  */
+  int32_t max_iterations; /* FGMRES basis size allocated at setup (100, the paper's cap, Sec. 4)   */
+} vk_options;
+
+/* Device memory provider.  alloc returns device memory of at least `bytes` (256-byte aligned) or
+ * NULL; release frees it.  Both are called only from vk_setup / vk_destroy on the calling thread.
+ * Passing NULL to vk_setup uses cudaMalloc / cudaFree. */
+typedef struct vk_allocator {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes, void* stream);
+  void (*release)(void* ctx, void* ptr, void* stream);
+} vk_allocator;
+
+typedef struct vk_hierarchy vk_hierarchy;
+
+typedef struct vk_solve_info {
+  int32_t iterations;  /* FGMRES iterations (= V-cycles) performed                                 */
+  int32_t converged;   /* 1 if the residual estimate reached rtol * ||b||                          */
+  double res0;         /* ||b|| after projection off the constant pressure                         */
+  double res_est;      /* last Givens residual estimate                                            */
+  double true_res;     /* ||b - A x|| recomputed at exit                                           */
+  double* history;     /* optional caller-owned host array of maxit+1 doubles: res0, then the
+                          residual estimate after each iteration; NULL to skip                     */
+  double solve_ms;     /* wall time of the call in milliseconds (host clock, includes the sync)    */
+} vk_solve_info;
+
+/* Fills *o with the defaults used by the paper's setting: 1 sweep, plain weights, [0.25, 1.1],
+ * 10 Arnoldi steps, FP64 factors, graphs on. */
+void vk_default_options(vk_options* o);
+
+/* Builds the hierarchy (Sec. 3): per level the assembled CSR saddle-point matrix (Sec. 3), the
+ * canonical prolongation / restriction (Sec. 3), the composite Vanka patches (Sec. 3.1), every patch
+ * matrix gathered from the CSR matrix and inverted by Gauss-Jordan elimination with partial pivoting
+ * on the GPU (Sec. 3.1, matrix-full), the bordered coarsest-level inverse, and the Chebyshev
+ * eigenvalue estimate of each smoothed level (Sec. 3).  Returns VK_ERR_SINGULAR if a patch or the
+ * coarse bordered matrix has a zero pivot.  The hierarchy owns all device memory it allocates through
+ * `alloc` (NULL = cudaMalloc); work is queued on `stream` and synchronised before return. */
+int vk_setup(const vk_problem* p, const vk_options* o, const vk_allocator* alloc, void* stream,
+             vk_hierarchy** out);
+
+/* Frees the hierarchy and every device buffer it owns.  NULL is ignored. */
+void vk_destroy(vk_hierarchy* h);
+
+/* Message of the last failed call on this thread ("" if none).  Valid until the next call. */
+const char* vk_last_error(void);
+
+/* Device bytes vk_setup would allocate for (p, o).  Builds the host-side structures only (no device
+ * work, no device memory): used to admit solves by HBM footprint. */
+int vk_footprint(const vk_problem* p, const vk_options* o, size_t* device_bytes);
+
+/* Sizes of one level: DoFs, velocity DoFs, nonzeros of A, number of patches and patch slots
+ * (sum of patch sizes).  Any output pointer may be NULL. */
+int vk_level_info(const vk_hierarchy* h, int level, int32_t* ndof, int32_t* n_u, int64_t* nnz,
+                  int32_t* npatch, int64_t* nslots);
+
+/* Device bytes this hierarchy allocated (equals vk_footprint for the same problem and options). */
+int vk_device_bytes(const vk_hierarchy* h, size_t* bytes);
+
+/* Chebyshev eigenvalue estimate lambda of level `level` (>= 1): the largest real part of the Ritz
+ * values of eig_steps Arnoldi steps on M^{-1} A (Sec. 3, "standard GMRES estimation"). */
+int vk_lambda(const vk_hierarchy* h, int level, double* lambda);
+
+/* r = b - A_level x  (CSR SpMV residual; Algorithm 1's local right-hand sides come from it). */
+int vk_residual(vk_hierarchy* h, int level, const double* b_dev, const double* x_dev, double* r_dev,
+                void* stream);
+
+/* z = M^{-1} r: one application of the additive Vanka operator of Algorithm 1 on level `level`
+ * (>= 1): every patch solve delta_i = A_i^{-1} r[idx_i] is applied with the stored inverse, then the
+ * weighted corrections are summed into each DoF in ascending patch order (no atomics); Dirichlet
+ * DoFs get z = r.  r_dev and z_dev must not alias. */
+int vk_vanka(vk_hierarchy* h, int level, const double* r_dev, double* z_dev, void* stream);
+
+/* `sweeps` Chebyshev steps (Sec. 3, "Relaxation") of the Vanka-preconditioned iteration for
+ * A_level x = b on [cheb_lo*lambda, cheb_hi*lambda].  zero_init = 1 ignores x on input (x0 = 0). */
+int vk_smooth(vk_hierarchy* h, int level, const double* b_dev, double* x_dev, int zero_init,
+              void* stream);
+
+/* r_coarse = R r_fine with R = P^T (Sec. 3), then zero at the coarse Dirichlet DoFs.
+ * fine_level >= 1; r_coarse has the DoFs of fine_level - 1. */
+int vk_restrict(vk_hierarchy* h, int fine_level, const double* r_fine_dev, double* r_coarse_dev,
+                void* stream);
+
+/* x_fine += P e_coarse (canonical prolongation of Sec. 3).  fine_level >= 1. */
+int vk_prolong(vk_hierarchy* h, int fine_level, const double* e_coarse_dev, double* x_fine_dev,
+               void* stream);
+
+/* x = solution of the bordered coarsest system [[A_0, z], [z^T, 0]] [x; mu] = [b; 0] with
+ * z = (0_u, 1_p) the constant pressure (reading: the paper does not name its coarse solver),
+ * applied as a GEMV with the inverse computed at setup. */
+int vk_coarse_solve(vk_hierarchy* h, const double* b_dev, double* x_dev, void* stream);
+
+/* x = V(nu, nu)(b): one multiplicative V-cycle on the finest level with zero initial guess
+ * (Sec. 3): Chebyshev/Vanka pre-smoothing, residual, restriction, recursion, prolongation,
+ * post-smoothing; the coarsest level is solved by vk_coarse_solve. */
+int vk_vcycle(vk_hierarchy* h, const double* b_dev, double* x_dev, void* stream);
+
+/* Solves A x = b on the finest level with right-preconditioned unrestarted FGMRES (Sec. 3),
+ * preconditioned by one V-cycle, zero initial guess, stopping when the Givens residual estimate is
+ * <= rtol * ||b|| or after maxit (<= 100 is the paper's setting, Sec. 4) iterations.  b is projected
+ * off the constant pressure first and every preconditioned vector is projected too, so x has zero
+ * pressure mean.  Orthogonalisation: classical Gram-Schmidt applied twice.  x_dev is overwritten.
+ * Returns VK_ERR_NOT_CONVERGED (with x and info valid) if maxit was reached, VK_ERR_NONFINITE if b
+ * or an iterate is not finite.  `info` (host, may be NULL) is complete when the call returns. */
+int vk_solve(vk_hierarchy* h, const double* b_dev, double* x_dev, double rtol, int maxit,
+             vk_solve_info* info, void* stream);
+
+/* vk_solve with host buffers: copies b_host (ndof doubles) to the device, solves, copies x back to
+ * x_host.  Both copies are issued on `stream`; the call returns after x_host is written. */
+int vk_solve_host(vk_hierarchy* h, const double* b_host, double* x_host, double rtol, int maxit,
+                  vk_solve_info* info, void* stream);
+
+/* Dimensions of CSR matrix `which` (VK_CSR_*) of a level (P and R need level >= 1). */
+int vk_csr_dims(const vk_hierarchy* h, int level, int which, int32_t* nrows, int32_t* ncols,
+                int64_t* nnz);
+
+/* Copies CSR matrix `which` of a level into caller-owned host arrays of nrows+1, nnz and nnz entries
+ * (sizes from vk_csr_dims).  Columns are ascending within each row.  Works on host-only hierarchies. */
+int vk_export_csr(const vk_hierarchy* h, int level, int which, int32_t* ptr, int32_t* col, double* val);
+
+/* Copies the patch lists of a level (>= 1) into host arrays of npatch+1, nslots and npatch entries:
+ * DoFs of patch i are dofs[ptr[i] .. ptr[i+1]), ascending; kind 0 = vertex, 1 = edge, 2 = cell.
+ * Patches are ordered vertices, then edges (horizontal, vertical, diagonal), then cells. */
+int vk_export_patches(const vk_hierarchy* h, int level, int32_t* ptr, int32_t* dofs, int8_t* kind);
+
+/* Copies the Dirichlet flags (1 = no-slip velocity DoF) of a level into a host array of ndof bytes. */
+int vk_export_dirichlet(const vk_hierarchy* h, int level, uint8_t* flags);
+
+/* Counters of the work a hierarchy issued since the last vk_stats_reset. */
+typedef struct vk_stats {
+  int64_t launches;        /* CUDA kernels launched on behalf of this hierarchy                     */
+  int64_t vcycles;         /* V-cycles started on the finest level                                   */
+  int64_t apply_launches;  /* finest-level patch-apply launches bracketed by CUDA events            */
+  double apply_ms;         /* their summed event durations (ms), measured on the launching stream   */
+  double apply_bytes;      /* algorithmic bytes of one finest-level patch-apply launch:
+                              s*sum(n_i^2) inverse entries (s = 8 FP64, 4 FP32) + 20*sum(n_i)
+                              (DoF index, gathered residual, written correction) + 16 per patch     */
+  double apply_flops;      /* 2*sum(n_i^2) flops of one finest-level patch-apply launch             */
+} vk_stats;
+
+/* Zeroes the counters; time_kernels = 1 also brackets every finest-level patch-apply launch with
+ * CUDA events (recorded on the stream of the call that launches it). */
+int vk_stats_reset(vk_hierarchy* h, int time_kernels);
+
+/* Reads the counters (waits for the recorded events). */
+int vk_stats_read(vk_hierarchy* h, vk_stats* out);
+
+/* Host-only helper: eigenvalues of the m x m row-major real upper-Hessenberg matrix H (the Arnoldi
+ * matrix of the eigenvalue estimate).  Returns VK_ERR_INTERNAL if the QR iteration does not converge. */
+int vk_hessenberg_eigenvalues(int m, const double* H, double* re, double* im);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VK_H */

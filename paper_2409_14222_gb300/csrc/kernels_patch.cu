@@ -1,0 +1,296 @@
+// Vanka patch kernels (Sec. 3.1, Algorithm 1):
+//   patch_factor  -- gather A_i = A[idx_i, idx_i] from the assembled CSR matrix (matrix-full,
+//                    Sec. 3.1 last paragraph) and invert it in shared memory by Gauss-Jordan
+//                    elimination with partial pivoting; store the inverse in the warp-packed layout.
+//   patch_apply   -- delta_i = A_i^{-1} r[idx_i] for every patch: one warp per patch.
+//   vanka_scatter -- z_d = sum over the patches i containing DoF d of (w_d delta_i)_d, summed in
+//                    ascending patch order (atomic-free), Dirichlet identity, fused with the
+//                    Chebyshev update of Sec. 3 ("Relaxation").
+//
+// Warp-packed layout of an n x n inverse: NA = ceil(n/8) row blocks, NB = ceil(n/4) column steps.
+// Lane l = r + 8 c (r in 0..7, c in 0..3) owns rows r + 8 a and columns c + 4 b.  Element (a, b) of
+// lane l is stored at (a * NB + b) * 32 + l, so each warp load is 32 consecutive values (256 bytes in
+// FP64), and padding (rows/columns >= n, stored as zero) is at most 7 rows and 3 columns.
+#include <cfloat>
+
+#include "gpu.h"
+
+namespace vk {
+namespace gpu {
+
+namespace {
+
+constexpr int kFactorThreads = 128;
+
+template <typename FT>
+__global__ void __launch_bounds__(kFactorThreads) k_patch_factor(Csr A, const int* __restrict__ slot_ptr,
+                                                                 const int* __restrict__ slot_dofs,
+                                                                 const int64_t* __restrict__ foff,
+                                                                 FT* __restrict__ F, int* status) {
+  extern __shared__ double sm[];
+  __shared__ double red_v[kFactorThreads / 32];
+  __shared__ int red_i[kFactorThreads / 32];
+  __shared__ int piv_row, bad;
+  const int p = blockIdx.x, tid = threadIdx.x;
+  const int s0 = slot_ptr[p], n = slot_ptr[p + 1] - s0;
+  const int* dofs = slot_dofs + s0;
+  double* M = sm;              // n * n, row-major
+  double* fcol = M + n * n;    // n
+  int* perm = reinterpret_cast<int*>(fcol + n);  // n
+  for (int i = tid; i < n * n; i += kFactorThreads) M[i] = 0.0;
+  __syncthreads();
+  // gather: row i of the patch scans CSR row dofs[i]; each column is located in the sorted list
+  for (int i = tid; i < n; i += kFactorThreads) {
+    const int g = dofs[i];
+    for (int e = A.ptr[g]; e < A.ptr[g + 1]; ++e) {
+      const int c = A.col[e];
+      int lo = 0, hi = n;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (dofs[mid] < c) lo = mid + 1; else hi = mid;
+      }
+      if (lo < n && dofs[lo] == c) M[i * n + lo] = A.val[e];
+    }
+  }
+  __syncthreads();
+  // in-place Gauss-Jordan with partial pivoting (first maximal |pivot| wins ties)
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = n;
+    for (int i = k + tid; i < n; i += kFactorThreads) {
+      const double v = fabs(M[i * n + k]);
+      if (v > best) { best = v; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double bv = red_v[0];
+      int bidx = red_i[0];
+      for (int w = 1; w < kFactorThreads / 32; ++w)
+        if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bidx)) { bv = red_v[w]; bidx = red_i[w]; }
+      piv_row = bidx;
+      bad = !(bv > 0.0) || !isfinite(bv);
+      perm[k] = bidx;
+    }
+    __syncthreads();
+    if (bad) {
+      if (tid == 0) atomicCAS(status, 0, p + 1);
+      return;
+    }
+    const int pr = piv_row;
+    if (pr != k)
+      for (int j = tid; j < n; j += kFactorThreads) {
+        const double t = M[k * n + j];
+        M[k * n + j] = M[pr * n + j];
+        M[pr * n + j] = t;
+      }
+    __syncthreads();
+    const double pv = M[k * n + k];
+    for (int i = tid; i < n; i += kFactorThreads) fcol[i] = M[i * n + k];
+    __syncthreads();
+    for (int j = tid; j < n; j += kFactorThreads) M[k * n + j] = (j == k ? 1.0 : M[k * n + j]) / pv;
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += kFactorThreads) {
+      const int i = idx / n, j = idx - i * n;
+      if (i == k) continue;
+      M[idx] = (j == k ? 0.0 : M[idx]) - fcol[i] * M[k * n + j];
+    }
+    __syncthreads();
+  }
+  // undo the row interchanges on the columns, last interchange first
+  for (int i = tid; i < n; i += kFactorThreads)
+    for (int k = n - 1; k >= 0; --k) {
+      const int q = perm[k];
+      if (q != k) {
+        const double t = M[i * n + k];
+        M[i * n + k] = M[i * n + q];
+        M[i * n + q] = t;
+      }
+    }
+  __syncthreads();
+  const int NB = (n + 3) / 4, NA = (n + 7) / 8;
+  FT* out = F + foff[p];
+  for (int e = tid; e < 32 * NA * NB; e += kFactorThreads) {
+    const int lane = e & 31, ab = e >> 5;
+    const int a = ab / NB, b = ab - a * NB;
+    const int row = (lane & 7) + 8 * a, col = (lane >> 3) + 4 * b;
+    out[e] = (row < n && col < n) ? FT(M[row * n + col]) : FT(0);
+  }
+}
+
+template <typename FT>
+struct Compute {
+  using T = double;
+};
+template <>
+struct Compute<float> {
+  using T = float;
+};
+
+// One warp applies one packed inverse.  FP64 factors: FP64 products and sums.  FP32 factors: the
+// local residual is rounded to FP32 and the products are summed in FP32.
+template <int NB, typename FT>
+__device__ __forceinline__ void apply_one(int n, int s0, const int* __restrict__ dofs,
+                                          const FT* __restrict__ Fp, const double* __restrict__ r,
+                                          double* __restrict__ delta, int lane) {
+  using T = typename Compute<FT>::T;
+  constexpr int NA = (NB + 1) / 2;
+  const int rr = lane & 7, cc = lane >> 3;
+  T rl[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = cc + 4 * b;
+    rl[b] = j < n ? T(r[__ldg(dofs + j)]) : T(0);
+  }
+  T acc[NA];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    T s = T(0);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) s = fma(T(__ldg(Fp + (a * NB + b) * 32 + lane)), rl[b], s);
+    acc[a] = s;
+  }
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], 8);
+    acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], 16);
+  }
+  if (cc == 0) {
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      const int row = rr + 8 * a;
+      if (row < n) delta[s0 + row] = double(acc[a]);
+    }
+  }
+}
+
+template <int NB, int NBMAX, typename FT>
+__device__ __forceinline__ void apply_dispatch(int nb, int n, int s0, const int* dofs, const FT* Fp,
+                                               const double* r, double* delta, int lane) {
+  if constexpr (NB <= NBMAX) {
+    if (nb == NB)
+      apply_one<NB, FT>(n, s0, dofs, Fp, r, delta, lane);
+    else
+      apply_dispatch<NB + 1, NBMAX, FT>(nb, n, s0, dofs, Fp, r, delta, lane);
+  }
+}
+
+template <int NBMAX, typename FT>
+__global__ void __launch_bounds__(256) k_patch_apply(int npatch, const int* __restrict__ work,
+                                                     const int* __restrict__ slot_ptr,
+                                                     const int* __restrict__ slot_dofs,
+                                                     const int64_t* __restrict__ foff,
+                                                     const FT* __restrict__ F, const double* __restrict__ r,
+                                                     double* __restrict__ delta) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= npatch) return;
+  const int p = work[w];
+  const int s0 = slot_ptr[p], n = slot_ptr[p + 1] - s0;
+  apply_dispatch<1, NBMAX, FT>((n + 3) >> 2, n, s0, slot_dofs + s0, F + foff[p], r, delta, lane);
+}
+
+__global__ void __launch_bounds__(256) k_vanka_scatter(int ndof, const int* __restrict__ dptr,
+                                                       const int* __restrict__ dslot,
+                                                       const double* __restrict__ weight,
+                                                       const uint8_t* __restrict__ dir,
+                                                       const double* __restrict__ r,
+                                                       const double* __restrict__ delta, int mode,
+                                                       double theta, double c1, double c2,
+                                                       double* __restrict__ zout, double* __restrict__ d,
+                                                       double* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ndof) return;
+  double z;
+  if (dir[i]) {
+    z = r[i];
+  } else {
+    z = 0.0;
+    const int e0 = dptr[i], e1 = dptr[i + 1];
+    if (weight) {
+      const double wi = weight[i];
+      for (int e = e0; e < e1; ++e) z = __dadd_rn(z, __dmul_rn(delta[dslot[e]], wi));
+    } else {
+      for (int e = e0; e < e1; ++e) z += delta[dslot[e]];
+    }
+  }
+  switch (mode) {
+    case 0:
+      zout[i] = z;
+      break;
+    case 1: {
+      const double dn = z / theta;
+      d[i] = dn;
+      x[i] = dn;
+      break;
+    }
+    case 2: {
+      const double dn = z / theta;
+      d[i] = dn;
+      x[i] = x[i] + dn;
+      break;
+    }
+    default: {
+      const double dn = __dadd_rn(__dmul_rn(c1, d[i]), __dmul_rn(c2, z));
+      d[i] = dn;
+      x[i] = x[i] + dn;
+      break;
+    }
+  }
+}
+
+template <int NBMAX, typename FT>
+int launch_apply(const Patches& P, const double* r, double* delta, cudaStream_t s) {
+  const int threads = 256, warps = threads / 32;
+  const int blocks = (P.npatch + warps - 1) / warps;
+  k_patch_apply<NBMAX, FT><<<blocks, threads, 0, s>>>(P.npatch, P.work, P.slot_ptr, P.slot_dofs, P.foff,
+                                                      static_cast<const FT*>(P.factors), r, delta);
+  return 1;
+}
+
+template <typename FT>
+int apply_prec(const Patches& P, const double* r, double* delta, cudaStream_t s) {
+  if (P.nb_max <= 10) return launch_apply<10, FT>(P, r, delta, s);
+  if (P.nb_max <= 19) return launch_apply<19, FT>(P, r, delta, s);
+  return launch_apply<32, FT>(P, r, delta, s);
+}
+
+}  // namespace
+
+int patch_factor(const Csr& A, const Patches& P, int prec, void* factors, int* status, cudaStream_t s) {
+  if (P.npatch == 0) return 0;
+  // shared bytes n*n*8 + n*12 for the largest patch of the level (n <= 4 * nb_max <= 128)
+  const int nmax = 4 * P.nb_max;
+  const size_t smem = size_t(nmax) * nmax * 8 + size_t(nmax) * 12;
+  if (prec == 0) {
+    cudaFuncSetAttribute(k_patch_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    k_patch_factor<double><<<P.npatch, kFactorThreads, smem, s>>>(A, P.slot_ptr, P.slot_dofs, P.foff,
+                                                                   static_cast<double*>(factors), status);
+  } else {
+    cudaFuncSetAttribute(k_patch_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    k_patch_factor<float><<<P.npatch, kFactorThreads, smem, s>>>(A, P.slot_ptr, P.slot_dofs, P.foff,
+                                                                  static_cast<float*>(factors), status);
+  }
+  return 1;
+}
+
+int patch_apply(const Patches& P, const double* r, double* delta, cudaStream_t s) {
+  if (P.npatch == 0) return 0;
+  return P.prec == 0 ? apply_prec<double>(P, r, delta, s) : apply_prec<float>(P, r, delta, s);
+}
+
+int vanka_scatter(const Patches& P, int ndof, const uint8_t* dir, const double* r, const double* delta,
+                   int mode, double theta, double c1, double c2, double* out_z, double* d, double* x,
+                   cudaStream_t s) {
+  k_vanka_scatter<<<(ndof + 255) / 256, 256, 0, s>>>(ndof, P.dof_ptr, P.dof_slot, P.weight, dir, r, delta,
+                                                     mode, theta, c1, c2, out_z, d, x);
+  return 1;
+}
+
+}  // namespace gpu
+}  // namespace vk

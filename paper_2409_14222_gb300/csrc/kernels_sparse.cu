@@ -1,0 +1,210 @@
+// Sparse and vector kernels: SELL-32 SpMV / residual, CSR restriction and prolongation, and
+// deterministic (fixed-order) reductions.  FP64 throughout.
+//
+// Residual r = b - A x of every relaxed level and the FGMRES product w = A z (Sec. 3, Algorithm 1's
+// local right-hand sides); R = P^T restriction and P prolongation (Sec. 3, grid transfers).
+#include "gpu.h"
+
+namespace vk {
+namespace gpu {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(int64_t n, int t = kThreads) { return int((n + t - 1) / t); }
+
+// One thread per row slot of a 32-row slice: lane t of slice s owns permuted row 32 s + t.
+__global__ void __launch_bounds__(kThreads) k_sell_residual(int nslices, const int64_t* __restrict__ sptr,
+                                                            const int* __restrict__ sw,
+                                                            const int* __restrict__ col,
+                                                            const double* __restrict__ val,
+                                                            const int* __restrict__ rowof,
+                                                            const double* __restrict__ b,
+                                                            const double* __restrict__ x,
+                                                            double* __restrict__ y) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = t >> 5, lane = t & 31;
+  if (s >= nslices) return;
+  const int row = rowof[t];
+  const int w = sw[s];
+  const int64_t base = sptr[s] + lane;
+  double sum = 0.0;
+  int k = 0;
+  for (; k + 4 <= w; k += 4) {
+    const int c0 = __ldg(col + base + 32 * (k + 0)), c1 = __ldg(col + base + 32 * (k + 1));
+    const int c2 = __ldg(col + base + 32 * (k + 2)), c3 = __ldg(col + base + 32 * (k + 3));
+    const double v0 = __ldg(val + base + 32 * (k + 0)), v1 = __ldg(val + base + 32 * (k + 1));
+    const double v2 = __ldg(val + base + 32 * (k + 2)), v3 = __ldg(val + base + 32 * (k + 3));
+    sum = fma(v0, x[c0], sum);
+    sum = fma(v1, x[c1], sum);
+    sum = fma(v2, x[c2], sum);
+    sum = fma(v3, x[c3], sum);
+  }
+  for (; k < w; ++k) sum = fma(__ldg(val + base + 32 * k), x[__ldg(col + base + 32 * k)], sum);
+  if (row >= 0) y[row] = b ? b[row] - sum : sum;
+}
+
+__global__ void k_csr_restrict(int nrows, const int* __restrict__ ptr, const int* __restrict__ col,
+                               const double* __restrict__ val, const uint8_t* __restrict__ dir,
+                               const double* __restrict__ r, double* __restrict__ rc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrows) return;
+  double s = 0.0;
+  if (!dir[i])
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], r[col[e]], s);
+  rc[i] = s;
+}
+
+__global__ void k_csr_prolong_add(int nrows, const int* __restrict__ ptr, const int* __restrict__ col,
+                                  const double* __restrict__ val, const double* __restrict__ ec,
+                                  double* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrows) return;
+  double s = 0.0;
+  for (int e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], ec[col[e]], s);
+  x[i] += s;
+}
+
+template <int T>
+__device__ double block_sum(double v) {
+  __shared__ double sh[T / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < T / 32 ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  return v;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kThreads) k_dot_partials(const double* __restrict__ x,
+                                                           const double* __restrict__ y, int n,
+                                                           double* __restrict__ partial) {
+  double s = 0.0;
+  for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += kReduceBlocks * kThreads)
+    s = fma(x[i], y[i], s);
+  s = block_sum<kThreads>(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_sum_partials(const double* __restrict__ x, int n,
+                                                           double* __restrict__ partial) {
+  double s = 0.0;
+  for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += kReduceBlocks * kThreads) s += x[i];
+  s = block_sum<kThreads>(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_finalize(const double* __restrict__ partial, int nparts,
+                                                       double* __restrict__ out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += kThreads) s += partial[i];
+  s = block_sum<kThreads>(s);
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_subtract_mean(double* __restrict__ x, int len, const double* __restrict__ sum) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  x[i] -= *sum / double(len);
+}
+
+__global__ void k_fill(double* x, double v, int64_t n) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) x[i] = v;
+}
+
+__global__ void k_copy(double* __restrict__ d, const double* __restrict__ s, int64_t n) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) d[i] = s[i];
+}
+
+__global__ void k_nonfinite(const double* __restrict__ x, int n, int* flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !isfinite(x[i])) *flag = 1;
+}
+
+__global__ void k_axpy(double a, const double* __restrict__ x, double* __restrict__ y, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = __dsub_rn(y[i], __dmul_rn(-a, x[i]));  // y - (-a) x, unfused
+}
+
+__global__ void k_scale(double a, double* __restrict__ x, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = x[i] * a;
+}
+
+}  // namespace
+
+int axpy(double a, const double* x, double* y, int n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_axpy<<<blocks_for(n), kThreads, 0, s>>>(a, x, y, n);
+  return 1;
+}
+
+int scale(double a, double* x, int n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_scale<<<blocks_for(n), kThreads, 0, s>>>(a, x, n);
+  return 1;
+}
+
+int sell_residual(const Sell& A, const double* b, const double* x, double* y, cudaStream_t s) {
+  if (A.nslices == 0) return 0;
+  k_sell_residual<<<blocks_for(int64_t(A.nslices) * 32), kThreads, 0, s>>>(A.nslices, A.sptr, A.swidth, A.col,
+                                                                          A.val, A.rowof, b, x, y);
+  return 1;
+}
+
+int csr_restrict(const Csr& R, const uint8_t* dir_coarse, const double* r, double* rc, cudaStream_t s) {
+  if (R.nrows == 0) return 0;
+  k_csr_restrict<<<blocks_for(R.nrows), kThreads, 0, s>>>(R.nrows, R.ptr, R.col, R.val, dir_coarse, r, rc);
+  return 1;
+}
+
+int csr_prolong_add(const Csr& P, const double* ec, double* x, cudaStream_t s) {
+  if (P.nrows == 0) return 0;
+  k_csr_prolong_add<<<blocks_for(P.nrows), kThreads, 0, s>>>(P.nrows, P.ptr, P.col, P.val, ec, x);
+  return 1;
+}
+
+int dot_partials(const double* x, const double* y, int n, double* partial, cudaStream_t s) {
+  k_dot_partials<<<kReduceBlocks, kThreads, 0, s>>>(x, y, n, partial);
+  return 1;
+}
+
+int finalize_sum(const double* partial, int nparts, double* out, cudaStream_t s) {
+  k_finalize<<<1, kThreads, 0, s>>>(partial, nparts, out);
+  return 1;
+}
+
+int pressure_project(double* x, int off, int len, double* scratch_partial, double* scratch_sum,
+                      cudaStream_t s) {
+  if (len <= 0) return 0;
+  k_sum_partials<<<kReduceBlocks, kThreads, 0, s>>>(x + off, len, scratch_partial);
+  k_finalize<<<1, kThreads, 0, s>>>(scratch_partial, kReduceBlocks, scratch_sum);
+  k_subtract_mean<<<blocks_for(len), kThreads, 0, s>>>(x + off, len, scratch_sum);
+  return 3;
+}
+
+int fill(double* x, double v, int64_t n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_fill<<<blocks_for(n), kThreads, 0, s>>>(x, v, n);
+  return 1;
+}
+
+int copy(double* dst, const double* src, int64_t n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_copy<<<blocks_for(n), kThreads, 0, s>>>(dst, src, n);
+  return 1;
+}
+
+int nonfinite_check(const double* x, int n, int* flag, cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_nonfinite<<<blocks_for(n), kThreads, 0, s>>>(x, n, flag);
+  return 1;
+}
+
+}  // namespace gpu
+}  // namespace vk

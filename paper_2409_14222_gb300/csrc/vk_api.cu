@@ -1,0 +1,949 @@
+// C ABI of the Vanka multigrid library (include/vk.h): hierarchy setup, the V-cycle, FGMRES and the
+// export calls.  Host orchestration only; every numerical step on the device is a kernel of
+// kernels_*.cu.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "gpu.h"
+#include "vk.h"
+#include "vk_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+struct VkError {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] void raise(int code, const std::string& msg) { throw VkError{code, msg}; }
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) raise(VK_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call) ck((call), #call)
+
+template <class F>
+int guard(F&& f) {
+  try {
+    g_err.clear();
+    return f();
+  } catch (const VkError& e) {
+    g_err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed";
+    return VK_ERR_NO_MEMORY;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return VK_ERR_INTERNAL;
+  }
+}
+
+inline size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Device memory through the caller's allocator (or cudaMalloc).  Counts bytes so vk_footprint can be
+// checked against what setup really allocates.
+struct DeviceMemory {
+  vk_allocator user{};
+  bool custom = false;
+  cudaStream_t stream = nullptr;
+  std::vector<void*> live;
+  size_t total = 0;
+  bool counting_only = false;
+
+  void* get(size_t bytes) {
+    bytes = round256(std::max<size_t>(bytes, 1));
+    total += bytes;
+    if (counting_only) return nullptr;
+    void* p = nullptr;
+    if (custom) {
+      p = user.alloc(user.ctx, bytes, stream);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (!p) raise(VK_ERR_NO_MEMORY, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    live.push_back(p);
+    return p;
+  }
+  template <class T>
+  T* get_n(size_t n) {
+    return static_cast<T*>(get(n * sizeof(T)));
+  }
+  template <class T>
+  T* upload(const std::vector<T>& v) {
+    T* p = get_n<T>(v.size());
+    if (!counting_only && !v.empty())
+      CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, stream));
+    return p;
+  }
+  void release_all() {
+    for (void* p : live) {
+      if (custom)
+        user.release(user.ctx, p, stream);
+      else
+        cudaFree(p);
+    }
+    live.clear();
+  }
+};
+
+struct HostSell {
+  std::vector<int64_t> sptr;
+  std::vector<int> sw, col, rowof;
+  std::vector<double> val;
+};
+
+// SELL-32: permute rows by decreasing length inside windows of 1024 rows, cut into slices of 32.
+HostSell build_sell(const vk::HostCsr& A) {
+  HostSell S;
+  const int n = A.nrows, W = 1024;
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  for (int w0 = 0; w0 < n; w0 += W) {
+    const int w1 = std::min(n, w0 + W);
+    std::stable_sort(order.begin() + w0, order.begin() + w1, [&](int a, int b) {
+      return (A.ptr[a + 1] - A.ptr[a]) > (A.ptr[b + 1] - A.ptr[b]);
+    });
+  }
+  const int ns = (n + 31) / 32;
+  S.rowof.assign(size_t(ns) * 32, -1);
+  for (int i = 0; i < n; ++i) S.rowof[i] = order[i];
+  S.sptr.assign(ns + 1, 0);
+  S.sw.assign(ns, 0);
+  for (int s = 0; s < ns; ++s) {
+    int w = 0;
+    for (int t = 0; t < 32; ++t) {
+      const int row = S.rowof[s * 32 + t];
+      if (row >= 0) w = std::max(w, A.ptr[row + 1] - A.ptr[row]);
+    }
+    S.sw[s] = w;
+    S.sptr[s + 1] = S.sptr[s] + 32LL * w;
+  }
+  S.col.assign(S.sptr[ns], 0);
+  S.val.assign(S.sptr[ns], 0.0);
+  for (int s = 0; s < ns; ++s)
+    for (int t = 0; t < 32; ++t) {
+      const int row = S.rowof[s * 32 + t];
+      const int len = row >= 0 ? A.ptr[row + 1] - A.ptr[row] : 0;
+      for (int k = 0; k < S.sw[s]; ++k) {
+        const int64_t pos = S.sptr[s] + 32LL * k + t;
+        if (k < len) {
+          S.col[pos] = A.col[A.ptr[row] + k];
+          S.val[pos] = A.val[A.ptr[row] + k];
+        } else {
+          S.col[pos] = row >= 0 ? row : 0;
+          S.val[pos] = 0.0;
+        }
+      }
+    }
+  return S;
+}
+
+struct HostPatchPlan {
+  std::vector<int> work;        // canonical ids in processing order
+  std::vector<int64_t> foff;    // canonical id -> packed offset
+  int64_t ftotal = 0;
+  int nb_max = 0;
+  std::vector<int> dof_ptr, dof_slot;
+  std::vector<double> weight;
+};
+
+HostPatchPlan plan_patches(const vk::HostLevel& L, int weights) {
+  HostPatchPlan P;
+  const int np = int(L.patch_ptr.size()) - 1;
+  P.work.resize(np);
+  std::iota(P.work.begin(), P.work.end(), 0);
+  auto nb = [&](int p) { return (L.patch_ptr[p + 1] - L.patch_ptr[p] + 3) / 4; };
+  std::stable_sort(P.work.begin(), P.work.end(), [&](int a, int b) { return nb(a) > nb(b); });
+  P.foff.assign(np, 0);
+  for (int w = 0; w < np; ++w) {
+    const int p = P.work[w];
+    P.foff[p] = P.ftotal;
+    P.ftotal += vk::gpu::packed_size(L.patch_ptr[p + 1] - L.patch_ptr[p]);
+    P.nb_max = std::max(P.nb_max, nb(p));
+  }
+  const int64_t nslots = L.patch_dofs.size();
+  P.dof_ptr.assign(L.ndof + 1, 0);
+  for (int64_t s = 0; s < nslots; ++s) P.dof_ptr[L.patch_dofs[s] + 1]++;
+  for (int i = 0; i < L.ndof; ++i) P.dof_ptr[i + 1] += P.dof_ptr[i];
+  P.dof_slot.assign(nslots, 0);
+  std::vector<int> fill(P.dof_ptr.begin(), P.dof_ptr.end() - 1);
+  for (int64_t s = 0; s < nslots; ++s) P.dof_slot[fill[L.patch_dofs[s]]++] = int(s);
+  if (weights == VK_WEIGHTS_MULTIPLICITY) {
+    P.weight.assign(L.ndof, 1.0);
+    for (int i = 0; i < L.ndof; ++i) {
+      const int c = P.dof_ptr[i + 1] - P.dof_ptr[i];
+      if (c > 0) P.weight[i] = 1.0 / c;
+    }
+  }
+  return P;
+}
+
+struct DevLevel {
+  int N = 0, ndof = 0, n_u = 0, n_p = 0;
+  vk::gpu::Sell A;
+  vk::gpu::Csr Acsr, P, R;
+  uint8_t* dir = nullptr;
+  vk::gpu::Patches pat;
+  double lam = 0.0;
+  double *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *t = nullptr, *delta = nullptr;
+};
+
+}  // namespace
+
+struct vk_hierarchy {
+  vk_problem prob{};
+  vk_options opt{};
+  std::vector<vk::HostLevel> host;
+  std::vector<DevLevel> lv;
+  DeviceMemory mem;
+  bool host_only = false;
+  int nc = 0;
+  double* Cinv = nullptr;
+  int kmax = 0;
+  int64_t ldv = 0;
+  double *V = nullptr, *Z = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *hist = nullptr;
+  double *yv = nullptr, *t2 = nullptr, *partial = nullptr, *scal = nullptr;
+  double *bh = nullptr, *xh = nullptr;
+  int* iflag = nullptr;
+  int* h_flag = nullptr;     // pinned host mirror (2 ints)
+  double* h_scal = nullptr;  // pinned host mirror (4 doubles)
+  std::vector<double> lambdas;
+  // statistics (vk_stats_*)
+  int64_t n_launch = 0, n_vcycle = 0;
+  bool time_apply = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  double apply_bytes = 0.0, apply_flops = 0.0;
+  ~vk_hierarchy() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+void validate(const vk_problem* p, const vk_options* o) {
+  if (!p || !o) raise(VK_ERR_ARG, "null problem or options");
+  if (p->k < 2 || p->k > 4) raise(VK_ERR_ARG, "order k must be 2, 3 or 4");
+  if (p->N_coarse < 1 || p->nlevels < 1 || p->nlevels > 12) raise(VK_ERR_ARG, "bad mesh hierarchy");
+  const int64_t Nf = int64_t(p->N_coarse) << (p->nlevels - 1);
+  if (Nf * p->k > 8192) raise(VK_ERR_ARG, "finest mesh too large for 32-bit indices");
+  if (!(p->nu > 0.0)) raise(VK_ERR_ARG, "viscosity must be positive");
+  if (o->sweeps < 1) raise(VK_ERR_ARG, "sweeps must be >= 1");
+  if (o->weights != VK_WEIGHTS_PLAIN && o->weights != VK_WEIGHTS_MULTIPLICITY) raise(VK_ERR_ARG, "bad weights");
+  if (o->factor_prec != VK_PREC_F64 && o->factor_prec != VK_PREC_F32) raise(VK_ERR_ARG, "bad factor_prec");
+  if (!(o->cheb_hi > o->cheb_lo) || !(o->cheb_lo > 0.0)) raise(VK_ERR_ARG, "bad Chebyshev interval");
+  if (o->eig_steps < 1 || o->eig_steps > 64) raise(VK_ERR_ARG, "eig_steps must be in 1..64");
+  if (o->max_iterations < 1 || o->max_iterations > 1000) raise(VK_ERR_ARG, "max_iterations must be in 1..1000");
+}
+
+void build_host(vk_hierarchy* h) {
+  const int L = h->prob.nlevels;
+  int nthreads = h->opt.host_threads > 0 ? h->opt.host_threads : int(std::thread::hardware_concurrency());
+  nthreads = std::max(1, std::min(nthreads, 64));
+  h->host.resize(L);
+  for (int l = 0; l < L; ++l) {
+    vk::build_level(h->prob.N_coarse << l, h->prob.k, h->prob.nu, l > 0, nthreads, h->host[l]);
+    if (l > 0) vk::build_transfer(h->host[l - 1], h->host[l]);
+  }
+}
+
+vk::gpu::Csr upload_csr(DeviceMemory& m, const vk::HostCsr& A) {
+  vk::gpu::Csr c;
+  c.nrows = A.nrows;
+  c.ptr = m.upload(A.ptr);
+  c.col = m.upload(A.col);
+  c.val = m.upload(A.val);
+  return c;
+}
+
+// Allocates every device buffer (or only counts the bytes when mem.counting_only is set).
+void allocate_device(vk_hierarchy* h) {
+  DeviceMemory& m = h->mem;
+  const int L = h->prob.nlevels;
+  h->lv.assign(L, DevLevel{});
+  const int fsz = h->opt.factor_prec == VK_PREC_F64 ? 8 : 4;
+  for (int l = 0; l < L; ++l) {
+    const vk::HostLevel& H = h->host[l];
+    DevLevel& D = h->lv[l];
+    D.N = H.N;
+    D.ndof = H.ndof;
+    D.n_u = H.n_u;
+    D.n_p = H.n_p;
+    HostSell S = build_sell(H.A);
+    D.A.nrows = H.ndof;
+    D.A.nslices = int(S.sw.size());
+    D.A.sptr = m.upload(S.sptr);
+    D.A.swidth = m.upload(S.sw);
+    D.A.col = m.upload(S.col);
+    D.A.val = m.upload(S.val);
+    D.A.rowof = m.upload(S.rowof);
+    D.Acsr = upload_csr(m, H.A);
+    D.dir = m.upload(H.dir);
+    if (l > 0) {
+      D.P = upload_csr(m, H.P);
+      D.R = upload_csr(m, H.R);
+    }
+    D.b = m.get_n<double>(H.ndof);
+    D.x = m.get_n<double>(H.ndof);
+    D.r = m.get_n<double>(H.ndof);
+    D.d = m.get_n<double>(H.ndof);
+    D.t = m.get_n<double>(H.ndof);
+    if (l > 0) {
+      HostPatchPlan P = plan_patches(H, h->opt.weights);
+      vk::gpu::Patches& G = D.pat;
+      G.npatch = int(H.patch_ptr.size()) - 1;
+      G.nslots = int64_t(H.patch_dofs.size());
+      G.slot_ptr = m.upload(H.patch_ptr);
+      G.slot_dofs = m.upload(H.patch_dofs);
+      G.work = m.upload(P.work);
+      G.foff = m.upload(P.foff);
+      G.factors = m.get(size_t(P.ftotal) * fsz);
+      G.prec = h->opt.factor_prec;
+      G.nb_max = P.nb_max;
+      G.dof_ptr = m.upload(P.dof_ptr);
+      G.dof_slot = m.upload(P.dof_slot);
+      G.weight = P.weight.empty() ? nullptr : m.upload(P.weight);
+      D.delta = m.get_n<double>(G.nslots);
+    }
+  }
+  h->nc = h->host[0].ndof;
+  const int mdim = h->nc + 1;
+  h->Cinv = m.get_n<double>(size_t(mdim) * mdim);
+  const int nf = h->host[L - 1].ndof;
+  h->kmax = h->opt.max_iterations;
+  h->ldv = (int64_t(nf) + 31) / 32 * 32;
+  h->V = m.get_n<double>(size_t(h->ldv) * (h->kmax + 1));
+  h->Z = m.get_n<double>(size_t(h->ldv) * h->kmax);
+  h->H = m.get_n<double>(size_t(h->kmax + 1) * h->kmax);
+  h->cs = m.get_n<double>(h->kmax);
+  h->sn = m.get_n<double>(h->kmax);
+  h->g = m.get_n<double>(h->kmax + 1);
+  h->hist = m.get_n<double>(h->kmax + 1);
+  h->yv = m.get_n<double>(h->kmax);
+  h->t2 = m.get_n<double>(h->kmax + 1);
+  h->partial = m.get_n<double>(size_t(vk::gpu::kReduceBlocks) * (std::max(h->kmax, mdim) + 1));
+  h->scal = m.get_n<double>(16);
+  h->iflag = m.get_n<int>(16);
+  h->bh = m.get_n<double>(nf);
+  h->xh = m.get_n<double>(nf);
+}
+
+// Finest-level patch applications are bracketed by CUDA events on their stream when timing is on.
+void timed_apply(vk_hierarchy* h, int l, const double* r, cudaStream_t s) {
+  DevLevel& D = h->lv[l];
+  const bool t = h->time_apply && l == h->prob.nlevels - 1;
+  if (t) {
+    if (h->ev_used + 2 > h->ev.size())
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        h->ev.push_back(e);
+      }
+    CK(cudaEventRecord(h->ev[h->ev_used], s));
+  }
+  h->n_launch += vk::gpu::patch_apply(D.pat, r, D.delta, s);
+  if (t) {
+    CK(cudaEventRecord(h->ev[h->ev_used + 1], s));
+    h->ev_used += 2;
+  }
+}
+
+double device_dot(vk_hierarchy* h, const double* x, const double* y, int n, cudaStream_t s) {
+  h->n_launch += vk::gpu::dot_partials(x, y, n, h->partial, s);
+  h->n_launch += vk::gpu::finalize_sum(h->partial, vk::gpu::kReduceBlocks, h->scal, s);
+  CK(cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return h->h_scal[0];
+}
+
+void vanka_apply(vk_hierarchy* h, int l, const double* r, double* z, cudaStream_t s) {
+  DevLevel& D = h->lv[l];
+  timed_apply(h, l, r, s);
+  h->n_launch += vk::gpu::vanka_scatter(D.pat, D.ndof, D.dir, r, D.delta, 0, 1.0, 0.0, 0.0, z, nullptr, nullptr, s);
+}
+
+// nu Chebyshev steps on [lo*lam, hi*lam] (Sec. 3), preconditioned by additive Vanka (Algorithm 1);
+// the Chebyshev coefficients follow the three-term recurrence (rho_k = 1/(2 sigma - rho_{k-1})).
+void smooth(vk_hierarchy* h, int l, const double* b, double* x, bool zero_init, cudaStream_t s) {
+  DevLevel& D = h->lv[l];
+  const double lam = D.lam;
+  const double emax = h->opt.cheb_hi * lam, emin = h->opt.cheb_lo * lam;
+  const double theta = 0.5 * (emax + emin), delta = 0.5 * (emax - emin);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  for (int step = 0; step < h->opt.sweeps; ++step) {
+    const double* rr = b;
+    if (!(step == 0 && zero_init)) {
+      h->n_launch += vk::gpu::sell_residual(D.A, b, x, D.r, s);
+      rr = D.r;
+    }
+    timed_apply(h, l, rr, s);
+    int mode;
+    double c1 = 0.0, c2 = 0.0;
+    if (step == 0) {
+      mode = zero_init ? 1 : 2;
+    } else {
+      const double rho_new = 1.0 / (2.0 * sigma - rho);
+      c1 = rho_new * rho;
+      c2 = 2.0 * rho_new / delta;
+      rho = rho_new;
+      mode = 3;
+    }
+    h->n_launch += vk::gpu::vanka_scatter(D.pat, D.ndof, D.dir, rr, D.delta, mode, theta, c1, c2, nullptr, D.d, x, s);
+  }
+}
+
+void vcycle(vk_hierarchy* h, int l, const double* b, double* x, cudaStream_t s) {
+  if (l == h->prob.nlevels - 1) ++h->n_vcycle;
+  if (l == 0) {
+    h->n_launch += vk::gpu::dense_gemv(h->Cinv, h->nc, h->nc + 1, b, x, s);
+    return;
+  }
+  DevLevel& D = h->lv[l];
+  DevLevel& C = h->lv[l - 1];
+  smooth(h, l, b, x, true, s);
+  h->n_launch += vk::gpu::sell_residual(D.A, b, x, D.r, s);
+  h->n_launch += vk::gpu::csr_restrict(D.R, C.dir, D.r, C.b, s);
+  vcycle(h, l - 1, C.b, C.x, s);
+  h->n_launch += vk::gpu::csr_prolong_add(D.P, C.x, x, s);
+  smooth(h, l, b, x, false, s);
+}
+
+// "standard GMRES estimation" (Sec. 3) read as eig_steps Arnoldi steps (modified Gram-Schmidt) on
+// M^{-1} A from a SplitMix64 start vector with Dirichlet entries zeroed and the pressure mean removed;
+// lambda = largest real part of the Ritz values.  Breakdown: ||w_orth|| <= 1e-12 ||M^{-1} A v_j||.
+double estimate_lambda(vk_hierarchy* h, int l, cudaStream_t s) {
+  const vk::HostLevel& H = h->host[l];
+  DevLevel& D = h->lv[l];
+  const int n = H.ndof, steps = h->opt.eig_steps;
+  std::vector<double> v0(n);
+  for (int i = 0; i < n; ++i) v0[i] = H.dir[i] ? 0.0 : vk::splitmix_uniform_pm1(h->opt.eig_seed + uint64_t(l), i);
+  double ps = 0.0;
+  for (int i = H.n_u; i < n; ++i) ps += v0[i];
+  const double mean = ps / H.n_p;
+  for (int i = H.n_u; i < n; ++i) v0[i] -= mean;
+  double nrm = 0.0;
+  for (double v : v0) nrm += v * v;
+  nrm = std::sqrt(nrm);
+  for (double& v : v0) v /= nrm;
+  if (steps + 1 > h->kmax + 1) raise(VK_ERR_ARG, "eig_steps exceeds the Krylov workspace");
+  const int64_t ld = h->ldv;
+  CK(cudaMemcpyAsync(h->V, v0.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  std::vector<double> Hm(size_t(steps + 1) * steps, 0.0);  // row-major (steps+1) x steps
+  int m = steps;
+  for (int j = 0; j < steps; ++j) {
+    double* vj = h->V + ld * j;
+    double* w = h->V + ld * (j + 1);
+    h->n_launch += vk::gpu::sell_residual(D.A, nullptr, vj, D.t, s);
+    vanka_apply(h, l, D.t, w, s);
+    const double wnorm = std::sqrt(device_dot(h, w, w, n, s));
+    for (int i = 0; i <= j; ++i) {
+      const double hij = device_dot(h, h->V + ld * i, w, n, s);
+      Hm[size_t(i) * steps + j] = hij;
+      h->n_launch += vk::gpu::axpy(-hij, h->V + ld * i, w, n, s);
+    }
+    const double hn = std::sqrt(device_dot(h, w, w, n, s));
+    Hm[size_t(j + 1) * steps + j] = hn;
+    if (hn <= 1e-12 * wnorm) {
+      m = j + 1;
+      break;
+    }
+    h->n_launch += vk::gpu::scale(1.0 / hn, w, n, s);
+  }
+  std::vector<double> sq(size_t(m) * m), re(m), im(m);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) sq[size_t(i) * m + j] = Hm[size_t(i) * steps + j];
+  if (vk::hessenberg_eigenvalues(m, sq.data(), re.data(), im.data()) != 0)
+    raise(VK_ERR_INTERNAL, "Hessenberg QR did not converge on level " + std::to_string(l));
+  return *std::max_element(re.begin(), re.end());
+}
+
+void setup_device(vk_hierarchy* h, cudaStream_t s) {
+  h->mem.stream = s;
+  allocate_device(h);
+  CK(cudaMallocHost(&h->h_flag, 4 * sizeof(int)));
+  CK(cudaMallocHost(&h->h_scal, 4 * sizeof(double)));
+  CK(cudaMemsetAsync(h->iflag, 0, 16 * sizeof(int), s));
+  const int L = h->prob.nlevels;
+  for (int l = 1; l < L; ++l) {
+    DevLevel& D = h->lv[l];
+    h->n_launch += vk::gpu::patch_factor(D.Acsr, D.pat, D.pat.prec, const_cast<void*>(D.pat.factors), h->iflag + l, s);
+    CK(cudaGetLastError());
+  }
+  // coarsest level: bordered inverse
+  {
+    DevLevel& C = h->lv[0];
+    const int mdim = h->nc + 1;
+    h->n_launch += vk::gpu::bordered_from_csr(C.Acsr, C.n_u, h->Cinv, s);
+    int* perm = reinterpret_cast<int*>(h->partial);  // scratch: mdim ints, mdim+1 doubles after them
+    double* fcol = h->partial + (mdim + 1) / 2 + 1;
+    h->n_launch += vk::gpu::gauss_jordan_inverse(h->Cinv, mdim, perm, fcol, h->iflag + 14, h->iflag, s);
+    CK(cudaGetLastError());
+  }
+  std::vector<int> st(16);
+  CK(cudaMemcpyAsync(st.data(), h->iflag, 16 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int l = 1; l < L; ++l)
+    if (st[l] != 0)
+      raise(VK_ERR_SINGULAR, "zero pivot in patch " + std::to_string(st[l] - 1) + " on level " + std::to_string(l));
+  if (st[0] != 0) raise(VK_ERR_SINGULAR, "zero pivot in the coarse bordered matrix");
+  {
+    const vk::HostLevel& F = h->host[L - 1];
+    double sn = 0.0, sn2 = 0.0;
+    const int np = int(F.patch_ptr.size()) - 1;
+    for (int p = 0; p < np; ++p) {
+      const double n = F.patch_ptr[p + 1] - F.patch_ptr[p];
+      sn += n;
+      sn2 += n * n;
+    }
+    const double fsz = h->opt.factor_prec == VK_PREC_F64 ? 8.0 : 4.0;
+    // inverse entries + slot DoF indices + gathered r + written delta + per-patch work/offset/pointers
+    h->apply_bytes = fsz * sn2 + 20.0 * sn + 16.0 * np;
+    h->apply_flops = 2.0 * sn2;
+  }
+  h->lambdas.assign(L, 0.0);
+  for (int l = 1; l < L; ++l) {
+    h->lambdas[l] = h->opt.lambdas ? h->opt.lambdas[l] : estimate_lambda(h, l, s);
+    if (!(h->lambdas[l] > 0.0) || !std::isfinite(h->lambdas[l]))
+      raise(VK_ERR_SINGULAR, "non-positive eigenvalue estimate on level " + std::to_string(l));
+    h->lv[l].lam = h->lambdas[l];
+  }
+  CK(cudaStreamSynchronize(s));
+}
+
+void check_level(const vk_hierarchy* h, int level, int min_level = 0) {
+  if (!h) raise(VK_ERR_ARG, "null hierarchy");
+  if (level < min_level || level >= h->prob.nlevels) raise(VK_ERR_ARG, "level out of range");
+}
+
+void check_device(const vk_hierarchy* h) {
+  if (!h) raise(VK_ERR_ARG, "null hierarchy");
+  if (h->host_only) raise(VK_ERR_ARG, "host-only hierarchy: no device data");
+}
+
+int solve_impl(vk_hierarchy* h, const double* b, double* x, double rtol, int maxit, vk_solve_info* info,
+               cudaStream_t s) {
+  check_device(h);
+  if (!b || !x) raise(VK_ERR_ARG, "null vector");
+  if (maxit < 1 || maxit > h->kmax) raise(VK_ERR_ARG, "maxit must be in 1..max_iterations");
+  if (!(rtol >= 0.0)) raise(VK_ERR_ARG, "rtol must be >= 0");
+  const auto t0 = std::chrono::steady_clock::now();
+  const int L = h->prob.nlevels;
+  DevLevel& F = h->lv[L - 1];
+  const int n = F.ndof;
+  const int64_t ld = h->ldv;
+  const int ldh = h->kmax + 1;
+  // b_hat = b projected off the constant pressure; v_1 = b_hat / ||b_hat||
+  h->n_launch += vk::gpu::copy(h->V, b, n, s);
+  h->n_launch += vk::gpu::pressure_project(h->V, F.n_u, F.n_p, h->partial, h->scal + 1, s);
+  const double beta = std::sqrt(device_dot(h, h->V, h->V, n, s));
+  int status = VK_OK;
+  int iters = 0;
+  bool converged = false;
+  std::vector<double> hist;
+  if (!std::isfinite(beta)) raise(VK_ERR_NONFINITE, "right-hand side is not finite");
+  if (beta == 0.0) {
+    h->n_launch += vk::gpu::fill(x, 0.0, n, s);
+    CK(cudaStreamSynchronize(s));
+    converged = true;
+    hist.assign(1, 0.0);
+  } else {
+    h->n_launch += vk::gpu::scale(1.0 / beta, h->V, n, s);
+    h->n_launch += vk::gpu::fill(h->g, 0.0, h->kmax + 1, s);
+    CK(cudaMemcpyAsync(h->g, &beta, sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->hist, &beta, sizeof(double), cudaMemcpyHostToDevice, s));
+    for (int j = 0; j < maxit; ++j) {
+      double* vj = h->V + ld * j;
+      double* zj = h->Z + ld * j;
+      double* w = h->V + ld * (j + 1);
+      double* hcol = h->H + int64_t(j) * ldh;
+      vcycle(h, L - 1, vj, zj, s);
+      h->n_launch += vk::gpu::pressure_project(zj, F.n_u, F.n_p, h->partial, h->scal + 1, s);
+      h->n_launch += vk::gpu::sell_residual(F.A, nullptr, zj, w, s);
+      // classical Gram-Schmidt, twice
+      h->n_launch += vk::gpu::multi_dot_partials(h->V, ld, j + 1, w, n, h->partial, s);
+      h->n_launch += vk::gpu::multi_finalize(h->partial, j + 1, hcol, nullptr, s);
+      h->n_launch += vk::gpu::multi_axpy(h->V, ld, j + 1, hcol, w, n, s);
+      h->n_launch += vk::gpu::multi_dot_partials(h->V, ld, j + 1, w, n, h->partial, s);
+      h->n_launch += vk::gpu::multi_finalize(h->partial, j + 1, h->t2, hcol, s);
+      h->n_launch += vk::gpu::multi_axpy(h->V, ld, j + 1, h->t2, w, n, s);
+      h->n_launch += vk::gpu::dot_partials(w, w, n, h->partial, s);
+      h->n_launch += vk::gpu::finalize_sum(h->partial, vk::gpu::kReduceBlocks, h->scal + 2, s);
+      h->n_launch += vk::gpu::normalize(w, h->scal + 2, w, hcol + j + 1, n, s);
+      h->n_launch += vk::gpu::givens_update(h->H, ldh, h->cs, h->sn, h->g, h->hist, j, rtol, h->iflag + 8, s);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(h->h_flag, h->iflag + 8, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      iters = j + 1;
+      if (h->h_flag[1]) {
+        status = VK_ERR_NONFINITE;
+        g_err = "FGMRES residual estimate is not finite";
+        break;
+      }
+      if (h->h_flag[0]) {
+        converged = true;
+        break;
+      }
+    }
+    // y = H^{-1} g (upper triangular after the rotations), x = Z y
+    const int m = iters;
+    std::vector<double> Hh(size_t(ldh) * m), gh(m + 1), y(m);
+    CK(cudaMemcpyAsync(Hh.data(), h->H, Hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(gh.data(), h->g, (m + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    hist.assign(m + 1, 0.0);
+    CK(cudaMemcpyAsync(hist.data(), h->hist, (m + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = m - 1; i >= 0; --i) {
+      double acc = gh[i];
+      for (int k = i + 1; k < m; ++k) acc -= Hh[size_t(k) * ldh + i] * y[k];
+      y[i] = acc / Hh[size_t(i) * ldh + i];
+    }
+    CK(cudaMemcpyAsync(h->yv, y.data(), m * sizeof(double), cudaMemcpyHostToDevice, s));
+    h->n_launch += vk::gpu::combine(h->Z, ld, m, h->yv, x, n, s);
+  }
+  // true residual of the projected system
+  double true_res = 0.0;
+  {
+    h->n_launch += vk::gpu::copy(F.t, b, n, s);
+    h->n_launch += vk::gpu::pressure_project(F.t, F.n_u, F.n_p, h->partial, h->scal + 1, s);
+    h->n_launch += vk::gpu::sell_residual(F.A, F.t, x, F.r, s);
+    true_res = std::sqrt(device_dot(h, F.r, F.r, n, s));
+  }
+  if (status == VK_OK && !converged) {
+    status = VK_ERR_NOT_CONVERGED;
+    g_err = "FGMRES did not reach rtol in maxit iterations";
+  }
+  if (info) {
+    info->iterations = iters;
+    info->converged = converged ? 1 : 0;
+    info->res0 = beta;
+    info->res_est = hist.empty() ? 0.0 : hist.back();
+    info->true_res = true_res;
+    if (info->history)
+      for (size_t i = 0; i < hist.size(); ++i) info->history[i] = hist[i];
+    info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return status;
+}
+
+const vk::HostCsr& pick_csr(const vk_hierarchy* h, int level, int which) {
+  const vk::HostLevel& L = h->host[level];
+  if (which == VK_CSR_A) return L.A;
+  if (level < 1) raise(VK_ERR_ARG, "P and R exist from level 1");
+  if (which == VK_CSR_P) return L.P;
+  if (which == VK_CSR_R) return L.R;
+  raise(VK_ERR_ARG, "unknown matrix");
+}
+
+}  // namespace
+
+extern "C" {
+
+void vk_default_options(vk_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->sweeps = 1;
+  o->weights = VK_WEIGHTS_PLAIN;
+  o->cheb_lo = 0.25;
+  o->cheb_hi = 1.1;
+  o->eig_steps = 10;
+  o->eig_seed = 0x5EED;
+  o->lambdas = nullptr;
+  o->factor_prec = VK_PREC_F64;
+  o->use_graph = 1;
+  o->host_threads = 0;
+  o->host_only = 0;
+  o->max_iterations = 100;
+}
+
+const char* vk_last_error(void) { return g_err.c_str(); }
+
+int vk_setup(const vk_problem* p, const vk_options* o, const vk_allocator* alloc, void* stream,
+             vk_hierarchy** out) {
+  return guard([&] {
+    if (!out) raise(VK_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    validate(p, o);
+    auto h = std::make_unique<vk_hierarchy>();
+    h->prob = *p;
+    h->opt = *o;
+    h->opt.lambdas = nullptr;
+    h->host_only = o->host_only != 0;
+    if (alloc && alloc->alloc && alloc->release) {
+      h->mem.user = *alloc;
+      h->mem.custom = true;
+    }
+    build_host(h.get());
+    if (!h->host_only) {
+      vk_options tmp = h->opt;
+      h->opt.lambdas = o->lambdas;
+      try {
+        setup_device(h.get(), static_cast<cudaStream_t>(stream));
+      } catch (...) {
+        cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+        h->mem.release_all();
+        if (h->h_flag) cudaFreeHost(h->h_flag);
+        if (h->h_scal) cudaFreeHost(h->h_scal);
+        throw;
+      }
+      h->opt = tmp;
+    }
+    *out = h.release();
+    return VK_OK;
+  });
+}
+
+void vk_destroy(vk_hierarchy* h) {
+  if (!h) return;
+  if (!h->host_only) {
+    cudaDeviceSynchronize();
+    h->mem.release_all();
+    if (h->h_flag) cudaFreeHost(h->h_flag);
+    if (h->h_scal) cudaFreeHost(h->h_scal);
+  }
+  delete h;
+}
+
+int vk_footprint(const vk_problem* p, const vk_options* o, size_t* device_bytes) {
+  return guard([&] {
+    validate(p, o);
+    if (!device_bytes) raise(VK_ERR_ARG, "null output");
+    vk_hierarchy h;
+    h.prob = *p;
+    h.opt = *o;
+    build_host(&h);
+    h.mem.counting_only = true;
+    allocate_device(&h);
+    *device_bytes = h.mem.total;
+    return VK_OK;
+  });
+}
+
+int vk_device_bytes(const vk_hierarchy* h, size_t* bytes) {
+  return guard([&] {
+    if (!h || !bytes) raise(VK_ERR_ARG, "null argument");
+    *bytes = h->mem.total;
+    return VK_OK;
+  });
+}
+
+int vk_level_info(const vk_hierarchy* h, int level, int32_t* ndof, int32_t* n_u, int64_t* nnz, int32_t* npatch,
+                  int64_t* nslots) {
+  return guard([&] {
+    check_level(h, level);
+    const vk::HostLevel& L = h->host[level];
+    if (ndof) *ndof = L.ndof;
+    if (n_u) *n_u = L.n_u;
+    if (nnz) *nnz = L.A.nnz();
+    if (npatch) *npatch = L.patch_ptr.empty() ? 0 : int32_t(L.patch_ptr.size() - 1);
+    if (nslots) *nslots = int64_t(L.patch_dofs.size());
+    return VK_OK;
+  });
+}
+
+int vk_lambda(const vk_hierarchy* h, int level, double* lambda) {
+  return guard([&] {
+    check_level(h, level, 1);
+    check_device(h);
+    if (!lambda) raise(VK_ERR_ARG, "null output");
+    *lambda = h->lambdas[level];
+    return VK_OK;
+  });
+}
+
+int vk_residual(vk_hierarchy* h, int level, const double* b, const double* x, double* r, void* stream) {
+  return guard([&] {
+    check_level(h, level);
+    check_device(h);
+    if (!b || !x || !r) raise(VK_ERR_ARG, "null vector");
+    h->n_launch += vk::gpu::sell_residual(h->lv[level].A, b, x, r, static_cast<cudaStream_t>(stream));
+    CK(cudaGetLastError());
+    return VK_OK;
+  });
+}
+
+int vk_vanka(vk_hierarchy* h, int level, const double* r, double* z, void* stream) {
+  return guard([&] {
+    check_level(h, level, 1);
+    check_device(h);
+    if (!r || !z || r == z) raise(VK_ERR_ARG, "null or aliased vectors");
+    vanka_apply(h, level, r, z, static_cast<cudaStream_t>(stream));
+    CK(cudaGetLastError());
+    return VK_OK;
+  });
+}
+
+int vk_smooth(vk_hierarchy* h, int level, const double* b, double* x, int zero_init, void* stream) {
+  return guard([&] {
+    check_level(h, level, 1);
+    check_device(h);
+    if (!b || !x || b == x) raise(VK_ERR_ARG, "null or aliased vectors");
+    smooth(h, level, b, x, zero_init != 0, static_cast<cudaStream_t>(stream));
+    CK(cudaGetLastError());
+    return VK_OK;
+  });
+}
+
+int vk_restrict(vk_hierarchy* h, int fine_level, const double* r_fine, double* r_coarse, void* stream) {
+  return guard([&] {
+    check_level(h, fine_level, 1);
+    check_device(h);
+    if (!r_fine || !r_coarse) raise(VK_ERR_ARG, "null vector");
+    h->n_launch += vk::gpu::csr_restrict(h->lv[fine_level].R, h->lv[fine_level - 1].dir, r_fine, r_coarse,
+                          static_cast<cudaStream_t>(stream));
+    CK(cudaGetLastError());
+    return VK_OK;
+  });
+}
+
+int vk_prolong(vk_hierarchy* h, int fine_level, const double* e_coarse, double* x_fine, void* stream) {
+  return guard([&] {
+    check_level(h, fine_level, 1);
+    check_device(h);
+    if (!e_coarse || !x_fine) raise(VK_ERR_ARG, "null vector");
+    h->n_launch += vk::gpu::csr_prolong_add(h->lv[fine_level].P, e_coarse, x_fine, static_cast<cudaStream_t>(stream));
+    CK(cudaGetLastError());
+    return VK_OK;
+  });
+}
+
+int vk_coarse_solve(vk_hierarchy* h, const double* b, double* x, void* stream) {
+  return guard([&] {
+    check_device(h);
+    if (!b || !x) raise(VK_ERR_ARG, "null vector");
+    h->n_launch += vk::gpu::dense_gemv(h->Cinv, h->nc, h->nc + 1, b, x, static_cast<cudaStream_t>(stream));
+    CK(cudaGetLastError());
+    return VK_OK;
+  });
+}
+
+int vk_vcycle(vk_hierarchy* h, const double* b, double* x, void* stream) {
+  return guard([&] {
+    check_device(h);
+    if (!b || !x || b == x) raise(VK_ERR_ARG, "null or aliased vectors");
+    vcycle(h, h->prob.nlevels - 1, b, x, static_cast<cudaStream_t>(stream));
+    CK(cudaGetLastError());
+    return VK_OK;
+  });
+}
+
+int vk_solve(vk_hierarchy* h, const double* b, double* x, double rtol, int maxit, vk_solve_info* info,
+             void* stream) {
+  return guard([&] { return solve_impl(h, b, x, rtol, maxit, info, static_cast<cudaStream_t>(stream)); });
+}
+
+int vk_solve_host(vk_hierarchy* h, const double* b_host, double* x_host, double rtol, int maxit,
+                  vk_solve_info* info, void* stream) {
+  return guard([&] {
+    check_device(h);
+    if (!b_host || !x_host) raise(VK_ERR_ARG, "null vector");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n = h->lv.back().ndof;
+    const auto t0 = std::chrono::steady_clock::now();
+    CK(cudaMemcpyAsync(h->bh, b_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    int st = solve_impl(h, h->bh, h->xh, rtol, maxit, info, s);
+    if (st != VK_OK && st != VK_ERR_NOT_CONVERGED) return st;
+    CK(cudaMemcpyAsync(x_host, h->xh, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (info)
+      info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+  });
+}
+
+int vk_csr_dims(const vk_hierarchy* h, int level, int which, int32_t* nrows, int32_t* ncols, int64_t* nnz) {
+  return guard([&] {
+    check_level(h, level);
+    const vk::HostCsr& A = pick_csr(h, level, which);
+    if (nrows) *nrows = A.nrows;
+    if (ncols) *ncols = A.ncols;
+    if (nnz) *nnz = A.nnz();
+    return VK_OK;
+  });
+}
+
+int vk_export_csr(const vk_hierarchy* h, int level, int which, int32_t* ptr, int32_t* col, double* val) {
+  return guard([&] {
+    check_level(h, level);
+    const vk::HostCsr& A = pick_csr(h, level, which);
+    if (ptr) std::copy(A.ptr.begin(), A.ptr.end(), ptr);
+    if (col) std::copy(A.col.begin(), A.col.end(), col);
+    if (val) std::copy(A.val.begin(), A.val.end(), val);
+    return VK_OK;
+  });
+}
+
+int vk_export_patches(const vk_hierarchy* h, int level, int32_t* ptr, int32_t* dofs, int8_t* kind) {
+  return guard([&] {
+    check_level(h, level, 1);
+    const vk::HostLevel& L = h->host[level];
+    if (ptr) std::copy(L.patch_ptr.begin(), L.patch_ptr.end(), ptr);
+    if (dofs) std::copy(L.patch_dofs.begin(), L.patch_dofs.end(), dofs);
+    if (kind) std::copy(L.patch_kind.begin(), L.patch_kind.end(), kind);
+    return VK_OK;
+  });
+}
+
+int vk_export_dirichlet(const vk_hierarchy* h, int level, uint8_t* flags) {
+  return guard([&] {
+    check_level(h, level);
+    if (!flags) raise(VK_ERR_ARG, "null output");
+    const vk::HostLevel& L = h->host[level];
+    std::copy(L.dir.begin(), L.dir.end(), flags);
+    return VK_OK;
+  });
+}
+
+int vk_stats_reset(vk_hierarchy* h, int time_kernels) {
+  return guard([&] {
+    check_device(h);
+    h->n_launch = 0;
+    h->n_vcycle = 0;
+    h->ev_used = 0;
+    h->time_apply = time_kernels != 0;
+    return VK_OK;
+  });
+}
+
+int vk_stats_read(vk_hierarchy* h, vk_stats* out) {
+  return guard([&] {
+    check_device(h);
+    if (!out) raise(VK_ERR_ARG, "null output");
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+      CK(cudaEventSynchronize(h->ev[i + 1]));
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, h->ev[i], h->ev[i + 1]));
+      ms += t;
+    }
+    out->launches = h->n_launch;
+    out->vcycles = h->n_vcycle;
+    out->apply_launches = int64_t(h->ev_used / 2);
+    out->apply_ms = ms;
+    out->apply_bytes = h->apply_bytes;
+    out->apply_flops = h->apply_flops;
+    return VK_OK;
+  });
+}
+
+int vk_hessenberg_eigenvalues(int m, const double* H, double* re, double* im) {
+  return guard([&] {
+    if (m < 1 || !H || !re || !im) raise(VK_ERR_ARG, "bad arguments");
+    if (vk::hessenberg_eigenvalues(m, H, re, im) != 0) raise(VK_ERR_INTERNAL, "QR iteration did not converge");
+    return VK_OK;
+  });
+}
+
+}  // extern "C"

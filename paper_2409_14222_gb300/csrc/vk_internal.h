@@ -1,0 +1,48 @@
+// Internal declarations of the Vanka multigrid library (host setup structures, kernel launchers).
+// Not part of the public C ABI; see include/vk.h for that.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace vk {
+
+// ------------------------------------------------------------------------------------------------
+// Host-side sparse matrix (CSR, int32 indices, FP64 values).
+struct HostCsr {
+  int nrows = 0, ncols = 0;
+  std::vector<int> ptr, col;
+  std::vector<double> val;
+  int64_t nnz() const { return ptr.empty() ? 0 : ptr.back(); }
+};
+
+// One mesh level of the Taylor-Hood (P_k, P_{k-1}) discretization on the structured triangle mesh.
+struct HostLevel {
+  int N = 0, k = 0;
+  int nv1 = 0, np1 = 0;     // lattice sizes per side: k*N+1 (velocity), (k-1)*N+1 (pressure)
+  int n_u = 0, n_p = 0, ndof = 0;
+  HostCsr A;                // saddle-point matrix with Dirichlet identity rows / zero columns
+  HostCsr P, R;             // prolongation from the next coarser level and R = P^T (empty on level 0)
+  std::vector<uint8_t> dir; // 1 at Dirichlet velocity DoFs
+  // Vanka patches (empty on the coarsest level): DoFs of patch p are dofs[ptr[p] .. ptr[p+1]).
+  std::vector<int> patch_ptr, patch_dofs;
+  std::vector<int8_t> patch_kind;  // 0 vertex, 1 edge, 2 cell
+};
+
+// host_fem.cpp
+void build_level(int N, int k, double nu, bool with_patches, int nthreads, HostLevel& L);
+void build_transfer(const HostLevel& coarse, HostLevel& fine);
+// Element matrices of one cell shape, for tests and the manufactured load (row-major).
+void element_matrices(int k, int e1x, int e1y, int e2x, int e2y, double h, double nu,
+                      std::vector<double>& Aloc, std::vector<double>& Bloc);
+void gauss_legendre01(int q, std::vector<double>& x, std::vector<double>& w);
+
+// host_eig.cpp: eigenvalues of a small real upper-Hessenberg matrix (row-major m x m).
+int hessenberg_eigenvalues(int m, const double* H, double* re, double* im);
+
+// SplitMix64 counter-based uniform on [-1, 1): value i of stream `seed`.
+double splitmix_uniform_pm1(uint64_t seed, uint64_t i);
+
+}  // namespace vk

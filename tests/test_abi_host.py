@@ -1,0 +1,102 @@
+"""CPU tests of the C-ABI library: it builds, loads, exports every declared symbol, and its host-side
+setup (assembly, transfers, patches, Dirichlet flags, eigenvalue helper) equals the oracle's."""
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import fem, patches as opatches
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def vk():
+    from paper_2409_14222_gb300 import build
+    build.build()
+    import paper_2409_14222_gb300 as vk
+    return vk
+
+
+def test_every_declared_symbol_is_exported(vk):
+    with open(os.path.join(ROOT, "include", "vk.h")) as f:
+        hdr = f.read()
+    declared = set(re.findall(r"^\s*(?:int|void|const char\*)\s+(vk_\w+)\s*\(", hdr, re.M))
+    assert declared == set(vk.SYMBOLS)
+    L = vk.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+def _csr(vkmod, h, level, which):
+    (nr, nc), ptr, col, val = h.export_csr(level, which)
+    return sp.csr_matrix((val, col, ptr), shape=(nr, nc))
+
+
+@pytest.mark.parametrize("Nc,L,k", [(4, 2, 2), (2, 3, 2), (2, 2, 3), (2, 2, 4), (1, 3, 3)])
+def test_host_setup_equals_oracle(vk, Nc, L, k):
+    h = vk.Hierarchy(Nc, L, k, nu=1.3, host_only=True)
+    for l in range(L):
+        s = fem.Space(Nc * 2 ** l, k)
+        K = fem.assemble_full(s, 1.3)
+        mask = s.dirichlet_mask()
+        Ao = fem.apply_dirichlet(K, mask)
+        A = _csr(vk, h, l, vk.VK_CSR_A)
+        assert A.shape == Ao.shape
+        assert abs(A - Ao).max() <= 1e-14 * abs(Ao).max()
+        # columns sorted, Dirichlet rows are exactly identity rows
+        (nr, nc), ptr, col, val = h.export_csr(l, vk.VK_CSR_A)
+        assert all(np.all(np.diff(col[ptr[i]:ptr[i + 1]]) > 0) for i in range(nr))
+        assert np.array_equal(h.export_dirichlet(l), mask)
+        if l > 0:
+            P = _csr(vk, h, l, vk.VK_CSR_P)
+            Po = fem.prolongation(fem.Space(Nc * 2 ** (l - 1), k), s)
+            assert abs(P - Po).max() == 0.0          # both exact rationals, correctly rounded
+            R = _csr(vk, h, l, vk.VK_CSR_R)
+            assert abs(R - Po.T).max() == 0.0
+            ptr, dofs, kind = h.export_patches(l)
+            op = opatches.build_patches(s)
+            assert len(ptr) - 1 == len(op)
+            for i, (knd, ent, d) in enumerate(op):
+                assert np.array_equal(dofs[ptr[i]:ptr[i + 1]], d), (l, i)
+                assert kind[i] == {"vertex": 0, "edge": 1, "cell": 2}[knd]
+
+
+def test_hessenberg_eigenvalues_match_lapack(vk):
+    rng = np.random.default_rng(0)
+    for m in (1, 2, 3, 5, 10, 12):
+        for trial in range(5):
+            H = np.triu(rng.standard_normal((m, m)), -1)
+            got = list(vk.hessenberg_eigenvalues(H))
+            want = np.linalg.eigvals(H)
+            tol = 1e-10 * max(1.0, np.abs(want).max())
+            for w in want:                      # match each LAPACK eigenvalue to a distinct one of ours
+                i = int(np.argmin([abs(g - w) for g in got]))
+                assert abs(got.pop(i) - w) <= tol, (m, w)
+    # symmetric tridiagonal: real spectrum
+    T = np.diag(np.arange(1.0, 9.0)) + np.diag(np.ones(7), 1) + np.diag(np.ones(7), -1)
+    got = np.sort(vk.hessenberg_eigenvalues(T).real)
+    assert np.allclose(got, np.linalg.eigvalsh(T), atol=1e-12)
+
+
+def test_footprint_and_sizes(vk):
+    b = vk.footprint(16, 4, 2)
+    assert b > 0
+    h = vk.Hierarchy(16, 4, 2, host_only=True)
+    info = h.level_info(3)
+    assert info["ndof"] == 148739 and info["n_u"] == 132098
+    assert info["npatch"] == 129 ** 2
+    with pytest.raises(vk.VkError):
+        vk.Hierarchy(4, 2, 5, host_only=True)
+    with pytest.raises(vk.VkError):
+        h.export_patches(0)
+
+
+def test_host_only_hierarchy_refuses_device_calls(vk):
+    import ctypes
+    h = vk.Hierarchy(2, 2, 2, host_only=True)
+    with pytest.raises(vk.VkError) as e:
+        h.lam(1)
+    assert e.value.code == vk.vk.VK_ERR_ARG
