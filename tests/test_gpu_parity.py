@@ -182,7 +182,8 @@ def _solve_parity(vk, H, G, b, rtol, maxit=100):
     check_history(hist, want)
     print(f"solve: {out['iterations']} iterations, x rel. dev {rel(host(x), ref.x):.2e}")
     assert rel(host(x), ref.x) <= 1e-10
-    assert abs(out["true_res"] - ref.true_res) <= 1e-6 * ref.hist[0] * rtol + 1e-8 * ref.true_res
+    # recomputing b - A x in FP64 carries about eps * ||b|| of rounding: compare with that floor
+    assert abs(out["true_res"] - ref.true_res) <= 1e-11 * ref.hist[0]
     return out, ref
 
 
