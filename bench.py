@@ -38,6 +38,22 @@ HBM_FALLBACK = 6800.0
 FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 (vector and tensor) nominal rate
 
 
+def recorded_traffic(config, prec):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu record, or None when the
+    record is for another workload or the kernel source changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)["k_patch_apply"]
+        with open(os.path.join(ROOT, "paper_2409_14222_gb300", "csrc", rec["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except (OSError, KeyError, ValueError):
+        return None
+    if sha != rec["source_sha256_16"] or config != "cfg2" or prec != "f64":
+        return None
+    return float(rec["dram_bytes_per_launch"])
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -260,6 +276,7 @@ def run_vk(args, cfg):
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": frac_hbm, "traffic": None,
                 "kernel": f"k_patch_apply (finest level, {args.prec.upper()} inverses)",
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+    roof["traffic"] = recorded_traffic(args.config, args.prec)
     roof["launch_avg_us"] = apply_avg_s * 1e6
     roof["bytes_per_launch"] = st["apply_bytes"]
     cpu = None
