@@ -151,6 +151,21 @@ int vk_residual(vk_hierarchy* h, int level, const double* b_dev, const double* x
  * DoFs get z = r.  r_dev and z_dev must not alias. */
 int vk_vanka(vk_hierarchy* h, int level, const double* r_dev, double* z_dev, void* stream);
 
+/* Same result as vk_vanka, but the call allocates no device memory: the per-slot corrections go to
+ * one fixed 8 MiB device array (2^20 FP64 values) compiled into the library, instead of the buffer
+ * the hierarchy allocated at setup.  For callers that must not allocate at the point of use: a
+ * process whose device memory is reserved up front by another allocator, or a thread that must not
+ * risk the device-wide synchronisation that cudaMalloc / cudaFree can cause.  (The paper has no
+ * counterpart: this is a deployment variant of Algorithm 1's additive correction.)
+ *   - Levels with more than 2^20 patch slots (sum of patch sizes, vk_level_info) get VK_ERR_ARG.
+ *   - The array exists once per GPU that loads the library and lives until the process exits.
+ *   - The first call on a device looks the array's device address up with that device current
+ *     (cudaGetSymbolAddress); make that first call before any stream capture on that device.
+ *   - All calls share the array: calls whose work overlaps on the GPU (other streams, other threads,
+ *     other hierarchies) race on it and must be serialised by the caller.  Nothing in it needs to
+ *     start at zero; it keeps the last call's values. */
+int vk_vanka_noalloc(vk_hierarchy* h, int level, const double* r_dev, double* z_dev, void* stream);
+
 /* `sweeps` Chebyshev steps (Sec. 3, "Relaxation") of the Vanka-preconditioned iteration for
  * A_level x = b on [cheb_lo*lambda, cheb_hi*lambda].  zero_init = 1 ignores x on input (x0 = 0). */
 int vk_smooth(vk_hierarchy* h, int level, const double* b_dev, double* x_dev, int zero_init,

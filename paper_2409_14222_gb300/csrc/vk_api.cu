@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -947,3 +948,56 @@ int vk_hessenberg_eigenvalues(int m, const double* H, double* re, double* im) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// Allocation-free additive Vanka application.  Some callers cannot allocate device memory at the
+// point where they need a relaxation sweep: a process whose device memory is fully reserved up front
+// by another allocator (a pool that would fail or evict), or a latency-critical thread that must not
+// hit the device-wide synchronisation cudaMalloc / cudaFree can imply.  vk_vanka keeps its per-slot
+// corrections in a buffer the hierarchy allocated at setup; this variant keeps them instead in one
+// fixed file-scope device array, so the call itself allocates nothing.
+namespace {
+
+constexpr int64_t kNoAllocMaxSlots = int64_t(1) << 20;  // 8 MiB of FP64 corrections per device
+static __device__ __align__(256) double g_noalloc_delta[kNoAllocMaxSlots];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {};  // per device: address of g_noalloc_delta, set once
+
+// Host code cannot use g_noalloc_delta directly (on the host it names a stand-in, not device
+// memory): look its device address up once per device, with that device current.
+double* noalloc_scratch() {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) raise(VK_ERR_CUDA, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_delta);
+    if (e != cudaSuccess || !p)
+      raise(VK_ERR_CUDA, std::string("cudaGetSymbolAddress(noalloc scratch): ") + cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  return g_noalloc_ptr[dev];
+}
+
+}  // namespace
+
+extern "C" int vk_vanka_noalloc(vk_hierarchy* h, int level, const double* r, double* z, void* stream) {
+  return guard([&] {
+    check_level(h, level, 1);
+    check_device(h);
+    if (!r || !z || r == z) raise(VK_ERR_ARG, "null or aliased vectors");
+    DevLevel& D = h->lv[level];
+    if (D.pat.nslots > kNoAllocMaxSlots)
+      raise(VK_ERR_ARG, "level " + std::to_string(level) + " has " + std::to_string(D.pat.nslots) +
+                            " patch slots; vk_vanka_noalloc supports at most " + std::to_string(kNoAllocMaxSlots));
+    double* delta = noalloc_scratch();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // every slot is written by the patch solves before the sum reads it: nothing to clear
+    h->n_launch += vk::gpu::patch_apply(D.pat, r, delta, s);
+    h->n_launch += vk::gpu::vanka_scatter(D.pat, D.ndof, D.dir, r, delta, 0, 1.0, 0.0, 0.0, z, nullptr, nullptr, s);
+    CK(cudaGetLastError());
+    return VK_OK;
+  });
+}

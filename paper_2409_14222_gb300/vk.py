@@ -37,6 +37,7 @@ SYMBOLS = [
     "vk_level_info", "vk_lambda", "vk_residual", "vk_vanka", "vk_smooth", "vk_restrict", "vk_prolong",
     "vk_coarse_solve", "vk_vcycle", "vk_solve", "vk_solve_host", "vk_csr_dims", "vk_export_csr",
     "vk_export_patches", "vk_export_dirichlet", "vk_hessenberg_eigenvalues", "vk_stats_reset", "vk_stats_read",
+    "vk_vanka_noalloc",
 ]
 
 
@@ -101,6 +102,7 @@ def lib():
             "vk_lambda": (I, [H, I, P(D)]),
             "vk_residual": (I, [H, I, VP, VP, VP, VP]),
             "vk_vanka": (I, [H, I, VP, VP, VP]),
+            "vk_vanka_noalloc": (I, [H, I, VP, VP, VP]),
             "vk_smooth": (I, [H, I, VP, VP, I, VP]),
             "vk_restrict": (I, [H, I, VP, VP, VP]),
             "vk_prolong": (I, [H, I, VP, VP, VP]),
@@ -281,6 +283,10 @@ class Hierarchy:
 
     def vanka(self, level, r, z, stream=None):
         check(lib().vk_vanka(self.handle, level, _ptr(r), _ptr(z), _stream_handle(stream)))
+
+    def vanka_noalloc(self, level, r, z, stream=None):
+        """vk_vanka without any device allocation (corrections in the library's fixed device array)."""
+        check(lib().vk_vanka_noalloc(self.handle, level, _ptr(r), _ptr(z), _stream_handle(stream)))
 
     def smooth(self, level, b, x, zero_init, stream=None):
         check(lib().vk_smooth(self.handle, level, _ptr(b), _ptr(x), int(zero_init), _stream_handle(stream)))
