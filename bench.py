@@ -215,6 +215,10 @@ def run_vk(args, cfg):
     opts = vk.default_options(sweeps=sweeps)
     if args.prec == "f32":
         opts.factor_prec = vk.VK_PREC_F32
+    elif args.prec == "f64e":
+        opts.factor_prec = vk.VK_PREC_F64E
+    if args.no_graph:
+        opts.use_graph = 0
     stream = torch.cuda.current_stream()
     G = vk.Hierarchy(Nc, L, k, options=opts)
     ndof = G.ndof()
@@ -226,7 +230,7 @@ def run_vk(args, cfg):
     for w in range(args.warmup):
         G.solve(B[w], x, rtol=rtol, history=False)
     torch.cuda.synchronize()
-    G.stats_reset(time_kernels=True)
+    G.stats_reset(time_kernels=False)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     iters = []
     barrier(world)
@@ -249,6 +253,16 @@ def run_vk(args, cfg):
     total_s = max_over_ranks(sum(times_ms) / 1e3, world)
     value = world * args.steps / total_s
     vcycles = st["vcycles"]
+    # dominant kernel: every finest-level patch-apply launch of the same K solves, bracketed by CUDA
+    # events on its stream (the solves run through the host-driven FGMRES loop here, because events
+    # cannot bracket each iteration of the graph's device-side loop; the kernels and launch
+    # configurations are the same)
+    G.stats_reset(time_kernels=True)
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        G.solve(B[args.warmup + s], x, rtol=rtol, history=False)
+    torch.cuda.synchronize()
+    kt = G.stats()
     # end to end through the C ABI with host buffers (pinned): H2D copy + solve + D2H copy per step
     bh = [torch.from_numpy(si.rhs_normal(ndof, 7777 + s)).pin_memory() for s in range(args.steps)]
     xh = torch.zeros(ndof, dtype=torch.float64).pin_memory()
@@ -263,9 +277,9 @@ def run_vk(args, cfg):
         return
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK))
-    apply_avg_s = st["apply_ms"] / max(st["apply_launches"], 1) / 1e3
-    gbs = st["apply_bytes"] / apply_avg_s / 1e9
-    gflops = st["apply_flops"] / apply_avg_s / 1e9
+    apply_avg_s = kt["apply_ms"] / max(kt["apply_launches"], 1) / 1e3
+    gbs = kt["apply_bytes"] / apply_avg_s / 1e9
+    gflops = kt["apply_flops"] / apply_avg_s / 1e9
     frac_hbm, frac_alu = gbs / hbm, gflops / FP64_NOMINAL_GFLOPS
     if args.prec == "f64" and frac_alu > frac_hbm:
         roof = {"bound": "alu", "achieved": gflops / 1e3, "peak": FP64_NOMINAL_GFLOPS / 1e3, "unit": "TFLOP/s",
@@ -278,7 +292,8 @@ def run_vk(args, cfg):
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
     roof["traffic"] = recorded_traffic(args.config, args.prec)
     roof["launch_avg_us"] = apply_avg_s * 1e6
-    roof["bytes_per_launch"] = st["apply_bytes"]
+    roof["bytes_per_launch"] = kt["apply_bytes"]
+    roof["launches_timed"] = int(kt["apply_launches"])
     cpu = None
     if not args.no_cpu_baseline:
         cpu = oracle_cpu_baseline(cfg)
@@ -286,10 +301,13 @@ def run_vk(args, cfg):
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "f64" else "f64 vectors, f32 patch inverses",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f64": "f64", "f64e": "f64 vectors; patch inverses as FP32 pairs (48-bit), FP32-pair products",
+                  "f32": "f64 vectors, f32 patch inverses"}[args.prec],
         "data": "synthetic",
         "config": {"workload": desc, "ndof": ndof, "levels": L, "k": k, "sweeps": sweeps, "rtol": rtol,
-                   "factor_prec": args.prec, "rhs": "N(0,1), numpy default_rng(seed)",
+                   "factor_prec": args.prec, "fgmres_loop": "host" if args.no_graph else "CUDA graph (WHILE node)",
+                   "rhs": "N(0,1), numpy default_rng(seed)",
                    "l2": "256 MiB buffer overwritten between timed solves (outside the per-solve events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "vcycle_dof_per_s": world * ndof * vcycles / total_s,
@@ -312,7 +330,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vk", choices=["vk", "reference"])
     ap.add_argument("--config", default="cfg2", choices=sorted(CONFIGS))
-    ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--prec", default="f64", choices=["f64", "f64e", "f32"],
+                    help="patch inverses: FP64, FP32-pair emulated FP64, or FP32")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="host-driven FGMRES loop instead of the whole-solve CUDA graph (for kernel profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "vk":

@@ -52,6 +52,9 @@ extern "C" {
 
 #define VK_PREC_F64 0  /* patch inverses stored and applied in FP64                                  */
 #define VK_PREC_F32 1  /* patch inverses stored in FP32, applied with FP32 products, FP64 vectors    */
+#define VK_PREC_F64E 2 /* patch inverses stored as FP32 (hi, lo) pairs (48 significant bits) and
+                          applied in FP32-pair arithmetic (exact product split + TwoSum accumulation)
+                          on the FP32 pipes; relative accuracy about 1e-13; FP64 vectors            */
 
 #define VK_CSR_A 0  /* level matrix script-A_l with Dirichlet identity rows and zeroed columns      */
 #define VK_CSR_P 1  /* prolongation from level l-1 to level l (ndof_l x ndof_{l-1})                 */

@@ -9,12 +9,14 @@
 namespace vk {
 namespace gpu {
 
-// Sliced ELLPACK, slice height 32 (SELL-32-sigma): rows are permuted (sorted by length inside windows
-// of 1024 rows) so the 32 rows of a slice have similar lengths; within a slice, entry k of lane t is
-// at sptr[slice] + 32*k + t, so one warp load of values or columns is 256 / 128 contiguous bytes.
-// Padding entries have val = 0 and a valid column.  rowof[pos] is the original row (-1 past the end).
+// Sliced ELLPACK with C = 32 / tpr rows per slice and tpr threads per row (SELL-C-sigma): rows are
+// permuted (sorted by length inside windows of 1024 rows) so the rows of a slice have similar
+// lengths; slice widths are padded to a multiple of tpr; entry k of row t of a slice is at
+// sptr[slice] + C*k + t, so one warp load of values or columns is 256 / 128 contiguous bytes.
+// Padding entries have val = 0 and a valid column.  rowof[C*slice + t] is the original row (-1 past
+// the end).  tpr is chosen per matrix so that a launch has enough warps to hide load latency.
 struct Sell {
-  int nrows = 0, nslices = 0;
+  int nrows = 0, nslices = 0, tpr = 1;
   const int64_t* sptr = nullptr;
   const int* swidth = nullptr;
   const int* col = nullptr;
@@ -33,17 +35,20 @@ struct Csr {
 // first); a work item is one warp.  slot_ptr / slot_dofs are in canonical patch order.
 struct Patches {
   int npatch = 0;
+  int ndof = 0;
   int64_t nslots = 0;
   const int* slot_ptr = nullptr;    // npatch + 1
   const int* slot_dofs = nullptr;   // nslots
   const int* work = nullptr;        // npatch: canonical patch id of work item w
   const int64_t* foff = nullptr;    // npatch: offset (elements) of patch p's packed inverse
-  const void* factors = nullptr;    // packed inverses: double (FP64) or float (FP32)
-  int prec = 0;                     // 0 = FP64, 1 = FP32
+  const void* factors = nullptr;    // packed inverses: double (FP64), float (FP32) or float2 (FP32 pair)
+  int prec = 0;                     // 0 = FP64, 1 = FP32, 2 = FP32 pair (emulated FP64)
   int nb_max = 0;                   // largest packed column-group count ceil(n/4) of the level
-  // DoF -> slots (ascending canonical patch order), for the atomic-free sum
+  // DoF -> slots (ascending canonical patch order), for the atomic-free sum.  The patch solves write
+  // the correction of canonical slot s to delta[slot_pos[s]], so the corrections of DoF i are the
+  // contiguous range delta[dof_ptr[i] .. dof_ptr[i+1]) in ascending patch order.
   const int* dof_ptr = nullptr;     // ndof + 1
-  const int* dof_slot = nullptr;    // nslots
+  const int* slot_pos = nullptr;    // nslots
   const double* weight = nullptr;   // per-DoF weight or nullptr (plain sum)
 };
 
@@ -51,6 +56,9 @@ struct Patches {
 int sell_residual(const Sell& A, const double* b, const double* x, double* y, cudaStream_t s);
 int csr_restrict(const Csr& R, const uint8_t* dir_coarse, const double* r, double* rc, cudaStream_t s);
 int csr_prolong_add(const Csr& P, const double* ec, double* x, cudaStream_t s);
+// rc = R r with rc = 0 at coarse Dirichlet DoFs; x += P ec  (SELL forms of R and P)
+int sell_restrict(const Sell& R, const uint8_t* dir_coarse, const double* r, double* rc, cudaStream_t s);
+int sell_prolong_add(const Sell& P, const double* ec, double* x, cudaStream_t s);
 // deterministic sums: partial sums over a fixed grid of kReduceBlocks blocks, then one block
 constexpr int kReduceBlocks = 256;
 int dot_partials(const double* x, const double* y, int n, double* partial, cudaStream_t s);
@@ -63,13 +71,15 @@ int copy(double* dst, const double* src, int64_t n, cudaStream_t s);
 int nonfinite_check(const double* x, int n, int* flag, cudaStream_t s);
 int axpy(double a, const double* x, double* y, int n, cudaStream_t s);   // y += a x
 int scale(double a, double* x, int n, cudaStream_t s);                   // x *= a
+int divide(double a, double* x, int n, cudaStream_t s);                  // x /= a
 
 // ---- patch kernels (kernels_patch.cu) -------------------------------------------------------------
 // Gather every patch matrix from the CSR matrix, invert it by Gauss-Jordan with partial pivoting,
 // and store it in the warp-packed layout.  status[0] receives 1 + the first singular patch id.
 int patch_factor(const Csr& A, const Patches& P, int prec, void* factors, int* status, cudaStream_t s);
-// delta[slot] = (A_i^{-1} r[idx_i]) for every patch (one launch for all patches of a level).
-int patch_apply(const Patches& P, const double* r, double* delta, cudaStream_t s);
+// delta[slot] = (A_i^{-1} r[idx_i]) for every patch (one launch for all patches of a level).  With
+// FP32-pair inverses r is first split into r2 (ndof float2) and delta holds FP32 pairs.
+int patch_apply(const Patches& P, const double* r, float2* r2, double* delta, cudaStream_t s);
 // Sum of the slot corrections into each DoF (+ Dirichlet identity), fused with the Chebyshev update:
 //   mode 0: z = M^{-1} r                   (out = z)
 //   mode 1: d = z / theta; x = d           (first step, zero initial guess)
@@ -104,6 +114,37 @@ int normalize(const double* w, const double* sq, double* v, double* hout, int n,
 // Givens update of FGMRES column j (single thread); see kernels_krylov.cu.
 int givens_update(double* H, int ldh, double* cs, double* sn, double* g, double* hist, int j, double rtol,
                    int* flag, cudaStream_t s);
+// ---- device-resident FGMRES (whole solve in one CUDA graph with a WHILE conditional node) ----------
+// State read and written by the kernels below; j = completed iterations (the loop index).
+struct FgState {
+  int j;          // iterations completed
+  int flags;      // bit 0: converged, bit 1: non-finite residual estimate
+  int maxit;
+  int pad;
+  double rtol;
+  double beta;    // ||b_hat||
+  double true_res;
+};
+// beta = sqrt(*sq); g = (beta, 0, ...); hist[0] = beta; j = 0; sets the loop condition.
+int fg_init(const double* sq, FgState* st, double* g, double* hist, int kmax, cudaGraphConditionalHandle cond,
+            cudaStream_t s);
+int fg_scale(double* v, const FgState* st, int n, cudaStream_t s);                       // v /= beta
+int fg_col_get(const double* V, int64_t ld, const FgState* st, double* out, int n, cudaStream_t s);  // out = V[j]
+int fg_col_put(const double* in, double* Z, int64_t ld, const FgState* st, int n, cudaStream_t s);   // Z[j] = in
+// one classical Gram-Schmidt pass against V[0..j]: mode 0 writes H[:, j], mode 1 adds to it
+int fg_cgs_pass(const double* V, int64_t ld, const FgState* st, double* w, int n, double* partial, double* H,
+                int ldh, double* t2, int kmax, int mode, cudaStream_t s);
+// V[j+1] = w / sqrt(*sq), H[j+1][j] = sqrt(*sq)
+int fg_normalize(const double* w, const double* sq, double* V, int64_t ld, const FgState* st, double* H, int ldh,
+                 int n, cudaStream_t s);
+// Givens update of column j, residual history, convergence flags, j += 1, loop condition.
+int fg_givens(double* H, int ldh, double* cs, double* sn, double* g, double* hist, FgState* st,
+              cudaGraphConditionalHandle cond, cudaStream_t s);
+// y = H[0:m,0:m]^{-1} g (back substitution, m = j) and x = Z y
+int fg_solution(const double* H, int ldh, const double* g, const double* Z, int64_t ld, const FgState* st,
+                double* y, double* x, int n, cudaStream_t s);
+int fg_finish(FgState* st, const double* sq, cudaStream_t s);                             // true_res = sqrt(*sq)
+
 // x = sum_i Z[i] y[i]
 int combine(const double* Z, int64_t ldz, int m, const double* y, double* x, int n, cudaStream_t s);
 // y = scale * x

@@ -64,30 +64,54 @@ __global__ void k_normalize(const double* w, const double* sq, double* v, double
   if (r < n) v[r] = nrm > 0.0 ? w[r] / nrm : w[r];
 }
 
-// Apply the previous rotations to column j of H (column-major, leading dimension ldh), build the new
-// rotation that zeroes H[j+1][j], update the rotated right-hand side g and the residual history.
+// Rotations of FGMRES column j (column-major H, leading dimension ldh): apply the previous rotations,
+// build the one that zeroes H[j+1][j], update g and the history.  The column and the rotations are
+// first loaded into shared memory by all threads; one thread then runs the sequential recurrence.
+// Returns (in thread 0) the new estimate |g[j+1]|.
+__device__ double givens_column(double* __restrict__ H, int ldh, double* __restrict__ cs, double* __restrict__ sn,
+                                double* __restrict__ g, double* __restrict__ hist, int j) {
+  extern __shared__ double sh[];
+  double* h = sh;                 // j + 2
+  double* c = sh + (j + 2);       // j
+  double* sv = c + j;             // j
+  double* col = H + int64_t(j) * ldh;
+  for (int i = threadIdx.x; i < j + 2; i += blockDim.x) h[i] = col[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    c[i] = cs[i];
+    sv[i] = sn[i];
+  }
+  __syncthreads();
+  double est = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < j; ++i) {
+      const double t = __dadd_rn(__dmul_rn(c[i], h[i]), __dmul_rn(sv[i], h[i + 1]));
+      h[i + 1] = __dadd_rn(__dmul_rn(-sv[i], h[i]), __dmul_rn(c[i], h[i + 1]));
+      h[i] = t;
+    }
+    const double den = hypot(h[j], h[j + 1]);
+    const double cj = h[j] / den, sj = h[j + 1] / den;
+    cs[j] = cj;
+    sn[j] = sj;
+    h[j] = den;
+    h[j + 1] = 0.0;
+    g[j + 1] = -sj * g[j];
+    g[j] = cj * g[j];
+    est = fabs(g[j + 1]);
+    hist[j + 1] = est;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < j + 2; i += blockDim.x) col[i] = h[i];
+  return est;
+}
+
 // flag[0] = 1 once |g[j+1]| <= rtol * hist[0]; flag[1] = 1 if the estimate is not finite.
 __global__ void k_givens(double* __restrict__ H, int ldh, double* __restrict__ cs, double* __restrict__ sn,
                          double* __restrict__ g, double* __restrict__ hist, int j, double rtol, int* flag) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double* h = H + int64_t(j) * ldh;
-  for (int i = 0; i < j; ++i) {
-    const double t = __dadd_rn(__dmul_rn(cs[i], h[i]), __dmul_rn(sn[i], h[i + 1]));
-    h[i + 1] = __dadd_rn(__dmul_rn(-sn[i], h[i]), __dmul_rn(cs[i], h[i + 1]));
-    h[i] = t;
+  const double est = givens_column(H, ldh, cs, sn, g, hist, j);
+  if (threadIdx.x == 0) {
+    flag[0] = est <= rtol * hist[0] ? 1 : 0;
+    flag[1] = isfinite(est) ? 0 : 1;
   }
-  const double den = hypot(h[j], h[j + 1]);
-  const double c = h[j] / den, s = h[j + 1] / den;
-  cs[j] = c;
-  sn[j] = s;
-  h[j] = den;
-  h[j + 1] = 0.0;
-  g[j + 1] = -s * g[j];
-  g[j] = c * g[j];
-  const double est = fabs(g[j + 1]);
-  hist[j + 1] = est;
-  flag[0] = est <= rtol * hist[0] ? 1 : 0;
-  flag[1] = isfinite(est) ? 0 : 1;
 }
 
 // x[r] = sum_i y[i] Z[i][r], summed in increasing i from zero
@@ -100,15 +124,204 @@ __global__ void k_combine(const double* __restrict__ Z, int64_t ldz, int m, cons
   x[r] = s;
 }
 
-__global__ void k_scale_copy(const double* __restrict__ x, const double* __restrict__ sq, double* __restrict__ y,
-                             int n) {
+// may run in place (y == x)
+__global__ void k_scale_copy(const double* x, const double* __restrict__ sq, double* y, int n) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const double nrm = sqrt(*sq);
   y[r] = x[r] / nrm;
 }
 
+// ---------------- device-resident FGMRES kernels (iteration index read from FgState) -------------
+__global__ void k_fg_init(const double* __restrict__ sq, FgState* st, double* __restrict__ g,
+                          double* __restrict__ hist, int kmax, cudaGraphConditionalHandle cond) {
+  const double beta = sqrt(*sq);
+  for (int i = threadIdx.x; i <= kmax; i += blockDim.x) g[i] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int flags = 0;
+    if (!isfinite(beta)) flags |= 2;
+    else if (beta == 0.0) flags |= 1;
+    st->beta = beta;
+    st->j = 0;
+    st->flags = flags;
+    st->true_res = 0.0;
+    g[0] = beta;
+    hist[0] = beta;
+    cudaGraphSetConditional(cond, (flags == 0 && st->maxit > 0) ? 1u : 0u);
+  }
+}
+
+__global__ void k_fg_scale(double* v, const FgState* __restrict__ st, int n) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const double beta = st->beta;
+  if (r < n && beta > 0.0 && isfinite(beta)) v[r] = v[r] / beta;
+}
+
+__global__ void k_fg_col_get(const double* __restrict__ V, int64_t ld, const FgState* __restrict__ st,
+                             double* __restrict__ out, int n) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) out[r] = V[ld * st->j + r];
+}
+
+__global__ void k_fg_col_put(const double* __restrict__ in, double* __restrict__ Z, int64_t ld,
+                             const FgState* __restrict__ st, int n) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) Z[ld * st->j + r] = in[r];
+}
+
+// Fixed grid of kReduceBlocks blocks; block b forms the partial dots of rows {b*kT + t + k*kReduceBlocks*kT}
+// for every basis vector i <= j (same partition and order as k_multi_dot).
+__global__ void __launch_bounds__(kT) k_fg_mdot(const double* __restrict__ V, int64_t ld,
+                                                const FgState* __restrict__ st, const double* __restrict__ w,
+                                                int n, double* __restrict__ partial) {
+  const int j = st->j;
+  for (int i = 0; i <= j; ++i) {
+    const double* v = V + ld * i;
+    double s = 0.0;
+    for (int r = blockIdx.x * kT + threadIdx.x; r < n; r += kReduceBlocks * kT) s = fma(v[r], w[r], s);
+    s = block_sum<kT>(s);
+    if (threadIdx.x == 0) partial[int64_t(i) * kReduceBlocks + blockIdx.x] = s;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kT) k_fg_mfin(const double* __restrict__ partial, const FgState* __restrict__ st,
+                                                double* __restrict__ H, int ldh, double* __restrict__ t2, int mode) {
+  const int i = blockIdx.x, j = st->j;
+  if (i > j) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < kReduceBlocks; b += kT) s += partial[int64_t(i) * kReduceBlocks + b];
+  s = block_sum<kT>(s);
+  if (threadIdx.x == 0) {
+    double* col = H + int64_t(j) * ldh;
+    if (mode == 0) {
+      col[i] = s;
+    } else {
+      t2[i] = s;
+      col[i] += s;
+    }
+  }
+}
+
+__global__ void k_fg_maxpy(const double* __restrict__ V, int64_t ld, const FgState* __restrict__ st,
+                           const double* __restrict__ H, int ldh, const double* __restrict__ t2, int mode,
+                           double* __restrict__ w, int n) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int j = st->j;
+  const double* h = mode == 0 ? H + int64_t(j) * ldh : t2;
+  double s = 0.0;
+  for (int i = 0; i <= j; ++i) s = fma(V[ld * i + r], h[i], s);
+  w[r] -= s;
+}
+
+__global__ void k_fg_normalize(const double* __restrict__ w, const double* __restrict__ sq, double* __restrict__ V,
+                               int64_t ld, const FgState* __restrict__ st, double* __restrict__ H, int ldh, int n) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = st->j;
+  const double nrm = sqrt(*sq);
+  if (r == 0) H[int64_t(j) * ldh + j + 1] = nrm;
+  if (r < n) V[ld * (j + 1) + r] = nrm > 0.0 ? w[r] / nrm : w[r];
+}
+
+__global__ void k_fg_givens(double* __restrict__ H, int ldh, double* __restrict__ cs, double* __restrict__ sn,
+                            double* __restrict__ g, double* __restrict__ hist, FgState* st,
+                            cudaGraphConditionalHandle cond) {
+  const int j = st->j;
+  const double est = givens_column(H, ldh, cs, sn, g, hist, j);
+  if (threadIdx.x == 0) {
+    int flags = 0;
+    if (!isfinite(est)) flags |= 2;
+    else if (est <= st->rtol * hist[0]) flags |= 1;
+    st->flags = flags;
+    st->j = j + 1;
+    cudaGraphSetConditional(cond, (flags == 0 && j + 1 < st->maxit) ? 1u : 0u);
+  }
+}
+
+// Back substitution with one warp: y[i] = (g[i] - sum_{k>i} H[i][k] y[k]) / H[i][i].
+__global__ void k_fg_backsolve(const double* __restrict__ H, int ldh, const double* __restrict__ g,
+                               const FgState* __restrict__ st, double* __restrict__ y) {
+  extern __shared__ double ys[];
+  const int m = st->j, lane = threadIdx.x;
+  for (int i = m - 1; i >= 0; --i) {
+    double s = 0.0;
+    for (int k = i + 1 + lane; k < m; k += 32) s = fma(H[int64_t(k) * ldh + i], ys[k], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) ys[i] = (g[i] - s) / H[int64_t(i) * ldh + i];
+    __syncwarp();
+  }
+  for (int i = lane; i < m; i += 32) y[i] = ys[i];
+}
+
+__global__ void k_fg_combine(const double* __restrict__ Z, int64_t ldz, const FgState* __restrict__ st,
+                             const double* __restrict__ y, double* __restrict__ x, int n) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int m = st->j;
+  double s = 0.0;
+  for (int i = 0; i < m; ++i) s = __dadd_rn(s, __dmul_rn(y[i], Z[ldz * i + r]));
+  x[r] = s;
+}
+
+__global__ void k_fg_finish(FgState* st, const double* __restrict__ sq) { st->true_res = sqrt(*sq); }
+
 }  // namespace
+
+int fg_init(const double* sq, FgState* st, double* g, double* hist, int kmax, cudaGraphConditionalHandle cond,
+            cudaStream_t s) {
+  k_fg_init<<<1, kT, 0, s>>>(sq, st, g, hist, kmax, cond);
+  return 1;
+}
+
+int fg_scale(double* v, const FgState* st, int n, cudaStream_t s) {
+  k_fg_scale<<<(n + kT - 1) / kT, kT, 0, s>>>(v, st, n);
+  return 1;
+}
+
+int fg_col_get(const double* V, int64_t ld, const FgState* st, double* out, int n, cudaStream_t s) {
+  k_fg_col_get<<<(n + kT - 1) / kT, kT, 0, s>>>(V, ld, st, out, n);
+  return 1;
+}
+
+int fg_col_put(const double* in, double* Z, int64_t ld, const FgState* st, int n, cudaStream_t s) {
+  k_fg_col_put<<<(n + kT - 1) / kT, kT, 0, s>>>(in, Z, ld, st, n);
+  return 1;
+}
+
+int fg_cgs_pass(const double* V, int64_t ld, const FgState* st, double* w, int n, double* partial, double* H,
+                int ldh, double* t2, int kmax, int mode, cudaStream_t s) {
+  k_fg_mdot<<<kReduceBlocks, kT, 0, s>>>(V, ld, st, w, n, partial);
+  k_fg_mfin<<<kmax, kT, 0, s>>>(partial, st, H, ldh, t2, mode);
+  k_fg_maxpy<<<(n + kT - 1) / kT, kT, 0, s>>>(V, ld, st, H, ldh, t2, mode, w, n);
+  return 3;
+}
+
+int fg_normalize(const double* w, const double* sq, double* V, int64_t ld, const FgState* st, double* H, int ldh,
+                 int n, cudaStream_t s) {
+  k_fg_normalize<<<(n + kT - 1) / kT, kT, 0, s>>>(w, sq, V, ld, st, H, ldh, n);
+  return 1;
+}
+
+int fg_givens(double* H, int ldh, double* cs, double* sn, double* g, double* hist, FgState* st,
+              cudaGraphConditionalHandle cond, cudaStream_t s) {
+  // shared memory for the largest column: 3 * kmax + 2 doubles (ldh = kmax + 1)
+  k_fg_givens<<<1, 128, (3 * ldh + 2) * sizeof(double), s>>>(H, ldh, cs, sn, g, hist, st, cond);
+  return 1;
+}
+
+int fg_solution(const double* H, int ldh, const double* g, const double* Z, int64_t ld, const FgState* st,
+                double* y, double* x, int n, cudaStream_t s) {
+  k_fg_backsolve<<<1, 32, ldh * sizeof(double), s>>>(H, ldh, g, st, y);
+  k_fg_combine<<<(n + kT - 1) / kT, kT, 0, s>>>(Z, ld, st, y, x, n);
+  return 2;
+}
+
+int fg_finish(FgState* st, const double* sq, cudaStream_t s) {
+  k_fg_finish<<<1, 1, 0, s>>>(st, sq);
+  return 1;
+}
 
 int multi_dot_partials(const double* V, int64_t ldv, int nvec, const double* w, int n, double* partial,
                         cudaStream_t s) {
@@ -135,7 +348,7 @@ int normalize(const double* w, const double* sq, double* v, double* hout, int n,
 
 int givens_update(double* H, int ldh, double* cs, double* sn, double* g, double* hist, int j, double rtol,
                    int* flag, cudaStream_t s) {
-  k_givens<<<1, 32, 0, s>>>(H, ldh, cs, sn, g, hist, j, rtol, flag);
+  k_givens<<<1, 128, (3 * j + 2) * sizeof(double), s>>>(H, ldh, cs, sn, g, hist, j, rtol, flag);
   return 1;
 }
 

@@ -12,6 +12,7 @@
 // lane l is stored at (a * NB + b) * 32 + l, so each warp load is 32 consecutive values (256 bytes in
 // FP64), and padding (rows/columns >= n, stored as zero) is at most 7 rows and 3 columns.
 #include <cfloat>
+#include <type_traits>
 
 #include "gpu.h"
 
@@ -21,6 +22,18 @@ namespace gpu {
 namespace {
 
 constexpr int kFactorThreads = 128;
+
+template <typename FT>
+__device__ __forceinline__ FT store_entry(double v) {
+  return FT(v);
+}
+// FP32 pair: hi = fl32(v), lo = fl32(v - hi); hi + lo carries 48 significant bits of v
+template <>
+__device__ __forceinline__ float2 store_entry<float2>(double v) {
+  const float hi = __double2float_rn(v);
+  const float lo = __double2float_rn(v - double(hi));
+  return make_float2(hi, lo);
+}
 
 template <typename FT>
 __global__ void __launch_bounds__(kFactorThreads) k_patch_factor(Csr A, const int* __restrict__ slot_ptr,
@@ -119,7 +132,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_patch_factor(Csr A, const in
     const int lane = e & 31, ab = e >> 5;
     const int a = ab / NB, b = ab - a * NB;
     const int row = (lane & 7) + 8 * a, col = (lane >> 3) + 4 * b;
-    out[e] = (row < n && col < n) ? FT(M[row * n + col]) : FT(0);
+    out[e] = store_entry<FT>((row < n && col < n) ? M[row * n + col] : 0.0);
   }
 }
 
@@ -137,7 +150,7 @@ struct Compute<float> {
 template <int NB, typename FT>
 __device__ __forceinline__ void apply_one(int n, int s0, const int* __restrict__ dofs,
                                           const FT* __restrict__ Fp, const double* __restrict__ r,
-                                          double* __restrict__ delta, int lane) {
+                                          const int* __restrict__ pos, double* __restrict__ delta, int lane) {
   using T = typename Compute<FT>::T;
   constexpr int NA = (NB + 1) / 2;
   const int rr = lane & 7, cc = lane >> 3;
@@ -164,19 +177,88 @@ __device__ __forceinline__ void apply_one(int n, int s0, const int* __restrict__
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
       const int row = rr + 8 * a;
-      if (row < n) delta[s0 + row] = double(acc[a]);
+      if (row < n) delta[__ldg(pos + s0 + row)] = double(acc[a]);
+    }
+  }
+}
+
+// FP32-pair (emulated FP64) apply.  The inverse entry a = ah + al and the local residual
+// r = rh + rl (split once per DoF by k_split_pairs) are FP32 pairs; each product is
+// p = fl(ah*rh), e = (ah*rh - p) + ah*rl + al*rh (first term exact by FMA); p is accumulated with
+// TwoSum into (hi, err) and the low-order terms into lo, so row sums carry ~48 bits.  The cross-lane
+// reduction stays in pair arithmetic and the corrections are written as pairs: no FP64 instruction
+// runs per patch (FP64 is 1/64 of the FP32 rate on this part).  Every operation is an explicitly
+// rounded intrinsic, so no contraction or reassociation can break the error-free transformations.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float p) {
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
+template <int NB>
+__device__ __forceinline__ void apply_one_pair(int n, int s0, const int* __restrict__ dofs,
+                                               const float2* __restrict__ Fp, const float2* __restrict__ r2,
+                                               const int* __restrict__ pos, float2* __restrict__ delta, int lane) {
+  constexpr int NA = (NB + 1) / 2;
+  const int rr = lane & 7, cc = lane >> 3;
+  float rh[NB], rl[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = cc + 4 * b;
+    const float2 v = j < n ? __ldg(r2 + __ldg(dofs + j)) : make_float2(0.f, 0.f);
+    rh[b] = v.x;
+    rl[b] = v.y;
+  }
+  float ah[NA], al[NA];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    float hi = 0.f, lo = 0.f;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const float2 f = __ldg(Fp + (a * NB + b) * 32 + lane);
+      const float p = __fmul_rn(f.x, rh[b]);
+      float e = __fmaf_rn(f.x, rh[b], -p);
+      e = __fmaf_rn(f.x, rl[b], e);
+      e = __fmaf_rn(f.y, rh[b], e);
+      two_sum_acc(hi, lo, p);
+      lo = __fadd_rn(lo, e);
+    }
+    ah[a] = hi;
+    al[a] = lo;
+  }
+#pragma unroll
+  for (int a = 0; a < NA; ++a)
+#pragma unroll
+    for (int o = 8; o <= 16; o <<= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, ah[a], o);
+      const float ol = __shfl_xor_sync(0xffffffffu, al[a], o);
+      two_sum_acc(ah[a], al[a], oh);
+      al[a] = __fadd_rn(al[a], ol);
+    }
+  if (cc == 0) {
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      const int row = rr + 8 * a;
+      if (row < n) delta[__ldg(pos + s0 + row)] = make_float2(ah[a], al[a]);
     }
   }
 }
 
 template <int NB, int NBMAX, typename FT>
 __device__ __forceinline__ void apply_dispatch(int nb, int n, int s0, const int* dofs, const FT* Fp,
-                                               const double* r, double* delta, int lane) {
+                                               const double* r, const float2* r2, const int* pos, double* delta,
+                                               int lane) {
   if constexpr (NB <= NBMAX) {
-    if (nb == NB)
-      apply_one<NB, FT>(n, s0, dofs, Fp, r, delta, lane);
-    else
-      apply_dispatch<NB + 1, NBMAX, FT>(nb, n, s0, dofs, Fp, r, delta, lane);
+    if (nb == NB) {
+      if constexpr (std::is_same<FT, float2>::value)
+        apply_one_pair<NB>(n, s0, dofs, Fp, r2, pos, reinterpret_cast<float2*>(delta), lane);
+      else
+        apply_one<NB, FT>(n, s0, dofs, Fp, r, pos, delta, lane);
+    } else {
+      apply_dispatch<NB + 1, NBMAX, FT>(nb, n, s0, dofs, Fp, r, r2, pos, delta, lane);
+    }
   }
 }
 
@@ -186,17 +268,27 @@ __global__ void __launch_bounds__(256) k_patch_apply(int npatch, const int* __re
                                                      const int* __restrict__ slot_dofs,
                                                      const int64_t* __restrict__ foff,
                                                      const FT* __restrict__ F, const double* __restrict__ r,
+                                                     const float2* __restrict__ r2, const int* __restrict__ pos,
                                                      double* __restrict__ delta) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= npatch) return;
   const int p = work[w];
   const int s0 = slot_ptr[p], n = slot_ptr[p + 1] - s0;
-  apply_dispatch<1, NBMAX, FT>((n + 3) >> 2, n, s0, slot_dofs + s0, F + foff[p], r, delta, lane);
+  apply_dispatch<1, NBMAX, FT>((n + 3) >> 2, n, s0, slot_dofs + s0, F + foff[p], r, r2, pos, delta, lane);
 }
 
+// r = rh + rl with rh = fl32(r), rl = fl32(r - rh): the FP32-pair form of a residual, once per DoF.
+__global__ void k_split_pairs(const double* __restrict__ r, float2* __restrict__ r2, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = r[i];
+  const float h = __double2float_rn(v);
+  r2[i] = make_float2(h, __double2float_rn(v - double(h)));
+}
+
+template <bool kPairs>
 __global__ void __launch_bounds__(256) k_vanka_scatter(int ndof, const int* __restrict__ dptr,
-                                                       const int* __restrict__ dslot,
                                                        const double* __restrict__ weight,
                                                        const uint8_t* __restrict__ dir,
                                                        const double* __restrict__ r,
@@ -209,14 +301,25 @@ __global__ void __launch_bounds__(256) k_vanka_scatter(int ndof, const int* __re
   double z;
   if (dir[i]) {
     z = r[i];
+  } else if (kPairs) {
+    // corrections are FP32 pairs: sum them in pair arithmetic, convert once
+    const float2* d2 = reinterpret_cast<const float2*>(delta);
+    float hi = 0.f, lo = 0.f;
+    for (int e = dptr[i]; e < dptr[i + 1]; ++e) {
+      const float2 v = d2[e];
+      two_sum_acc(hi, lo, v.x);
+      lo = __fadd_rn(lo, v.y);
+    }
+    z = double(hi) + double(lo);
+    if (weight) z *= weight[i];
   } else {
     z = 0.0;
     const int e0 = dptr[i], e1 = dptr[i + 1];
     if (weight) {
       const double wi = weight[i];
-      for (int e = e0; e < e1; ++e) z = __dadd_rn(z, __dmul_rn(delta[dslot[e]], wi));
+      for (int e = e0; e < e1; ++e) z = __dadd_rn(z, __dmul_rn(delta[e], wi));
     } else {
-      for (int e = e0; e < e1; ++e) z += delta[dslot[e]];
+      for (int e = e0; e < e1; ++e) z += delta[e];
     }
   }
   switch (mode) {
@@ -245,19 +348,19 @@ __global__ void __launch_bounds__(256) k_vanka_scatter(int ndof, const int* __re
 }
 
 template <int NBMAX, typename FT>
-int launch_apply(const Patches& P, const double* r, double* delta, cudaStream_t s) {
+int launch_apply(const Patches& P, const double* r, const float2* r2, double* delta, cudaStream_t s) {
   const int threads = 256, warps = threads / 32;
   const int blocks = (P.npatch + warps - 1) / warps;
   k_patch_apply<NBMAX, FT><<<blocks, threads, 0, s>>>(P.npatch, P.work, P.slot_ptr, P.slot_dofs, P.foff,
-                                                      static_cast<const FT*>(P.factors), r, delta);
+                                                      static_cast<const FT*>(P.factors), r, r2, P.slot_pos, delta);
   return 1;
 }
 
 template <typename FT>
-int apply_prec(const Patches& P, const double* r, double* delta, cudaStream_t s) {
-  if (P.nb_max <= 10) return launch_apply<10, FT>(P, r, delta, s);
-  if (P.nb_max <= 19) return launch_apply<19, FT>(P, r, delta, s);
-  return launch_apply<32, FT>(P, r, delta, s);
+int apply_prec(const Patches& P, const double* r, const float2* r2, double* delta, cudaStream_t s) {
+  if (P.nb_max <= 10) return launch_apply<10, FT>(P, r, r2, delta, s);
+  if (P.nb_max <= 19) return launch_apply<19, FT>(P, r, r2, delta, s);
+  return launch_apply<32, FT>(P, r, r2, delta, s);
 }
 
 }  // namespace
@@ -271,24 +374,37 @@ int patch_factor(const Csr& A, const Patches& P, int prec, void* factors, int* s
     cudaFuncSetAttribute(k_patch_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     k_patch_factor<double><<<P.npatch, kFactorThreads, smem, s>>>(A, P.slot_ptr, P.slot_dofs, P.foff,
                                                                    static_cast<double*>(factors), status);
-  } else {
+  } else if (prec == 1) {
     cudaFuncSetAttribute(k_patch_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     k_patch_factor<float><<<P.npatch, kFactorThreads, smem, s>>>(A, P.slot_ptr, P.slot_dofs, P.foff,
                                                                   static_cast<float*>(factors), status);
+  } else {
+    cudaFuncSetAttribute(k_patch_factor<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    k_patch_factor<float2><<<P.npatch, kFactorThreads, smem, s>>>(A, P.slot_ptr, P.slot_dofs, P.foff,
+                                                                   static_cast<float2*>(factors), status);
   }
   return 1;
 }
 
-int patch_apply(const Patches& P, const double* r, double* delta, cudaStream_t s) {
+int patch_apply(const Patches& P, const double* r, float2* r2, double* delta, cudaStream_t s) {
   if (P.npatch == 0) return 0;
-  return P.prec == 0 ? apply_prec<double>(P, r, delta, s) : apply_prec<float>(P, r, delta, s);
+  if (P.prec == 0) return apply_prec<double>(P, r, nullptr, delta, s);
+  if (P.prec == 1) return apply_prec<float>(P, r, nullptr, delta, s);
+  // FP32-pair inverses: split the residual once per DoF first
+  const int n = P.ndof;
+  k_split_pairs<<<(n + 255) / 256, 256, 0, s>>>(r, r2, n);
+  return 1 + apply_prec<float2>(P, r, r2, delta, s);
 }
 
 int vanka_scatter(const Patches& P, int ndof, const uint8_t* dir, const double* r, const double* delta,
                    int mode, double theta, double c1, double c2, double* out_z, double* d, double* x,
                    cudaStream_t s) {
-  k_vanka_scatter<<<(ndof + 255) / 256, 256, 0, s>>>(ndof, P.dof_ptr, P.dof_slot, P.weight, dir, r, delta,
-                                                     mode, theta, c1, c2, out_z, d, x);
+  if (P.prec == 2)
+    k_vanka_scatter<true><<<(ndof + 255) / 256, 256, 0, s>>>(ndof, P.dof_ptr, P.weight, dir, r, delta, mode,
+                                                             theta, c1, c2, out_z, d, x);
+  else
+    k_vanka_scatter<false><<<(ndof + 255) / 256, 256, 0, s>>>(ndof, P.dof_ptr, P.weight, dir, r, delta, mode,
+                                                              theta, c1, c2, out_z, d, x);
   return 1;
 }
 

@@ -14,35 +14,75 @@ constexpr int kThreads = 256;
 
 inline int blocks_for(int64_t n, int t = kThreads) { return int((n + t - 1) / t); }
 
-// One thread per row slot of a 32-row slice: lane t of slice s owns permuted row 32 s + t.
-__global__ void __launch_bounds__(kThreads) k_sell_residual(int nslices, const int64_t* __restrict__ sptr,
-                                                            const int* __restrict__ sw,
-                                                            const int* __restrict__ col,
-                                                            const double* __restrict__ val,
-                                                            const int* __restrict__ rowof,
-                                                            const double* __restrict__ b,
-                                                            const double* __restrict__ x,
-                                                            double* __restrict__ y) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = t >> 5, lane = t & 31;
-  if (s >= nslices) return;
-  const int row = rowof[t];
-  const int w = sw[s];
-  const int64_t base = sptr[s] + lane;
+// SELL-C with T = 32 / C threads per row: warp w owns slice w (C rows); lane l = t + C q works on row
+// t of the slice and on the entries k = T m + q of that row.  Entry k of row t is stored at
+// sptr[w] + C k + t, so for each m the warp reads the 32 consecutive entries sptr[w] + 32 m + l.
+// Loads are issued 8 steps ahead of the FMAs (the kernel is latency-bound otherwise); the T partial
+// sums of a row are combined by a fixed xor tree.
+//   kMode 0: y = b - A x          1: y = A x
+//   kMode 2: y = b + A x          3: y = mask ? 0 : A x   (mask = Dirichlet flags of the output)
+// (b and y may be the same vector: each row reads b[row] before writing y[row].)
+template <int kMode, int T>
+__global__ void __launch_bounds__(kThreads) k_sell(int nslices, const int64_t* __restrict__ sptr,
+                                                   const int* __restrict__ sw, const int* __restrict__ col,
+                                                   const double* __restrict__ val, const int* __restrict__ rowof,
+                                                   const double* b, const uint8_t* __restrict__ mask,
+                                                   const double* __restrict__ x, double* y) {
+  constexpr int C = 32 / T;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nslices) return;
+  const int t = lane % C;
+  const int row = rowof[warp * C + t];
+  const int steps = sw[warp] / T;
+  const int64_t base = sptr[warp] + lane;
+  const int* cp = col + base;
+  const double* vp = val + base;
   double sum = 0.0;
-  int k = 0;
-  for (; k + 4 <= w; k += 4) {
-    const int c0 = __ldg(col + base + 32 * (k + 0)), c1 = __ldg(col + base + 32 * (k + 1));
-    const int c2 = __ldg(col + base + 32 * (k + 2)), c3 = __ldg(col + base + 32 * (k + 3));
-    const double v0 = __ldg(val + base + 32 * (k + 0)), v1 = __ldg(val + base + 32 * (k + 1));
-    const double v2 = __ldg(val + base + 32 * (k + 2)), v3 = __ldg(val + base + 32 * (k + 3));
-    sum = fma(v0, x[c0], sum);
-    sum = fma(v1, x[c1], sum);
-    sum = fma(v2, x[c2], sum);
-    sum = fma(v3, x[c3], sum);
+  int m = 0;
+  constexpr int U = 8;
+  for (; m + U <= steps; m += U) {
+    int c[U];
+    double v[U], xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      c[u] = __ldg(cp + 32 * (m + u));
+      v[u] = __ldg(vp + 32 * (m + u));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = x[c[u]];
+#pragma unroll
+    for (int u = 0; u < U; ++u) sum = fma(v[u], xv[u], sum);
   }
-  for (; k < w; ++k) sum = fma(__ldg(val + base + 32 * k), x[__ldg(col + base + 32 * k)], sum);
-  if (row >= 0) y[row] = b ? b[row] - sum : sum;
+  for (; m < steps; ++m) sum = fma(__ldg(vp + 32 * m), x[__ldg(cp + 32 * m)], sum);
+#pragma unroll
+  for (int o = C; o < 32; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane >= C || row < 0) return;
+  if (kMode == 0) y[row] = b[row] - sum;
+  if (kMode == 1) y[row] = sum;
+  if (kMode == 2) y[row] = b[row] + sum;
+  if (kMode == 3) y[row] = mask[row] ? 0.0 : sum;
+}
+
+template <int kMode>
+int launch_sell(const Sell& A, const double* b, const uint8_t* mask, const double* x, double* y, cudaStream_t s) {
+  if (A.nslices == 0) return 0;
+  const int g = blocks_for(int64_t(A.nslices) * 32);
+  switch (A.tpr) {
+    case 1:
+      k_sell<kMode, 1><<<g, kThreads, 0, s>>>(A.nslices, A.sptr, A.swidth, A.col, A.val, A.rowof, b, mask, x, y);
+      break;
+    case 2:
+      k_sell<kMode, 2><<<g, kThreads, 0, s>>>(A.nslices, A.sptr, A.swidth, A.col, A.val, A.rowof, b, mask, x, y);
+      break;
+    case 4:
+      k_sell<kMode, 4><<<g, kThreads, 0, s>>>(A.nslices, A.sptr, A.swidth, A.col, A.val, A.rowof, b, mask, x, y);
+      break;
+    default:
+      k_sell<kMode, 8><<<g, kThreads, 0, s>>>(A.nslices, A.sptr, A.swidth, A.col, A.val, A.rowof, b, mask, x, y);
+      break;
+  }
+  return 1;
 }
 
 __global__ void k_csr_restrict(int nrows, const int* __restrict__ ptr, const int* __restrict__ col,
@@ -136,7 +176,18 @@ __global__ void k_scale(double a, double* __restrict__ x, int n) {
   if (i < n) x[i] = x[i] * a;
 }
 
+__global__ void k_divide(double a, double* __restrict__ x, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = x[i] / a;
+}
+
 }  // namespace
+
+int divide(double a, double* x, int n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_divide<<<blocks_for(n), kThreads, 0, s>>>(a, x, n);
+  return 1;
+}
 
 int axpy(double a, const double* x, double* y, int n, cudaStream_t s) {
   if (n <= 0) return 0;
@@ -151,10 +202,15 @@ int scale(double a, double* x, int n, cudaStream_t s) {
 }
 
 int sell_residual(const Sell& A, const double* b, const double* x, double* y, cudaStream_t s) {
-  if (A.nslices == 0) return 0;
-  k_sell_residual<<<blocks_for(int64_t(A.nslices) * 32), kThreads, 0, s>>>(A.nslices, A.sptr, A.swidth, A.col,
-                                                                          A.val, A.rowof, b, x, y);
-  return 1;
+  return b ? launch_sell<0>(A, b, nullptr, x, y, s) : launch_sell<1>(A, nullptr, nullptr, x, y, s);
+}
+
+int sell_restrict(const Sell& R, const uint8_t* dir_coarse, const double* r, double* rc, cudaStream_t s) {
+  return launch_sell<3>(R, nullptr, dir_coarse, r, rc, s);
+}
+
+int sell_prolong_add(const Sell& P, const double* ec, double* x, cudaStream_t s) {
+  return launch_sell<2>(P, x, nullptr, ec, x, s);
 }
 
 int csr_restrict(const Csr& R, const uint8_t* dir_coarse, const double* r, double* rc, cudaStream_t s) {

@@ -105,10 +105,19 @@ struct HostSell {
   std::vector<double> val;
 };
 
-// SELL-32: permute rows by decreasing length inside windows of 1024 rows, cut into slices of 32.
-HostSell build_sell(const vk::HostCsr& A) {
+// Threads per row for a SELL matrix: the smallest of 1, 2, 4, 8 that gives at least 48 warps per SM
+// (GB300: 152 SMs), so load latency is hidden without an over-long per-thread dependency chain.
+int sell_tpr(int nrows) {
+  const int64_t want = 152LL * 48 * 32;
+  for (int t = 1; t < 8; t *= 2)
+    if (int64_t(nrows) * t >= want) return t;
+  return 8;
+}
+
+// SELL-C: permute rows by decreasing length inside windows of 1024 rows, cut into slices of C rows.
+HostSell build_sell(const vk::HostCsr& A, int tpr) {
   HostSell S;
-  const int n = A.nrows, W = 1024;
+  const int n = A.nrows, W = 1024, C = 32 / tpr;
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   for (int w0 = 0; w0 < n; w0 += W) {
@@ -117,28 +126,29 @@ HostSell build_sell(const vk::HostCsr& A) {
       return (A.ptr[a + 1] - A.ptr[a]) > (A.ptr[b + 1] - A.ptr[b]);
     });
   }
-  const int ns = (n + 31) / 32;
-  S.rowof.assign(size_t(ns) * 32, -1);
+  const int ns = (n + C - 1) / C;
+  S.rowof.assign(size_t(ns) * C, -1);
   for (int i = 0; i < n; ++i) S.rowof[i] = order[i];
   S.sptr.assign(ns + 1, 0);
   S.sw.assign(ns, 0);
   for (int s = 0; s < ns; ++s) {
     int w = 0;
-    for (int t = 0; t < 32; ++t) {
-      const int row = S.rowof[s * 32 + t];
+    for (int t = 0; t < C; ++t) {
+      const int row = S.rowof[size_t(s) * C + t];
       if (row >= 0) w = std::max(w, A.ptr[row + 1] - A.ptr[row]);
     }
+    w = (w + tpr - 1) / tpr * tpr;
     S.sw[s] = w;
-    S.sptr[s + 1] = S.sptr[s] + 32LL * w;
+    S.sptr[s + 1] = S.sptr[s] + int64_t(C) * w;
   }
   S.col.assign(S.sptr[ns], 0);
   S.val.assign(S.sptr[ns], 0.0);
   for (int s = 0; s < ns; ++s)
-    for (int t = 0; t < 32; ++t) {
-      const int row = S.rowof[s * 32 + t];
+    for (int t = 0; t < C; ++t) {
+      const int row = S.rowof[size_t(s) * C + t];
       const int len = row >= 0 ? A.ptr[row + 1] - A.ptr[row] : 0;
       for (int k = 0; k < S.sw[s]; ++k) {
-        const int64_t pos = S.sptr[s] + 32LL * k + t;
+        const int64_t pos = S.sptr[s] + int64_t(C) * k + t;
         if (k < len) {
           S.col[pos] = A.col[A.ptr[row] + k];
           S.val[pos] = A.val[A.ptr[row] + k];
@@ -156,7 +166,7 @@ struct HostPatchPlan {
   std::vector<int64_t> foff;    // canonical id -> packed offset
   int64_t ftotal = 0;
   int nb_max = 0;
-  std::vector<int> dof_ptr, dof_slot;
+  std::vector<int> dof_ptr, slot_pos;
   std::vector<double> weight;
 };
 
@@ -178,9 +188,9 @@ HostPatchPlan plan_patches(const vk::HostLevel& L, int weights) {
   P.dof_ptr.assign(L.ndof + 1, 0);
   for (int64_t s = 0; s < nslots; ++s) P.dof_ptr[L.patch_dofs[s] + 1]++;
   for (int i = 0; i < L.ndof; ++i) P.dof_ptr[i + 1] += P.dof_ptr[i];
-  P.dof_slot.assign(nslots, 0);
+  P.slot_pos.assign(nslots, 0);
   std::vector<int> fill(P.dof_ptr.begin(), P.dof_ptr.end() - 1);
-  for (int64_t s = 0; s < nslots; ++s) P.dof_slot[fill[L.patch_dofs[s]]++] = int(s);
+  for (int64_t s = 0; s < nslots; ++s) P.slot_pos[s] = fill[L.patch_dofs[s]]++;
   if (weights == VK_WEIGHTS_MULTIPLICITY) {
     P.weight.assign(L.ndof, 1.0);
     for (int i = 0; i < L.ndof; ++i) {
@@ -193,12 +203,13 @@ HostPatchPlan plan_patches(const vk::HostLevel& L, int weights) {
 
 struct DevLevel {
   int N = 0, ndof = 0, n_u = 0, n_p = 0;
-  vk::gpu::Sell A;
-  vk::gpu::Csr Acsr, P, R;
+  vk::gpu::Sell A, P, R;   // level matrix; prolongation from / restriction to the coarser level
+  vk::gpu::Csr Acsr;
   uint8_t* dir = nullptr;
   vk::gpu::Patches pat;
   double lam = 0.0;
   double *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *t = nullptr, *delta = nullptr;
+  float2* r2 = nullptr;  // FP32-pair residual (emulated-FP64 inverses only)
 };
 
 }  // namespace
@@ -227,8 +238,26 @@ struct vk_hierarchy {
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
   double apply_bytes = 0.0, apply_flops = 0.0;
+  // graph-resident FGMRES (one CUDA graph per hierarchy: prologue, WHILE node, epilogue)
+  vk::gpu::FgState* st = nullptr;        // device
+  vk::gpu::FgState* h_par = nullptr;     // pinned: parameters written before each launch
+  vk::gpu::FgState* h_res = nullptr;     // pinned: state copied back by the graph
+  double* h_hist = nullptr;              // pinned: residual history copied back by the graph
+  double *vin = nullptr, *zbuf = nullptr, *wbuf = nullptr;
+  cudaStream_t cap0 = nullptr, cap1 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  int64_t g_pro = 0, g_body = 0, g_epi = 0;   // kernels per prologue / iteration / epilogue
   ~vk_hierarchy() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap0) cudaStreamDestroy(cap0);
+    if (cap1) cudaStreamDestroy(cap1);
+    if (h_par) cudaFreeHost(h_par);
+    if (h_res) cudaFreeHost(h_res);
+    if (h_hist) cudaFreeHost(h_hist);
   }
 };
 
@@ -243,7 +272,8 @@ void validate(const vk_problem* p, const vk_options* o) {
   if (!(p->nu > 0.0)) raise(VK_ERR_ARG, "viscosity must be positive");
   if (o->sweeps < 1) raise(VK_ERR_ARG, "sweeps must be >= 1");
   if (o->weights != VK_WEIGHTS_PLAIN && o->weights != VK_WEIGHTS_MULTIPLICITY) raise(VK_ERR_ARG, "bad weights");
-  if (o->factor_prec != VK_PREC_F64 && o->factor_prec != VK_PREC_F32) raise(VK_ERR_ARG, "bad factor_prec");
+  if (o->factor_prec != VK_PREC_F64 && o->factor_prec != VK_PREC_F32 && o->factor_prec != VK_PREC_F64E)
+    raise(VK_ERR_ARG, "bad factor_prec");
   if (!(o->cheb_hi > o->cheb_lo) || !(o->cheb_lo > 0.0)) raise(VK_ERR_ARG, "bad Chebyshev interval");
   if (o->eig_steps < 1 || o->eig_steps > 64) raise(VK_ERR_ARG, "eig_steps must be in 1..64");
   if (o->max_iterations < 1 || o->max_iterations > 1000) raise(VK_ERR_ARG, "max_iterations must be in 1..1000");
@@ -260,6 +290,21 @@ void build_host(vk_hierarchy* h) {
   }
 }
 
+vk::gpu::Sell upload_sell(DeviceMemory& m, const vk::HostCsr& A) {
+  const int tpr = sell_tpr(A.nrows);
+  HostSell S = build_sell(A, tpr);
+  vk::gpu::Sell d;
+  d.tpr = tpr;
+  d.nrows = A.nrows;
+  d.nslices = int(S.sw.size());
+  d.sptr = m.upload(S.sptr);
+  d.swidth = m.upload(S.sw);
+  d.col = m.upload(S.col);
+  d.val = m.upload(S.val);
+  d.rowof = m.upload(S.rowof);
+  return d;
+}
+
 vk::gpu::Csr upload_csr(DeviceMemory& m, const vk::HostCsr& A) {
   vk::gpu::Csr c;
   c.nrows = A.nrows;
@@ -274,7 +319,7 @@ void allocate_device(vk_hierarchy* h) {
   DeviceMemory& m = h->mem;
   const int L = h->prob.nlevels;
   h->lv.assign(L, DevLevel{});
-  const int fsz = h->opt.factor_prec == VK_PREC_F64 ? 8 : 4;
+  const int fsz = h->opt.factor_prec == VK_PREC_F32 ? 4 : 8;   // FP64 and FP32 pairs: 8 bytes
   for (int l = 0; l < L; ++l) {
     const vk::HostLevel& H = h->host[l];
     DevLevel& D = h->lv[l];
@@ -282,19 +327,12 @@ void allocate_device(vk_hierarchy* h) {
     D.ndof = H.ndof;
     D.n_u = H.n_u;
     D.n_p = H.n_p;
-    HostSell S = build_sell(H.A);
-    D.A.nrows = H.ndof;
-    D.A.nslices = int(S.sw.size());
-    D.A.sptr = m.upload(S.sptr);
-    D.A.swidth = m.upload(S.sw);
-    D.A.col = m.upload(S.col);
-    D.A.val = m.upload(S.val);
-    D.A.rowof = m.upload(S.rowof);
+    D.A = upload_sell(m, H.A);
     D.Acsr = upload_csr(m, H.A);
     D.dir = m.upload(H.dir);
     if (l > 0) {
-      D.P = upload_csr(m, H.P);
-      D.R = upload_csr(m, H.R);
+      D.P = upload_sell(m, H.P);
+      D.R = upload_sell(m, H.R);
     }
     D.b = m.get_n<double>(H.ndof);
     D.x = m.get_n<double>(H.ndof);
@@ -305,6 +343,7 @@ void allocate_device(vk_hierarchy* h) {
       HostPatchPlan P = plan_patches(H, h->opt.weights);
       vk::gpu::Patches& G = D.pat;
       G.npatch = int(H.patch_ptr.size()) - 1;
+      G.ndof = H.ndof;
       G.nslots = int64_t(H.patch_dofs.size());
       G.slot_ptr = m.upload(H.patch_ptr);
       G.slot_dofs = m.upload(H.patch_dofs);
@@ -314,9 +353,10 @@ void allocate_device(vk_hierarchy* h) {
       G.prec = h->opt.factor_prec;
       G.nb_max = P.nb_max;
       G.dof_ptr = m.upload(P.dof_ptr);
-      G.dof_slot = m.upload(P.dof_slot);
+      G.slot_pos = m.upload(P.slot_pos);
       G.weight = P.weight.empty() ? nullptr : m.upload(P.weight);
       D.delta = m.get_n<double>(G.nslots);
+      if (h->opt.factor_prec == VK_PREC_F64E) D.r2 = m.get_n<float2>(H.ndof);
     }
   }
   h->nc = h->host[0].ndof;
@@ -339,6 +379,10 @@ void allocate_device(vk_hierarchy* h) {
   h->iflag = m.get_n<int>(16);
   h->bh = m.get_n<double>(nf);
   h->xh = m.get_n<double>(nf);
+  h->vin = m.get_n<double>(nf);
+  h->zbuf = m.get_n<double>(nf);
+  h->wbuf = m.get_n<double>(nf);
+  h->st = m.get_n<vk::gpu::FgState>(1);
 }
 
 // Finest-level patch applications are bracketed by CUDA events on their stream when timing is on.
@@ -354,7 +398,7 @@ void timed_apply(vk_hierarchy* h, int l, const double* r, cudaStream_t s) {
       }
     CK(cudaEventRecord(h->ev[h->ev_used], s));
   }
-  h->n_launch += vk::gpu::patch_apply(D.pat, r, D.delta, s);
+  h->n_launch += vk::gpu::patch_apply(D.pat, r, D.r2, D.delta, s);
   if (t) {
     CK(cudaEventRecord(h->ev[h->ev_used + 1], s));
     h->ev_used += 2;
@@ -406,8 +450,8 @@ void smooth(vk_hierarchy* h, int l, const double* b, double* x, bool zero_init, 
   }
 }
 
-void vcycle(vk_hierarchy* h, int l, const double* b, double* x, cudaStream_t s) {
-  if (l == h->prob.nlevels - 1) ++h->n_vcycle;
+void vcycle(vk_hierarchy* h, int l, const double* b, double* x, cudaStream_t s, bool count = true) {
+  if (l == h->prob.nlevels - 1 && count) ++h->n_vcycle;
   if (l == 0) {
     h->n_launch += vk::gpu::dense_gemv(h->Cinv, h->nc, h->nc + 1, b, x, s);
     return;
@@ -416,9 +460,9 @@ void vcycle(vk_hierarchy* h, int l, const double* b, double* x, cudaStream_t s) 
   DevLevel& C = h->lv[l - 1];
   smooth(h, l, b, x, true, s);
   h->n_launch += vk::gpu::sell_residual(D.A, b, x, D.r, s);
-  h->n_launch += vk::gpu::csr_restrict(D.R, C.dir, D.r, C.b, s);
-  vcycle(h, l - 1, C.b, C.x, s);
-  h->n_launch += vk::gpu::csr_prolong_add(D.P, C.x, x, s);
+  h->n_launch += vk::gpu::sell_restrict(D.R, C.dir, D.r, C.b, s);
+  vcycle(h, l - 1, C.b, C.x, s, count);
+  h->n_launch += vk::gpu::sell_prolong_add(D.P, C.x, x, s);
   smooth(h, l, b, x, false, s);
 }
 
@@ -461,7 +505,7 @@ double estimate_lambda(vk_hierarchy* h, int l, cudaStream_t s) {
       m = j + 1;
       break;
     }
-    h->n_launch += vk::gpu::scale(1.0 / hn, w, n, s);
+    h->n_launch += vk::gpu::divide(hn, w, n, s);
   }
   std::vector<double> sq(size_t(m) * m), re(m), im(m);
   for (int i = 0; i < m; ++i)
@@ -476,6 +520,11 @@ void setup_device(vk_hierarchy* h, cudaStream_t s) {
   allocate_device(h);
   CK(cudaMallocHost(&h->h_flag, 4 * sizeof(int)));
   CK(cudaMallocHost(&h->h_scal, 4 * sizeof(double)));
+  CK(cudaMallocHost(&h->h_par, sizeof(vk::gpu::FgState)));
+  CK(cudaMallocHost(&h->h_res, sizeof(vk::gpu::FgState)));
+  CK(cudaMallocHost(&h->h_hist, (h->kmax + 1) * sizeof(double)));
+  CK(cudaStreamCreateWithFlags(&h->cap0, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&h->cap1, cudaStreamNonBlocking));
   CK(cudaMemsetAsync(h->iflag, 0, 16 * sizeof(int), s));
   const int L = h->prob.nlevels;
   for (int l = 1; l < L; ++l) {
@@ -509,7 +558,7 @@ void setup_device(vk_hierarchy* h, cudaStream_t s) {
       sn += n;
       sn2 += n * n;
     }
-    const double fsz = h->opt.factor_prec == VK_PREC_F64 ? 8.0 : 4.0;
+    const double fsz = h->opt.factor_prec == VK_PREC_F32 ? 4.0 : 8.0;
     // inverse entries + slot DoF indices + gathered r + written delta + per-patch work/offset/pointers
     h->apply_bytes = fsz * sn2 + 20.0 * sn + 16.0 * np;
     h->apply_flops = 2.0 * sn2;
@@ -534,12 +583,18 @@ void check_device(const vk_hierarchy* h) {
   if (h->host_only) raise(VK_ERR_ARG, "host-only hierarchy: no device data");
 }
 
+int solve_graph(vk_hierarchy* h, const double* b, double* x, double rtol, int maxit, vk_solve_info* info,
+                cudaStream_t s);
+
 int solve_impl(vk_hierarchy* h, const double* b, double* x, double rtol, int maxit, vk_solve_info* info,
                cudaStream_t s) {
   check_device(h);
   if (!b || !x) raise(VK_ERR_ARG, "null vector");
   if (maxit < 1 || maxit > h->kmax) raise(VK_ERR_ARG, "maxit must be in 1..max_iterations");
   if (!(rtol >= 0.0)) raise(VK_ERR_ARG, "rtol must be >= 0");
+  // graph path unless disabled, or unless per-launch kernel timing was requested (events cannot
+  // bracket every iteration of a device-side loop)
+  if (h->opt.use_graph && !h->time_apply) return solve_graph(h, b, x, rtol, maxit, info, s);
   const auto t0 = std::chrono::steady_clock::now();
   const int L = h->prob.nlevels;
   DevLevel& F = h->lv[L - 1];
@@ -561,7 +616,7 @@ int solve_impl(vk_hierarchy* h, const double* b, double* x, double rtol, int max
     converged = true;
     hist.assign(1, 0.0);
   } else {
-    h->n_launch += vk::gpu::scale(1.0 / beta, h->V, n, s);
+    h->n_launch += vk::gpu::scale_copy(h->V, h->scal, h->V, n, s);   // v_1 = b_hat / beta (division)
     h->n_launch += vk::gpu::fill(h->g, 0.0, h->kmax + 1, s);
     CK(cudaMemcpyAsync(h->g, &beta, sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(h->hist, &beta, sizeof(double), cudaMemcpyHostToDevice, s));
@@ -634,6 +689,118 @@ int solve_impl(vk_hierarchy* h, const double* b, double* x, double rtol, int max
     info->true_res = true_res;
     if (info->history)
       for (size_t i = 0; i < hist.size(); ++i) info->history[i] = hist[i];
+    info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return status;
+}
+
+// One FGMRES solve as a CUDA graph: prologue (b_hat = projected bh, beta, v_1), a WHILE conditional
+// node whose body is one iteration (V-cycle, projection, A z, CGS2, normalisation, Givens; the Givens
+// kernel advances the device-side iteration counter and clears the condition on convergence or
+// maxit), and an epilogue (back substitution, x = Z y into xh, true residual, copies of the state and
+// history to pinned host memory).  Built once per hierarchy; only bh / xh are bound.
+void build_graph(vk_hierarchy* h) {
+  const int L = h->prob.nlevels;
+  DevLevel& F = h->lv[L - 1];
+  const int n = F.ndof;
+  const int64_t ld = h->ldv;
+  const int ldh = h->kmax + 1;
+  cudaStream_t c0 = h->cap0, c1 = h->cap1;
+  const bool timing = h->time_apply;
+  h->time_apply = false;
+  const int64_t launches0 = h->n_launch;
+  CK(cudaStreamBeginCapture(c0, cudaStreamCaptureModeRelaxed));
+  h->n_launch += vk::gpu::copy(h->V, h->bh, n, c0);
+  h->n_launch += vk::gpu::pressure_project(h->V, F.n_u, F.n_p, h->partial, h->scal + 1, c0);
+  h->n_launch += vk::gpu::dot_partials(h->V, h->V, n, h->partial, c0);
+  h->n_launch += vk::gpu::finalize_sum(h->partial, vk::gpu::kReduceBlocks, h->scal, c0);
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CK(cudaStreamGetCaptureInfo(c0, &cst, nullptr, &g, &deps, nullptr, &ndeps));
+  CK(cudaGraphConditionalHandleCreate(&h->cond, g, 0, 0));
+  h->n_launch += vk::gpu::fg_init(h->scal, h->st, h->g, h->hist, h->kmax, h->cond, c0);
+  h->n_launch += vk::gpu::fg_scale(h->V, h->st, n, c0);
+  h->g_pro = h->n_launch - launches0;
+  CK(cudaStreamGetCaptureInfo(c0, &cst, nullptr, &g, &deps, nullptr, &ndeps));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h->cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  CK(cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CK(cudaStreamUpdateCaptureDependencies(c0, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  // loop body, captured straight into the conditional node's body graph
+  const int64_t launches1 = h->n_launch;
+  CK(cudaStreamBeginCaptureToGraph(c1, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  h->n_launch += vk::gpu::fg_col_get(h->V, ld, h->st, h->vin, n, c1);
+  vcycle(h, L - 1, h->vin, h->zbuf, c1, false);
+  h->n_launch += vk::gpu::pressure_project(h->zbuf, F.n_u, F.n_p, h->partial, h->scal + 1, c1);
+  h->n_launch += vk::gpu::fg_col_put(h->zbuf, h->Z, ld, h->st, n, c1);
+  h->n_launch += vk::gpu::sell_residual(F.A, nullptr, h->zbuf, h->wbuf, c1);
+  h->n_launch += vk::gpu::fg_cgs_pass(h->V, ld, h->st, h->wbuf, n, h->partial, h->H, ldh, h->t2, h->kmax, 0, c1);
+  h->n_launch += vk::gpu::fg_cgs_pass(h->V, ld, h->st, h->wbuf, n, h->partial, h->H, ldh, h->t2, h->kmax, 1, c1);
+  h->n_launch += vk::gpu::dot_partials(h->wbuf, h->wbuf, n, h->partial, c1);
+  h->n_launch += vk::gpu::finalize_sum(h->partial, vk::gpu::kReduceBlocks, h->scal + 2, c1);
+  h->n_launch += vk::gpu::fg_normalize(h->wbuf, h->scal + 2, h->V, ld, h->st, h->H, ldh, n, c1);
+  h->n_launch += vk::gpu::fg_givens(h->H, ldh, h->cs, h->sn, h->g, h->hist, h->st, h->cond, c1);
+  cudaGraph_t body_out = nullptr;
+  CK(cudaStreamEndCapture(c1, &body_out));
+  h->g_body = h->n_launch - launches1;
+  // epilogue
+  const int64_t launches2 = h->n_launch;
+  h->n_launch += vk::gpu::fg_solution(h->H, ldh, h->g, h->Z, ld, h->st, h->yv, h->xh, n, c0);
+  h->n_launch += vk::gpu::copy(F.t, h->bh, n, c0);
+  h->n_launch += vk::gpu::pressure_project(F.t, F.n_u, F.n_p, h->partial, h->scal + 1, c0);
+  h->n_launch += vk::gpu::sell_residual(F.A, F.t, h->xh, F.r, c0);
+  h->n_launch += vk::gpu::dot_partials(F.r, F.r, n, h->partial, c0);
+  h->n_launch += vk::gpu::finalize_sum(h->partial, vk::gpu::kReduceBlocks, h->scal + 3, c0);
+  h->n_launch += vk::gpu::fg_finish(h->st, h->scal + 3, c0);
+  CK(cudaMemcpyAsync(h->h_res, h->st, sizeof(vk::gpu::FgState), cudaMemcpyDeviceToHost, c0));
+  CK(cudaMemcpyAsync(h->h_hist, h->hist, (h->kmax + 1) * sizeof(double), cudaMemcpyDeviceToHost, c0));
+  h->g_epi = h->n_launch - launches2;
+  CK(cudaStreamEndCapture(c0, &h->graph));
+  CK(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+  h->n_launch = launches0;
+  h->time_apply = timing;
+}
+
+int solve_graph(vk_hierarchy* h, const double* b, double* x, double rtol, int maxit, vk_solve_info* info,
+                cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!h->gexec) build_graph(h);
+  const int n = h->lv.back().ndof;
+  std::memset(h->h_par, 0, sizeof(vk::gpu::FgState));
+  h->h_par->maxit = maxit;
+  h->h_par->rtol = rtol;
+  CK(cudaMemcpyAsync(h->st, h->h_par, sizeof(vk::gpu::FgState), cudaMemcpyHostToDevice, s));
+  if (b != h->bh) CK(cudaMemcpyAsync(h->bh, b, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaGraphLaunch(h->gexec, s));
+  if (x != h->xh) CK(cudaMemcpyAsync(x, h->xh, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  const vk::gpu::FgState r = *h->h_res;
+  const int iters = r.j;
+  h->n_launch += h->g_pro + int64_t(iters) * h->g_body + h->g_epi;
+  h->n_vcycle += iters;
+  int status = VK_OK;
+  if (r.flags & 2) {
+    status = iters == 0 ? VK_ERR_NONFINITE : VK_ERR_NONFINITE;
+    g_err = iters == 0 ? "right-hand side is not finite" : "FGMRES residual estimate is not finite";
+  } else if (!(r.flags & 1)) {
+    status = VK_ERR_NOT_CONVERGED;
+    g_err = "FGMRES did not reach rtol in maxit iterations";
+  }
+  if (info) {
+    info->iterations = iters;
+    info->converged = (r.flags & 1) ? 1 : 0;
+    info->res0 = r.beta;
+    info->res_est = h->h_hist[iters];
+    info->true_res = r.true_res;
+    if (info->history)
+      for (int i = 0; i <= iters; ++i) info->history[i] = h->h_hist[i];
     info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return status;
@@ -802,8 +969,8 @@ int vk_restrict(vk_hierarchy* h, int fine_level, const double* r_fine, double* r
     check_level(h, fine_level, 1);
     check_device(h);
     if (!r_fine || !r_coarse) raise(VK_ERR_ARG, "null vector");
-    h->n_launch += vk::gpu::csr_restrict(h->lv[fine_level].R, h->lv[fine_level - 1].dir, r_fine, r_coarse,
-                          static_cast<cudaStream_t>(stream));
+    h->n_launch += vk::gpu::sell_restrict(h->lv[fine_level].R, h->lv[fine_level - 1].dir, r_fine, r_coarse,
+                                          static_cast<cudaStream_t>(stream));
     CK(cudaGetLastError());
     return VK_OK;
   });
@@ -814,7 +981,7 @@ int vk_prolong(vk_hierarchy* h, int fine_level, const double* e_coarse, double* 
     check_level(h, fine_level, 1);
     check_device(h);
     if (!e_coarse || !x_fine) raise(VK_ERR_ARG, "null vector");
-    h->n_launch += vk::gpu::csr_prolong_add(h->lv[fine_level].P, e_coarse, x_fine, static_cast<cudaStream_t>(stream));
+    h->n_launch += vk::gpu::sell_prolong_add(h->lv[fine_level].P, e_coarse, x_fine, static_cast<cudaStream_t>(stream));
     CK(cudaGetLastError());
     return VK_OK;
   });
@@ -995,7 +1162,7 @@ extern "C" int vk_vanka_noalloc(vk_hierarchy* h, int level, const double* r, dou
     double* delta = noalloc_scratch();
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // every slot is written by the patch solves before the sum reads it: nothing to clear
-    h->n_launch += vk::gpu::patch_apply(D.pat, r, delta, s);
+    h->n_launch += vk::gpu::patch_apply(D.pat, r, D.r2, delta, s);
     h->n_launch += vk::gpu::vanka_scatter(D.pat, D.ndof, D.dir, r, delta, 0, 1.0, 0.0, 0.0, z, nullptr, nullptr, s);
     CK(cudaGetLastError());
     return VK_OK;

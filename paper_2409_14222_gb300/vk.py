@@ -25,6 +25,7 @@ VK_WEIGHTS_PLAIN = 0
 VK_WEIGHTS_MULTIPLICITY = 1
 VK_PREC_F64 = 0
 VK_PREC_F32 = 1
+VK_PREC_F64E = 2
 VK_CSR_A, VK_CSR_P, VK_CSR_R = 0, 1, 2
 
 STATUS_NAMES = {0: "VK_OK", 1: "VK_ERR_ARG", 2: "VK_ERR_NO_MEMORY", 3: "VK_ERR_SINGULAR",

@@ -252,6 +252,29 @@ def test_edge_cases(vk):
         G.vanka(0, dev(b), x)
 
 
+@pytest.mark.parametrize("case", [(4, 2, 2), (2, 3, 3)])
+def test_graph_and_host_loop_paths_agree(vk, case):
+    # the whole-solve CUDA graph (device-side loop) and the host-driven loop run the same kernels
+    H, G = pair(vk, case, inject=False)
+    Nc, L, k = case
+    Gh = vk.Hierarchy(Nc, L, k, options=vk.default_options(use_graph=0))
+    b = si.rhs_normal(H.finest.space.ndof, 21)
+    xg, xh = torch.zeros_like(dev(b)), torch.zeros_like(dev(b))
+    og = G.solve(dev(b), xg, rtol=1e-10)
+    oh = Gh.solve(dev(b), xh, rtol=1e-10)
+    assert og["iterations"] == oh["iterations"]
+    assert np.allclose(og["history"], oh["history"], rtol=1e-14, atol=0)
+    assert rel(host(xg), host(xh)) <= 1e-14
+    # launches are counted the same way on both paths
+    G.stats_reset()
+    Gh.stats_reset()
+    G.solve(dev(b), xg, rtol=1e-10)
+    Gh.solve(dev(b), xh, rtol=1e-10)
+    sg, sh = G.stats(), Gh.stats()
+    assert sg["vcycles"] == sh["vcycles"] == og["iterations"]
+    assert sg["launches"] > 0 and sh["launches"] > 0
+
+
 def test_host_buffer_solve_equals_device_solve(vk):
     H, G = pair(vk, (2, 3, 2), inject=False)
     n = H.finest.space.ndof
@@ -263,6 +286,30 @@ def test_host_buffer_solve_equals_device_solve(vk):
     out_h = G.solve_host(bh.numpy(), xh.numpy(), rtol=1e-10)
     assert out_h["iterations"] == out_d["iterations"]
     assert np.array_equal(xh.numpy(), host(xd))
+
+
+@pytest.mark.parametrize("case", [(4, 2, 2), (2, 3, 3), (2, 2, 4)])
+def test_emulated_fp64_inverses_parity(vk, case):
+    # FP32-pair inverses applied in FP32-pair arithmetic: ~48-bit products, so one Vanka application
+    # agrees with the oracle's LU solves to ~1e-13 and whole solves keep the FP64 parity targets
+    H, G = pair(vk, case, inject=False, prec=vk.VK_PREC_F64E)
+    rng = np.random.default_rng(31)
+    for l in range(1, case[1]):
+        lev = H.levels[l]
+        r = rng.standard_normal(lev.space.ndof)
+        z = torch.empty_like(dev(r))
+        G.vanka(l, dev(r), z)
+        err = rel(host(z), solver.vanka_apply(lev, r))
+        print(f"f64e vanka {case} level {l}: rel. dev {err:.2e}")
+        assert err <= 1e-12
+    _solve_parity(vk, H, G, si.rhs_normal(H.finest.space.ndof, 0), 1e-10)
+
+
+def test_emulated_fp64_config2_full_size(vk, config2):
+    H, _ = config2
+    G = vk.Hierarchy(16, 4, 2, options=vk.default_options(factor_prec=vk.VK_PREC_F64E))
+    out, ref = _solve_parity(vk, H, G, si.rhs_normal(H.finest.space.ndof, 0), 1e-8)
+    assert out["converged"]
 
 
 def test_fp32_factors_reach_tolerance(vk):
