@@ -32,6 +32,8 @@ CONFIGS = {
     "cfg3p3": (16, 3, 3, 1, 1e-8, "2D Stokes TH P3/P2, 16x16 -> 64x64 (3 levels), FGMRES to 1e-8"),
     "cfg3p4": (16, 3, 4, 1, 1e-8, "2D Stokes TH P4/P3, 16x16 -> 64x64 (3 levels), FGMRES to 1e-8"),
     "cfg4": (32, 5, 2, 1, 1e-8, "2D Stokes TH P2/P1, 32x32 -> 512x512 (5 levels), FGMRES to 1e-8"),
+    "cfg5": (8, 0, 0, 1, 1e-8, "Serving: Poisson stream of solve requests, N in {16..256} (coarsest 8x8), "
+                               "k in {2,3,4}, FGMRES to 1e-8"),
 }
 
 HBM_FALLBACK = 6800.0
@@ -263,6 +265,7 @@ def run_vk(args, cfg):
         G.solve(B[args.warmup + s], x, rtol=rtol, history=False)
     torch.cuda.synchronize()
     kt = G.stats()
+    G.stats_reset(time_kernels=False)       # back to the graph path for the end-to-end pass
     # end to end through the C ABI with host buffers (pinned): H2D copy + solve + D2H copy per step
     bh = [torch.from_numpy(si.rhs_normal(ndof, 7777 + s)).pin_memory() for s in range(args.steps)]
     xh = torch.zeros(ndof, dtype=torch.float64).pin_memory()
@@ -323,6 +326,109 @@ def run_vk(args, cfg):
     print(json.dumps(out), flush=True)
 
 
+def serve_pass(vk, srv, reqs, arrivals):
+    """Submit reqs at the given arrival offsets (s) from one thread; collect results in order."""
+    import threading
+    import synthetic_inputs as si
+    tickets = [None] * len(reqs)
+    rhs = [si.rhs_normal(vk.ndof_of(*key), seed) for key, seed in reqs]
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, ((key, seed), ta) in enumerate(zip(reqs, arrivals)):
+            delay = t0 + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets[i] = srv.submit(*key, rhs[i], rtol=1e-8)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat, done_t, iters = [], [], []
+    for i in range(len(reqs)):
+        while tickets[i] is None:
+            time.sleep(1e-4)
+        x, res = srv.wait(tickets[i])
+        if res["status"] not in (0, 5):
+            raise RuntimeError(f"request {i} failed: {res}")
+        lat.append(res["latency_ms"])
+        iters.append(res["iterations"])
+        done_t.append(time.perf_counter() - t0)
+    th.join()
+    span = max(done_t) - min(arrivals)
+    return {"requests": len(reqs), "solves_per_s": len(reqs) / span,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_iterations": float(np.mean(iters))}
+
+
+def run_serving(args):
+    """cfg5: continuous batching of a Poisson request stream (vk_server, C++ runtime)."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    import paper_2409_14222_gb300 as vk
+    import synthetic_inputs as si
+    torch.cuda.set_device(0)
+    mix = si.request_mix(args.requests, seed=42)
+    keys = lambda N, k: (8, int(np.log2(N // 8)) + 1, k)
+    reqs = [(keys(N, k), seed) for N, k, seed in mix]
+    uniq = sorted(set(k for k, _ in reqs))
+    opts = vk.default_options()
+    if args.prec == "f32":
+        opts.factor_prec = vk.VK_PREC_F32
+    elif args.prec == "f64e":
+        opts.factor_prec = vk.VK_PREC_F64E
+
+    def warm(srv, per_key):
+        # every hierarchy resident (per_key instances of each key) before any timed request
+        for key in uniq:
+            ts = [srv.submit(*key, si.rhs_normal(vk.ndof_of(*key), 7), rtol=1e-8) for _ in range(per_key)]
+            for t in ts:
+                _, res = srv.wait(t)
+                if res["status"] not in (0, 5):
+                    raise RuntimeError(f"warm-up solve of {key} failed: {res}")
+
+    out_rates = {}
+    per_key = min(args.slots, 2)
+    srv = vk.Server(slots=args.slots, options=opts, max_per_key=per_key)
+    t0 = time.perf_counter()
+    warm(srv, per_key)
+    warm_s = time.perf_counter() - t0
+    ncap = min(len(reqs), 300)
+    cap = serve_pass(vk, srv, reqs[:ncap], [0.0] * ncap)
+    capacity = cap["solves_per_s"]
+    with ClockSampler(0) as clk:
+        for mult in (0.5, 1.0, 2.0):
+            n = len(reqs) if mult == 1.0 else min(len(reqs), 300)
+            arr = si.poisson_arrivals(n, mult * capacity, seed=42 + int(10 * mult))
+            out_rates[f"{mult}x"] = serve_pass(vk, srv, reqs[:n], arr)
+    st = srv.stats()
+    srv.close()
+    # plain FP64, one request at a time, same stream at the measured 1x rate
+    base = {}
+    if not args.no_baseline:
+        srv1 = vk.Server(slots=1, options=vk.default_options())
+        warm(srv1, 1)
+        n1 = min(len(reqs), 300)
+        base_cap = serve_pass(vk, srv1, reqs[:n1], [0.0] * n1)
+        base_rate = serve_pass(vk, srv1, reqs[:n1], si.poisson_arrivals(n1, capacity, seed=52))
+        base = {"capacity_solves_per_s": base_cap["solves_per_s"], "at_1x_rate": base_rate}
+        srv1.close()
+    one = out_rates["1.0x"]
+    print(json.dumps({
+        "metric": METRIC, "value": capacity, "unit": "solves/s", "n_gpus": 1, "steps": len(reqs),
+        "warmup": len(uniq) * per_key, "ms_per_step": 1e3 / capacity, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f64": "f64", "f64e": "f64 vectors; FP32-pair patch inverses", "f32": "f64 vectors, f32 patch inverses"}[args.prec],
+        "data": "synthetic",
+        "config": {"workload": CONFIGS["cfg5"][5], "requests": len(reqs), "slots": args.slots,
+                   "distinct_hierarchies": len(uniq), "factor_prec": args.prec, "arrivals": "Poisson, seed 42",
+                   "warm_s": warm_s},
+        "latency_ms": {"p50": one["p50_ms"], "p99": one["p99_ms"]},
+        "rates": out_rates, "capacity": cap, "one_at_a_time_plain_fp64": base,
+        "server": st, "clocks": clk.summary(),
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,12 +441,17 @@ def main():
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven FGMRES loop instead of the whole-solve CUDA graph (for kernel profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=1000, help="cfg5: requests in the 1x stream")
+    ap.add_argument("--slots", type=int, default=4, help="cfg5: concurrent solves")
+    ap.add_argument("--no-baseline", action="store_true", help="cfg5: skip the one-at-a-time FP64 pass")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "vk":
         ap.error("--warmup must be >= 3")
     cfg = CONFIGS[args.config]
     if args.impl == "reference":
         run_reference(args, cfg)
+    elif args.config == "cfg5":
+        run_serving(args)
     else:
         run_vk(args, cfg)
 

@@ -243,6 +243,63 @@ int vk_stats_reset(vk_hierarchy* h, int time_kernels);
 /* Reads the counters (waits for the recorded events). */
 int vk_stats_read(vk_hierarchy* h, vk_stats* out);
 
+/* ---- solve service (continuous batching on one GPU) ------------------------------------------- *
+ * A request is one FGMRES solve (vk_solve semantics) of a problem of its own mesh size and order.
+ * `slots` worker threads, each with its own CUDA stream, take requests in arrival order as soon as
+ * they are free, so the solves of admitted requests overlap on the device.  Hierarchies stay resident
+ * between requests (one pool entry serves one slot at a time).  Admission is by device footprint
+ * (vk_footprint): when memory_budget would be exceeded, idle hierarchies are destroyed least recently
+ * used first, and a request waits while the memory it needs is held by running solves; a request
+ * larger than the whole budget fails with VK_ERR_NO_MEMORY.  Results do not depend on the mix: each
+ * solve runs the same deterministic kernels on its own hierarchy. */
+typedef struct vk_server vk_server;
+
+typedef struct vk_server_config {
+  int32_t slots;         /* concurrent solves (1..64)                                             */
+  int32_t max_per_key;   /* resident hierarchies per (N_coarse, nlevels, k); requests of a key whose
+                            hierarchies are all busy wait for one (0 = slots; default 2)          */
+  int32_t device;        /* CUDA device ordinal                                                   */
+  size_t memory_budget;  /* device bytes for resident hierarchies; 0 = 60% of free memory         */
+  vk_options options;    /* options of every hierarchy the server builds                          */
+} vk_server_config;
+
+typedef struct vk_request {
+  vk_problem problem;    /* mesh hierarchy, order and viscosity of this solve                     */
+  const double* b;       /* host right-hand side (ndof doubles), copied by vk_server_submit       */
+  double rtol;
+  int32_t maxit;
+} vk_request;
+
+typedef struct vk_result {
+  int32_t status;        /* VK_OK, VK_ERR_NOT_CONVERGED, or the error of the solve / setup        */
+  int32_t iterations;
+  int32_t converged;
+  double res0, true_res; /* as in vk_solve_info                                                   */
+  double queue_ms;       /* submission -> start on a slot                                         */
+  double setup_ms;       /* hierarchy build time charged to this request (0 when resident)        */
+  double solve_ms;       /* vk_solve_host time (copies included)                                  */
+  double latency_ms;     /* submission -> result ready on the host                                */
+} vk_result;
+
+typedef struct vk_server_stats {
+  int64_t submitted, completed, failed, builds, evictions;
+  int32_t resident;      /* hierarchies currently resident                                        */
+  int32_t queued;        /* requests waiting for a slot                                           */
+  size_t bytes_used;     /* device bytes of resident hierarchies                                  */
+  size_t memory_budget;
+} vk_server_stats;
+
+void vk_default_server_config(vk_server_config* c);   /* 4 slots, 2 per key, device 0, budget 0 */
+int vk_server_create(const vk_server_config* c, vk_server** out);
+/* Queues a request; *ticket identifies it for vk_server_wait. */
+int vk_server_submit(vk_server* s, const vk_request* r, uint64_t* ticket);
+/* Waits for a request (timeout_ms < 0: forever); copies x (ndof doubles) to x_host if not NULL and
+ * fills *res.  Returns VK_ERR_TIMEOUT if the result is not ready in time (the request stays queued). */
+int vk_server_wait(vk_server* s, uint64_t ticket, double* x_host, vk_result* res, int timeout_ms);
+int vk_server_get_stats(vk_server* s, vk_server_stats* out);
+/* Finishes the queued requests, stops the workers and frees every hierarchy. */
+void vk_server_destroy(vk_server* s);
+
 /* Host-only helper: eigenvalues of the m x m row-major real upper-Hessenberg matrix H (the Arnoldi
  * matrix of the eigenvalue estimate).  Returns VK_ERR_INTERNAL if the QR iteration does not converge. */
 int vk_hessenberg_eigenvalues(int m, const double* H, double* re, double* im);

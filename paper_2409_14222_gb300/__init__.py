@@ -4,6 +4,6 @@ Implements the hot path of arXiv 2409.14222 (composite Vanka patches, Chebyshev-
 additive relaxation, V-cycle preconditioned FGMRES) as a C-ABI CUDA library (``libvk.so``, declared in
 ``include/vk.h``) with this thin binding.  Build the library with ``build.build()``.
 """
-from .vk import (Hierarchy, VkError, default_options, footprint, hessenberg_eigenvalues, lib,  # noqa: F401
+from .vk import (Hierarchy, Server, VkError, ndof_of, default_options, footprint, hessenberg_eigenvalues, lib,  # noqa: F401
                  VK_PREC_F32, VK_PREC_F64, VK_PREC_F64E, VK_WEIGHTS_MULTIPLICITY, VK_WEIGHTS_PLAIN, VK_CSR_A, VK_CSR_P,
                  VK_CSR_R, SYMBOLS)

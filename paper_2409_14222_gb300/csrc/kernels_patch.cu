@@ -367,19 +367,23 @@ int apply_prec(const Patches& P, const double* r, const float2* r2, double* delt
 
 int patch_factor(const Csr& A, const Patches& P, int prec, void* factors, int* status, cudaStream_t s) {
   if (P.npatch == 0) return 0;
-  // shared bytes n*n*8 + n*12 for the largest patch of the level (n <= 4 * nb_max <= 128)
+  // shared bytes n*n*8 + n*12 for the largest patch of the level (n <= 4 * nb_max <= 128).  The
+  // function attribute is always set to the bound for n = 128 (the same value from every thread, so
+  // concurrent setups cannot lower it under each other's launches).
   const int nmax = 4 * P.nb_max;
   const size_t smem = size_t(nmax) * nmax * 8 + size_t(nmax) * 12;
+  const int smem_cap = 128 * 128 * 8 + 128 * 12;
+  if (nmax > 128) return 0;
   if (prec == 0) {
-    cudaFuncSetAttribute(k_patch_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaFuncSetAttribute(k_patch_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);
     k_patch_factor<double><<<P.npatch, kFactorThreads, smem, s>>>(A, P.slot_ptr, P.slot_dofs, P.foff,
                                                                    static_cast<double*>(factors), status);
   } else if (prec == 1) {
-    cudaFuncSetAttribute(k_patch_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaFuncSetAttribute(k_patch_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);
     k_patch_factor<float><<<P.npatch, kFactorThreads, smem, s>>>(A, P.slot_ptr, P.slot_dofs, P.foff,
                                                                   static_cast<float*>(factors), status);
   } else {
-    cudaFuncSetAttribute(k_patch_factor<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaFuncSetAttribute(k_patch_factor<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);
     k_patch_factor<float2><<<P.npatch, kFactorThreads, smem, s>>>(A, P.slot_ptr, P.slot_dofs, P.foff,
                                                                    static_cast<float2*>(factors), status);
   }

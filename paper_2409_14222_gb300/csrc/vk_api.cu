@@ -20,6 +20,12 @@ namespace {
 
 thread_local std::string g_err;
 
+// Library-wide lock around the operations that allocate, free or synchronise the whole device, and
+// around stream capture: a device-wide synchronisation or a free issued by one thread while another
+// thread captures a graph would invalidate that capture.  Solves (launches, copies and waits on the
+// caller's stream) never take it, so concurrent solves on different hierarchies still overlap.
+std::mutex g_device_mu;
+
 struct VkError {
   int code;
   std::string msg;
@@ -153,11 +159,15 @@ HostSell build_sell(const vk::HostCsr& A, int tpr) {
           S.col[pos] = A.col[A.ptr[row] + k];
           S.val[pos] = A.val[A.ptr[row] + k];
         } else {
-          S.col[pos] = row >= 0 ? row : 0;
+          // padding: value 0 at a valid column of x (the row itself when the matrix is square,
+          // else column 0: P has more rows than the coarse vector has entries)
+          S.col[pos] = (row >= 0 && row < A.ncols) ? row : 0;
           S.val[pos] = 0.0;
         }
       }
     }
+  for (const int c : S.col)
+    if (c < 0 || c >= A.ncols) raise(VK_ERR_INTERNAL, "SELL column out of range");
   return S;
 }
 
@@ -516,6 +526,7 @@ double estimate_lambda(vk_hierarchy* h, int l, cudaStream_t s) {
 }
 
 void setup_device(vk_hierarchy* h, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g_device_mu);
   h->mem.stream = s;
   allocate_device(h);
   CK(cudaMallocHost(&h->h_flag, 4 * sizeof(int)));
@@ -699,7 +710,31 @@ int solve_impl(vk_hierarchy* h, const double* b, double* x, double rtol, int max
 // kernel advances the device-side iteration counter and clears the condition on convergence or
 // maxit), and an epilogue (back substitution, x = Z y into xh, true residual, copies of the state and
 // history to pinned host memory).  Built once per hierarchy; only bh / xh are bound.
+void build_graph_locked(vk_hierarchy* h);
+
 void build_graph(vk_hierarchy* h) {
+  std::lock_guard<std::mutex> lock(g_device_mu);
+  try {
+    build_graph_locked(h);
+  } catch (...) {
+    // leave no stream in capture mode and no half-built graph behind
+    cudaStreamCaptureStatus st;
+    for (cudaStream_t c : {h->cap1, h->cap0})
+      if (c && cudaStreamIsCapturing(c, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(c, &g);
+        if (g) cudaGraphDestroy(g);
+      }
+    cudaGetLastError();
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+    throw;
+  }
+}
+
+void build_graph_locked(vk_hierarchy* h) {
   const int L = h->prob.nlevels;
   DevLevel& F = h->lv[L - 1];
   const int n = F.ndof;
@@ -875,6 +910,7 @@ int vk_setup(const vk_problem* p, const vk_options* o, const vk_allocator* alloc
 
 void vk_destroy(vk_hierarchy* h) {
   if (!h) return;
+  std::lock_guard<std::mutex> lock(g_device_mu);
   if (!h->host_only) {
     cudaDeviceSynchronize();
     h->mem.release_all();

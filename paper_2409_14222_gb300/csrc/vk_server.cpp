@@ -1,0 +1,332 @@
+// Solve service on one GPU (include/vk.h, vk_server_*): a FIFO of Stokes solve requests of mixed mesh
+// size and order, served by `slots` worker threads that each own a CUDA stream, so solves that are
+// admitted together run concurrently on the device (continuous batching: a request is admitted as
+// soon as a slot and enough device memory are free).  Hierarchies are kept resident between requests
+// in a pool keyed by (N_coarse, nlevels, k); a pool entry is used by one slot at a time.  Admission is
+// by device footprint (vk_footprint): when the budget would be exceeded, idle hierarchies are evicted
+// least-recently-used first; a request waits while the memory it needs is held by busy solves.
+//
+// Built only on the public C ABI (vk_setup / vk_solve / vk_footprint / vk_destroy): every solve runs
+// the same kernels as a direct vk_solve, so a result does not depend on what else is being served.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "vk.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_since(Clock::time_point t0, Clock::time_point t1) {
+  return std::chrono::duration<double, std::milli>(t1 - t0).count();
+}
+
+using Key = std::tuple<int, int, int>;  // N_coarse, nlevels, k
+
+struct Instance {
+  vk_hierarchy* h = nullptr;
+  size_t bytes = 0;
+  bool busy = false;
+  Clock::time_point last_used;
+};
+
+struct Job {
+  uint64_t ticket = 0;
+  vk_problem problem{};
+  std::vector<double> b;
+  double rtol = 1e-8;
+  int maxit = 100;
+  Clock::time_point submitted;
+};
+
+struct Done {
+  vk_result res{};
+  std::vector<double> x;
+};
+
+}  // namespace
+
+struct vk_server {
+  vk_server_config cfg{};
+  std::mutex mu;
+  std::condition_variable cv_work;   // workers: new job or freed memory
+  std::condition_variable cv_done;   // waiters: a result arrived
+  std::deque<Job> queue;
+  std::map<Key, std::vector<std::unique_ptr<Instance>>> pool;
+  std::map<uint64_t, Done> done;
+  std::vector<std::thread> workers;
+  uint64_t next_ticket = 1;
+  size_t used = 0;
+  bool stopping = false;
+  vk_server_stats st{};
+  std::string error;
+};
+
+namespace {
+
+thread_local std::string g_srv_err;
+
+size_t footprint_of(vk_server* s, const vk_problem& p) {
+  size_t b = 0;
+  if (vk_footprint(&p, &s->cfg.options, &b) != VK_OK) return 0;
+  return b;
+}
+
+// Called with s->mu held.  Returns an idle instance for key (marked busy), builds one if memory
+// allows (evicting idle LRU instances), or returns nullptr if the request must wait.
+Instance* acquire(vk_server* s, std::unique_lock<std::mutex>& lk, const vk_problem& p, int stream_id,
+                  cudaStream_t stream, double* setup_ms, int* status) {
+  const Key key{p.N_coarse, p.nlevels, p.k};
+  auto& list = s->pool[key];
+  for (auto& inst : list)
+    if (!inst->busy) {
+      inst->busy = true;
+      return inst.get();
+    }
+  // all instances of this key are busy: wait for one rather than build beyond the per-key cap
+  if (int(list.size()) >= s->cfg.max_per_key) return nullptr;
+  const size_t need = footprint_of(s, p);
+  if (need == 0) {
+    *status = VK_ERR_ARG;
+    return nullptr;
+  }
+  if (need > s->cfg.memory_budget) {
+    *status = VK_ERR_NO_MEMORY;
+    return nullptr;
+  }
+  while (s->used + need > s->cfg.memory_budget) {
+    // evict the least recently used idle instance of any key
+    Instance* victim = nullptr;
+    Key vkey{};
+    for (auto& kv : s->pool)
+      for (auto& inst : kv.second)
+        if (!inst->busy && (!victim || inst->last_used < victim->last_used)) {
+          victim = inst.get();
+          vkey = kv.first;
+        }
+    if (!victim) return nullptr;  // everything resident is busy: wait for a release
+    auto& vl = s->pool[vkey];
+    for (size_t i = 0; i < vl.size(); ++i)
+      if (vl[i].get() == victim) {
+        vk_hierarchy* h = victim->h;
+        s->used -= victim->bytes;
+        vl.erase(vl.begin() + long(i));
+        lk.unlock();
+        vk_destroy(h);
+        lk.lock();
+        s->st.evictions++;
+        break;
+      }
+  }
+  // reserve the memory, build outside the lock
+  s->used += need;
+  auto inst = std::make_unique<Instance>();
+  inst->busy = true;
+  inst->bytes = need;
+  Instance* raw = inst.get();
+  s->pool[key].push_back(std::move(inst));
+  lk.unlock();
+  const auto t0 = Clock::now();
+  vk_hierarchy* h = nullptr;
+  const int rc = vk_setup(&p, &s->cfg.options, nullptr, stream, &h);
+  *setup_ms = ms_since(t0, Clock::now());
+  lk.lock();
+  (void)stream_id;
+  if (rc != VK_OK) {
+    auto& l2 = s->pool[key];
+    for (size_t i = 0; i < l2.size(); ++i)
+      if (l2[i].get() == raw) {
+        l2.erase(l2.begin() + long(i));
+        break;
+      }
+    s->used -= need;
+    *status = rc;
+    return nullptr;
+  }
+  raw->h = h;
+  s->st.builds++;
+  return raw;
+}
+
+void worker(vk_server* s, int id) {
+  cudaSetDevice(s->cfg.device);
+  cudaStream_t stream = nullptr;
+  const bool stream_ok = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess;
+  // host staging is pageable: pinned allocations or frees at run time would synchronise the device
+  std::vector<double> hx;
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    s->cv_work.wait(lk, [&] { return s->stopping || !s->queue.empty(); });
+    if (s->stopping && s->queue.empty()) break;
+    Job job = std::move(s->queue.front());
+    s->queue.pop_front();
+    const auto t_start = Clock::now();
+    double setup_ms = 0.0;
+    int status = VK_OK;
+    Instance* inst = nullptr;
+    if (!stream_ok) status = VK_ERR_CUDA;
+    while (status == VK_OK) {
+      inst = acquire(s, lk, job.problem, id, stream, &setup_ms, &status);
+      if (inst || status != VK_OK || s->stopping) break;
+      s->cv_work.wait(lk);  // memory held by busy solves: wait for a release
+    }
+    Done out;
+    out.res.queue_ms = ms_since(job.submitted, t_start);
+    out.res.setup_ms = setup_ms;
+    if (inst) {
+      lk.unlock();
+      const size_t n = job.b.size();
+      hx.assign(n, 0.0);
+      vk_solve_info info{};
+      status = vk_solve_host(inst->h, job.b.data(), hx.data(), job.rtol, job.maxit, &info, stream);
+      out.x = hx;
+      out.res.iterations = info.iterations;
+      out.res.converged = info.converged;
+      out.res.res0 = info.res0;
+      out.res.true_res = info.true_res;
+      out.res.solve_ms = info.solve_ms;
+      lk.lock();
+      inst->busy = false;
+      inst->last_used = Clock::now();
+      s->cv_work.notify_all();
+    }
+    out.res.status = status;
+    out.res.latency_ms = ms_since(job.submitted, Clock::now());
+    s->st.completed++;
+    if (status != VK_OK && status != VK_ERR_NOT_CONVERGED) s->st.failed++;
+    s->done[job.ticket] = std::move(out);
+    s->cv_done.notify_all();
+  }
+  lk.unlock();
+  if (stream_ok) cudaStreamDestroy(stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+void vk_default_server_config(vk_server_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->slots = 4;
+  c->max_per_key = 2;
+  c->memory_budget = 0;
+  c->device = 0;
+  vk_default_options(&c->options);
+}
+
+int vk_server_create(const vk_server_config* cfg, vk_server** out) {
+  g_srv_err.clear();
+  if (!cfg || !out || cfg->slots < 1 || cfg->slots > 64) {
+    g_srv_err = "bad server configuration";
+    return VK_ERR_ARG;
+  }
+  auto s = std::make_unique<vk_server>();
+  s->cfg = *cfg;
+  if (s->cfg.max_per_key < 1) s->cfg.max_per_key = s->cfg.slots;
+  s->cfg.options.lambdas = nullptr;
+  s->cfg.options.host_only = 0;
+  if (cudaSetDevice(cfg->device) != cudaSuccess) {
+    cudaGetLastError();
+    g_srv_err = "cudaSetDevice failed";
+    return VK_ERR_CUDA;
+  }
+  if (s->cfg.memory_budget == 0) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      g_srv_err = "cudaMemGetInfo failed";
+      return VK_ERR_CUDA;
+    }
+    s->cfg.memory_budget = free_b / 10 * 6;
+  }
+  vk_server* raw = s.get();
+  for (int i = 0; i < cfg->slots; ++i) raw->workers.emplace_back(worker, raw, i);
+  *out = s.release();
+  return VK_OK;
+}
+
+int vk_server_submit(vk_server* s, const vk_request* r, uint64_t* ticket) {
+  g_srv_err.clear();
+  if (!s || !r || !r->b || !ticket || r->maxit < 1) {
+    g_srv_err = "bad request";
+    return VK_ERR_ARG;
+  }
+  const int k = r->problem.k;
+  const int64_t Nf = int64_t(r->problem.N_coarse) << std::max(0, r->problem.nlevels - 1);
+  if (k < 2 || k > 4 || r->problem.nlevels < 1 || r->problem.N_coarse < 1) {
+    g_srv_err = "bad problem";
+    return VK_ERR_ARG;
+  }
+  const int64_t ndof = 2 * (k * Nf + 1) * (k * Nf + 1) + ((k - 1) * Nf + 1) * ((k - 1) * Nf + 1);
+  Job job;
+  job.problem = r->problem;
+  job.b.assign(r->b, r->b + ndof);
+  job.rtol = r->rtol;
+  job.maxit = r->maxit;
+  job.submitted = Clock::now();
+  std::lock_guard<std::mutex> lk(s->mu);
+  job.ticket = s->next_ticket++;
+  *ticket = job.ticket;
+  s->queue.push_back(std::move(job));
+  s->st.submitted++;
+  s->cv_work.notify_one();
+  return VK_OK;
+}
+
+int vk_server_wait(vk_server* s, uint64_t ticket, double* x_host, vk_result* res, int timeout_ms) {
+  g_srv_err.clear();
+  if (!s) return VK_ERR_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto ready = [&] { return s->done.count(ticket) > 0; };
+  if (timeout_ms < 0)
+    s->cv_done.wait(lk, ready);
+  else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+    return VK_ERR_TIMEOUT;
+  Done d = std::move(s->done[ticket]);
+  s->done.erase(ticket);
+  lk.unlock();
+  if (x_host && !d.x.empty()) std::memcpy(x_host, d.x.data(), d.x.size() * sizeof(double));
+  if (res) *res = d.res;
+  return VK_OK;
+}
+
+int vk_server_get_stats(vk_server* s, vk_server_stats* out) {
+  if (!s || !out) return VK_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->st;
+  out->resident = 0;
+  for (auto& kv : s->pool) out->resident += int32_t(kv.second.size());
+  out->bytes_used = s->used;
+  out->memory_budget = s->cfg.memory_budget;
+  out->queued = int32_t(s->queue.size());
+  return VK_OK;
+}
+
+void vk_server_destroy(vk_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stopping = true;
+  }
+  s->cv_work.notify_all();
+  for (auto& t : s->workers) t.join();
+  for (auto& kv : s->pool)
+    for (auto& inst : kv.second)
+      if (inst->h) vk_destroy(inst->h);
+  delete s;
+}
+
+}  // extern "C"

@@ -38,7 +38,8 @@ SYMBOLS = [
     "vk_level_info", "vk_lambda", "vk_residual", "vk_vanka", "vk_smooth", "vk_restrict", "vk_prolong",
     "vk_coarse_solve", "vk_vcycle", "vk_solve", "vk_solve_host", "vk_csr_dims", "vk_export_csr",
     "vk_export_patches", "vk_export_dirichlet", "vk_hessenberg_eigenvalues", "vk_stats_reset", "vk_stats_read",
-    "vk_vanka_noalloc",
+    "vk_vanka_noalloc", "vk_default_server_config", "vk_server_create", "vk_server_submit", "vk_server_wait",
+    "vk_server_get_stats", "vk_server_destroy",
 ]
 
 
@@ -80,6 +81,28 @@ class vk_stats(ctypes.Structure):
                 ("apply_ms", ctypes.c_double), ("apply_bytes", ctypes.c_double), ("apply_flops", ctypes.c_double)]
 
 
+class vk_server_config(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_per_key", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("memory_budget", ctypes.c_size_t), ("options", vk_options)]
+
+
+class vk_request(ctypes.Structure):
+    _fields_ = [("problem", vk_problem), ("b", ctypes.c_void_p), ("rtol", ctypes.c_double),
+                ("maxit", ctypes.c_int32)]
+
+
+class vk_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("res0", ctypes.c_double), ("true_res", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class vk_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("builds", ctypes.c_int64), ("evictions", ctypes.c_int64), ("resident", ctypes.c_int32),
+                ("queued", ctypes.c_int32), ("bytes_used", ctypes.c_size_t), ("memory_budget", ctypes.c_size_t)]
+
+
 _lib = None
 
 
@@ -117,6 +140,12 @@ def lib():
             "vk_export_dirichlet": (I, [H, I, VP]),
             "vk_hessenberg_eigenvalues": (I, [I, VP, VP, VP]),
             "vk_stats_reset": (I, [H, I]),
+            "vk_default_server_config": (None, [P(vk_server_config)]),
+            "vk_server_create": (I, [P(vk_server_config), P(VP)]),
+            "vk_server_submit": (I, [VP, P(vk_request), P(ctypes.c_uint64)]),
+            "vk_server_wait": (I, [VP, ctypes.c_uint64, VP, P(vk_result), I]),
+            "vk_server_get_stats": (I, [VP, P(vk_server_stats)]),
+            "vk_server_destroy": (None, [VP]),
             "vk_stats_read": (I, [H, P(vk_stats)]),
         }
         for name, (res, args) in sig.items():
@@ -354,3 +383,64 @@ def hessenberg_eigenvalues(H):
     re, im = np.zeros(m), np.zeros(m)
     check(lib().vk_hessenberg_eigenvalues(m, _ptr(H), _ptr(re), _ptr(im)))
     return re + 1j * im
+
+
+def ndof_of(N_coarse, nlevels, k):
+    """DoFs of the finest level (canonical numbering of include/vk.h)."""
+    Nf = N_coarse << (nlevels - 1)
+    return 2 * (k * Nf + 1) ** 2 + ((k - 1) * Nf + 1) ** 2
+
+
+class Server:
+    """The solve service of include/vk.h (vk_server_*): submit host right-hand sides, wait for results."""
+
+    def __init__(self, slots=4, memory_budget=0, device=0, options=None, max_per_key=None):
+        c = vk_server_config()
+        lib().vk_default_server_config(ctypes.byref(c))
+        c.slots = slots
+        if max_per_key is not None:
+            c.max_per_key = max_per_key
+        c.memory_budget = int(memory_budget)
+        c.device = device
+        if options is not None:
+            c.options = options
+        self.handle = ctypes.c_void_p()
+        check(lib().vk_server_create(ctypes.byref(c), ctypes.byref(self.handle)))
+        self._keep = {}
+
+    def submit(self, N_coarse, nlevels, k, b, rtol=1e-8, maxit=100, nu=1.0):
+        import numpy as np
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        assert b.size == ndof_of(N_coarse, nlevels, k)
+        r = vk_request(vk_problem(N_coarse, nlevels, k, nu), b.ctypes.data, float(rtol), int(maxit))
+        t = ctypes.c_uint64()
+        check(lib().vk_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
+        self._keep[t.value] = ndof_of(N_coarse, nlevels, k)
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        """Returns (x, result dict); raises VkError(VK_ERR_TIMEOUT) if not ready in time."""
+        import numpy as np
+        n = self._keep[ticket]
+        x = np.zeros(n)
+        res = vk_result()
+        check(lib().vk_server_wait(self.handle, ctypes.c_uint64(ticket), x.ctypes.data_as(ctypes.c_void_p),
+                                   ctypes.byref(res), int(timeout_ms)))
+        del self._keep[ticket]
+        return x, {name: getattr(res, name) for name, _ in vk_result._fields_}
+
+    def stats(self):
+        st = vk_server_stats()
+        check(lib().vk_server_get_stats(self.handle, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in vk_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().vk_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -100,3 +100,10 @@ def test_host_only_hierarchy_refuses_device_calls(vk):
     with pytest.raises(vk.VkError) as e:
         h.lam(1)
     assert e.value.code == vk.vk.VK_ERR_ARG
+
+
+@pytest.mark.parametrize("key", [(8, 3, 2), (8, 3, 4), (4, 3, 3)])
+def test_footprint_builds_every_device_layout_on_the_host(vk, key):
+    # vk_footprint builds the SELL forms of A, P and R (with their column-range check) and the patch
+    # plans without a device; P has more rows than columns, so its padding must point at column 0
+    assert vk.footprint(*key) > 0
