@@ -326,6 +326,102 @@ def run_vk(args, cfg):
     print(json.dumps(out), flush=True)
 
 
+def run_batch(args, cfg):
+    """cfg4: 16 right-hand sides per step through vk_solve_batch (FP32 V-cycle, BF16/FP16 patch
+    inverses on the tensor cores, FP64 FGMRES per column), against plain FP64 single solves."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    import paper_2409_14222_gb300 as vk
+    import synthetic_inputs as si
+    torch.cuda.set_device(0)
+    Nc, L, k, sweeps, rtol, desc = cfg
+    bp = vk.VK_BATCH_FP16 if args.batch_prec == "fp16" else vk.VK_BATCH_BF16
+    t0 = time.perf_counter()
+    G = vk.Hierarchy(Nc, L, k, options=vk.default_options(sweeps=sweeps, batch_prec=bp))
+    setup_s = time.perf_counter() - t0
+    n = G.ndof()
+    stream = torch.cuda.current_stream()
+    nb = args.warmup + args.steps
+    Bs = [torch.from_numpy(si.rhs_batch(n, range(16 * i, 16 * i + 16)).T.copy()).cuda() for i in range(min(nb, 4))]
+    X = torch.zeros(16, n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for w in range(args.warmup):
+        G.solve_batch(Bs[w % len(Bs)], X, rtol=rtol)
+    torch.cuda.synchronize()
+    G.stats_reset(time_kernels=False)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters = []
+    with ClockSampler(0) as clk:
+        torch.cuda.profiler.start()
+        for st in range(args.steps):
+            flush.fill_(float(st))
+            ev[st][0].record(stream)
+            out = G.solve_batch(Bs[st % len(Bs)], X, rtol=rtol)
+            ev[st][1].record(stream)
+            iters += [o["iterations"] for o in out]
+            if not all(o["converged"] for o in out):
+                raise RuntimeError("a column did not converge")
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    stt = G.stats()
+    times_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(times_ms) / 1e3
+    value = 16 * args.steps / total_s
+    # tensor-core patch apply, finest level: CUDA events around every launch of the same solves
+    G.stats_reset(time_kernels=True)
+    for st in range(min(args.steps, 3)):
+        G.solve_batch(Bs[st % len(Bs)], X, rtol=rtol)
+    torch.cuda.synchronize()
+    kt = G.stats()
+    G.stats_reset(time_kernels=False)
+    avg_s = kt["apply_ms"] / max(kt["apply_launches"], 1) / 1e3
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK))
+    gbs = kt["batch_apply_bytes"] / avg_s / 1e9
+    tflops = kt["batch_apply_flops"] / avg_s / 1e12
+    roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+            "kernel": f"k_patch_mma ({args.batch_prec.upper()} inverses x 16 right-hand sides, finest level)",
+            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})", "launch_avg_us": avg_s * 1e6,
+            "bytes_per_launch": kt["batch_apply_bytes"], "tensor_tflops": tflops,
+            "tensor_frac_of_bf16_peak": tflops / float(peaks.get("bf16_tflops", 1888.3))}
+    # plain FP64, one right-hand side at a time, same GPU and tolerance
+    G64 = vk.Hierarchy(Nc, L, k, options=vk.default_options(sweeps=sweeps))
+    x1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    B0 = Bs[0]
+    G64.solve(B0[0].contiguous(), x1, rtol=rtol)
+    torch.cuda.synchronize()
+    nf = min(args.steps, 8)
+    errs, t64 = [], 0.0
+    G.solve_batch(B0, X, rtol=rtol)
+    for r in range(nf):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(float(r))
+        e0.record(stream)
+        G64.solve(B0[r].contiguous(), x1, rtol=rtol, history=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 += e0.elapsed_time(e1) / 1e3
+        errs.append(float(torch.linalg.vector_norm(X[r] - x1) / torch.linalg.vector_norm(x1)))
+    fp64 = {"solves_per_s": nf / t64, "ms_per_solve": 1e3 * t64 / nf}
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": f"f64 FGMRES per column; f32 V-cycle; {args.batch_prec} patch inverses (tensor cores, f32 accumulate)",
+        "data": "synthetic",
+        "config": {"workload": desc + ", 16 right-hand sides per step", "ndof": n, "levels": L, "k": k,
+                   "rhs_per_step": 16, "rtol": rtol, "setup_s": setup_s,
+                   "l2": "256 MiB buffer overwritten between timed steps (outside the events)"},
+        "iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)), "max": int(max(iters))},
+        "vcycle_dof_per_s": 16 * n * stt["vcycles"] / total_s,
+        "latency_ms": {"p50": float(np.percentile(times_ms, 50)), "p99": float(np.percentile(times_ms, 99))},
+        "plain_fp64_single_rhs": fp64, "speedup_vs_plain_fp64": value / fp64["solves_per_s"],
+        "rel_error_vs_fp64_solution": {"max": max(errs), "mean": float(np.mean(errs)), "columns": nf},
+        "gpu_launches": int(stt["launches"]), "roofline": roof, "clocks": clk.summary(),
+    }), flush=True)
+
+
 def serve_pass(vk, srv, reqs, arrivals):
     """Submit reqs at the given arrival offsets (s) from one thread; collect results in order."""
     import threading
@@ -444,6 +540,7 @@ def main():
     ap.add_argument("--requests", type=int, default=1000, help="cfg5: requests in the 1x stream")
     ap.add_argument("--slots", type=int, default=4, help="cfg5: concurrent solves")
     ap.add_argument("--no-baseline", action="store_true", help="cfg5: skip the one-at-a-time FP64 pass")
+    ap.add_argument("--batch-prec", default="bf16", choices=["bf16", "fp16"], help="cfg4: 16-bit inverse format")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "vk":
         ap.error("--warmup must be >= 3")
@@ -452,6 +549,8 @@ def main():
         run_reference(args, cfg)
     elif args.config == "cfg5":
         run_serving(args)
+    elif args.config == "cfg4":
+        run_batch(args, cfg)
     else:
         run_vk(args, cfg)
 

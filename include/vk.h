@@ -56,6 +56,10 @@ extern "C" {
                           applied in FP32-pair arithmetic (exact product split + TwoSum accumulation)
                           on the FP32 pipes; relative accuracy about 1e-13; FP64 vectors            */
 
+#define VK_BATCH_NONE 0  /* no multi-right-hand-side support (vk_solve_batch refused)             */
+#define VK_BATCH_BF16 1  /* vk_solve_batch: FP32 V-cycle, BF16 scaled patch inverses on tensor cores */
+#define VK_BATCH_FP16 2  /* vk_solve_batch: FP32 V-cycle, FP16 scaled patch inverses on tensor cores */
+
 #define VK_CSR_A 0  /* level matrix script-A_l with Dirichlet identity rows and zeroed columns      */
 #define VK_CSR_P 1  /* prolongation from level l-1 to level l (ndof_l x ndof_{l-1})                 */
 #define VK_CSR_R 2  /* restriction R = P^T (ndof_{l-1} x ndof_l)                                     */
@@ -84,6 +88,9 @@ typedef struct vk_options {
   int32_t host_threads;/* threads for host assembly (0 = hardware concurrency)                      */
   int32_t host_only;   /* 1: build and keep the host-side hierarchy only (export calls, no solves)  */
   int32_t max_iterations; /* FGMRES basis size allocated at setup (100, the paper's cap, Sec. 4)   */
+  int32_t batch_prec;     /* VK_BATCH_*: build the multi-right-hand-side structures (needs FP64
+                             factor_prec: the 16-bit inverses are rounded from the FP64 ones)     */
+  int32_t batch_max_iterations; /* FGMRES basis size of vk_solve_batch (per right-hand side)       */
 } vk_options;
 
 /* Device memory provider.  alloc returns device memory of at least `bytes` (256-byte aligned) or
@@ -203,6 +210,18 @@ int vk_vcycle(vk_hierarchy* h, const double* b_dev, double* x_dev, void* stream)
 int vk_solve(vk_hierarchy* h, const double* b_dev, double* x_dev, double rtol, int maxit,
              vk_solve_info* info, void* stream);
 
+/* Solves A X = B for nrhs <= 16 right-hand sides at once (B, X: device, column-major, ndof x nrhs,
+ * leading dimension ldb >= ndof).  Each column is an independent FGMRES solve with the vk_solve
+ * semantics in FP64 (projection, CGS2, Givens, its own convergence test and iteration count); the
+ * V-cycle preconditioner runs on all columns together in FP32, with every patch solve of Algorithm 1
+ * applied as a small dense product on the tensor cores (BF16 or FP16 inverses scaled per patch,
+ * right-hand-side columns scaled separately, FP32 accumulation).  A column's result does not depend
+ * on the other columns.  Needs a hierarchy set up with batch_prec != VK_BATCH_NONE.  infos (host,
+ * nrhs entries, may be NULL) receive the per-column results; histories are not recorded.
+ * Returns VK_ERR_NOT_CONVERGED if a column reached maxit, VK_ERR_NONFINITE if a column diverged. */
+int vk_solve_batch(vk_hierarchy* h, int nrhs, const double* B_dev, int64_t ldb, double* X_dev, double rtol,
+                   int maxit, vk_solve_info* infos, void* stream);
+
 /* vk_solve with host buffers: copies b_host (ndof doubles) to the device, solves, copies x back to
  * x_host.  Both copies are issued on `stream`; the call returns after x_host is written. */
 int vk_solve_host(vk_hierarchy* h, const double* b_host, double* x_host, double rtol, int maxit,
@@ -234,10 +253,13 @@ typedef struct vk_stats {
                               s*sum(n_i^2) inverse entries (s = 8 FP64, 4 FP32) + 20*sum(n_i)
                               (DoF index, gathered residual, written correction) + 16 per patch     */
   double apply_flops;      /* 2*sum(n_i^2) flops of one finest-level patch-apply launch             */
+  double batch_apply_bytes;/* algorithmic bytes of one finest-level tensor-core patch apply of
+                              vk_solve_batch: 16-bit fragments as stored + 136*sum(n_i) + 28/patch   */
+  double batch_apply_flops;/* 32*sum(n_i^2) flops of that launch (16 right-hand sides)              */
 } vk_stats;
 
-/* Zeroes the counters; time_kernels = 1 also brackets every finest-level patch-apply launch with
- * CUDA events (recorded on the stream of the call that launches it). */
+/* Zeroes the counters; time_kernels = 1 also brackets every finest-level patch-apply launch (of
+ * vk_solve and of vk_solve_batch) with CUDA events recorded on the stream that launches it. */
 int vk_stats_reset(vk_hierarchy* h, int time_kernels);
 
 /* Reads the counters (waits for the recorded events). */

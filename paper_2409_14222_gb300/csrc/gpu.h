@@ -145,6 +145,34 @@ int fg_solution(const double* H, int ldh, const double* g, const double* Z, int6
                 double* y, double* x, int n, cudaStream_t s);
 int fg_finish(FgState* st, const double* sq, cudaStream_t s);                             // true_res = sqrt(*sq)
 
+// ---- multi-right-hand-side (kernels_batch.cu): 16 right-hand sides interleaved per DoF -----------
+template <typename T>
+int mm_csr(const Csr& A, const T* val, int mode, const T* b, const uint8_t* mask, const T* x, T* y, cudaStream_t s);
+int pack_mma(const Patches& P, const double* inv64, const int64_t* foff16, void* frag, float* ascale, bool half,
+             cudaStream_t s);
+int patch_apply_mma(const Patches& P, const int64_t* foff16, const void* frag, const float* ascale, bool half,
+                    int mt_max, const float* rhs, float* delta, cudaStream_t s);
+int scatter_mm(const Patches& P, int ndof, const uint8_t* dir, const float* r, const float* delta, int mode,
+               float theta, float c1, float c2, float* zout, float* d, float* x, cudaStream_t s);
+int coarse_mm(const float* Minv, int n, int ld, const float* B, float* X, cudaStream_t s);
+int to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+int to_f64(const float* a, double* b, int64_t n, cudaStream_t s);
+int gather_cols(const double* B, int64_t ld, int nrhs, double* Y, int n, cudaStream_t s);
+int scatter_cols(const double* Y, double* X, int64_t ld, int nrhs, int n, cudaStream_t s);
+// out[v*16 + r] = sum_rows X_v[row][r] W[row][r] for v < nvec (acc[.] += the same when not null)
+int mdot_mm(const double* X, int64_t ldx, int nvec, const double* W, int n, double* partial, double* out,
+            double* acc, cudaStream_t s);
+int maxpy_mm(const double* X, int64_t ldx, int nvec, const double* h, double* W, int n, cudaStream_t s);
+int project_mm(double* X, int lo, int len, double* partial, double* sum, cudaStream_t s);
+int normalize_mm(const double* W, const double* sq, const int* active, double* Y, int n, cudaStream_t s);
+int combine_mm(const double* Z, int64_t ldz, const int* m, const double* y, int ldy, double* X, int n,
+               cudaStream_t s);
+int givens_mm(double* H, int ldh, int64_t hstride, double* cs, double* sn, double* g, double* hist,
+              const double* hcol, const double* hnrm, int j, double rtol, int* active, int* iters, int* nonfinite,
+              cudaStream_t s);
+// 16-bit fragment count (uint4 units) of an n x n patch: (ceil(n/16))^2 tiles of 32 lanes
+inline int64_t frag_size(int n) { return 32LL * ((n + 15) / 16) * ((n + 15) / 16); }
+
 // x = sum_i Z[i] y[i]
 int combine(const double* Z, int64_t ldz, int m, const double* y, double* x, int n, cudaStream_t s);
 // y = scale * x

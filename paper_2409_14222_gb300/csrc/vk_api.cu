@@ -220,6 +220,14 @@ struct DevLevel {
   double lam = 0.0;
   double *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *t = nullptr, *delta = nullptr;
   float2* r2 = nullptr;  // FP32-pair residual (emulated-FP64 inverses only)
+  // multi-right-hand-side structures (batch_prec != VK_BATCH_NONE)
+  vk::gpu::Csr Pc, Rc;                       // CSR transfers (FP64 values unused by the batch path)
+  float *aval_f = nullptr, *pval_f = nullptr, *rval_f = nullptr;
+  int64_t* foff16 = nullptr;
+  void* frag = nullptr;
+  float* ascale = nullptr;
+  int mt_max = 0;
+  float *bb = nullptr, *xb = nullptr, *rb = nullptr, *db = nullptr, *delta_f = nullptr;
 };
 
 }  // namespace
@@ -248,6 +256,7 @@ struct vk_hierarchy {
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
   double apply_bytes = 0.0, apply_flops = 0.0;
+  double bapply_bytes = 0.0, bapply_flops = 0.0;
   // graph-resident FGMRES (one CUDA graph per hierarchy: prologue, WHILE node, epilogue)
   vk::gpu::FgState* st = nullptr;        // device
   vk::gpu::FgState* h_par = nullptr;     // pinned: parameters written before each launch
@@ -259,6 +268,14 @@ struct vk_hierarchy {
   cudaGraphExec_t gexec = nullptr;
   cudaGraphConditionalHandle cond = 0;
   int64_t g_pro = 0, g_body = 0, g_epi = 0;   // kernels per prologue / iteration / epilogue
+  // vk_solve_batch workspace (finest level, FP64, 16 interleaved right-hand sides)
+  int kb = 0;
+  int64_t ldb = 0;
+  float* cinv_f = nullptr;
+  double *Vb = nullptr, *Zb = nullptr, *wb = nullptr, *xob = nullptr, *Hb = nullptr, *csb = nullptr, *snb = nullptr;
+  double *gb = nullptr, *histb = nullptr, *hcolb = nullptr, *t2b = nullptr, *partb = nullptr, *sqb = nullptr;
+  double* yb = nullptr;
+  int *activeb = nullptr, *itersb = nullptr, *nonfb = nullptr;
   ~vk_hierarchy() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -287,6 +304,12 @@ void validate(const vk_problem* p, const vk_options* o) {
   if (!(o->cheb_hi > o->cheb_lo) || !(o->cheb_lo > 0.0)) raise(VK_ERR_ARG, "bad Chebyshev interval");
   if (o->eig_steps < 1 || o->eig_steps > 64) raise(VK_ERR_ARG, "eig_steps must be in 1..64");
   if (o->max_iterations < 1 || o->max_iterations > 1000) raise(VK_ERR_ARG, "max_iterations must be in 1..1000");
+  if (o->batch_prec < VK_BATCH_NONE || o->batch_prec > VK_BATCH_FP16) raise(VK_ERR_ARG, "bad batch_prec");
+  if (o->batch_prec != VK_BATCH_NONE) {
+    if (o->factor_prec != VK_PREC_F64) raise(VK_ERR_ARG, "batch_prec needs FP64 factor_prec");
+    if (o->batch_max_iterations < 1 || o->batch_max_iterations > 1000)
+      raise(VK_ERR_ARG, "batch_max_iterations must be in 1..1000");
+  }
 }
 
 void build_host(vk_hierarchy* h) {
@@ -322,6 +345,73 @@ vk::gpu::Csr upload_csr(DeviceMemory& m, const vk::HostCsr& A) {
   c.col = m.upload(A.col);
   c.val = m.upload(A.val);
   return c;
+}
+
+// Multi-right-hand-side structures: FP32 copies of the matrices, CSR transfers, 16-bit patch
+// fragments, FP32 block vectors per level, the FP32 coarse inverse and the FP64 batched Krylov bases.
+void allocate_batch(vk_hierarchy* h) {
+  DeviceMemory& m = h->mem;
+  const int L = h->prob.nlevels;
+  constexpr int NR = 16;
+  auto f32 = [](const std::vector<double>& v) {
+    std::vector<float> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = float(v[i]);
+    return o;
+  };
+  for (int l = 0; l < L; ++l) {
+    const vk::HostLevel& H = h->host[l];
+    DevLevel& D = h->lv[l];
+    D.aval_f = m.upload(f32(H.A.val));
+    if (l > 0) {
+      D.Pc = upload_csr(m, H.P);
+      D.Rc = upload_csr(m, H.R);
+      D.pval_f = m.upload(f32(H.P.val));
+      D.rval_f = m.upload(f32(H.R.val));
+      const int np = int(H.patch_ptr.size()) - 1;
+      std::vector<int64_t> f16(np);
+      int64_t tot = 0;
+      int mt = 0;
+      for (int p = 0; p < np; ++p) {
+        const int n = H.patch_ptr[p + 1] - H.patch_ptr[p];
+        f16[p] = tot;
+        tot += vk::gpu::frag_size(n);
+        mt = std::max(mt, (n + 15) / 16);
+      }
+      if (mt > 8) raise(VK_ERR_ARG, "patches larger than 128 are not supported by the batched path");
+      D.mt_max = mt;
+      D.foff16 = m.upload(f16);
+      D.frag = m.get(size_t(tot) * 16);
+      D.ascale = m.get_n<float>(np);
+      D.delta_f = m.get_n<float>(size_t(H.patch_dofs.size()) * NR);
+    }
+    D.bb = m.get_n<float>(size_t(H.ndof) * NR);
+    D.xb = m.get_n<float>(size_t(H.ndof) * NR);
+    D.rb = m.get_n<float>(size_t(H.ndof) * NR);
+    D.db = m.get_n<float>(size_t(H.ndof) * NR);
+  }
+  const int mdim = h->nc + 1;
+  h->cinv_f = m.get_n<float>(size_t(mdim) * mdim);
+  const int nf = h->host[L - 1].ndof;
+  h->kb = h->opt.batch_max_iterations;
+  const int ldh = h->kb + 1;
+  h->ldb = int64_t(nf) * NR;
+  h->Vb = m.get_n<double>(size_t(h->ldb) * (h->kb + 1));
+  h->Zb = m.get_n<double>(size_t(h->ldb) * h->kb);
+  h->wb = m.get_n<double>(size_t(h->ldb));
+  h->xob = m.get_n<double>(size_t(h->ldb));
+  h->Hb = m.get_n<double>(size_t(NR) * ldh * h->kb);
+  h->csb = m.get_n<double>(size_t(NR) * ldh);
+  h->snb = m.get_n<double>(size_t(NR) * ldh);
+  h->gb = m.get_n<double>(size_t(NR) * ldh);
+  h->histb = m.get_n<double>(size_t(NR) * ldh);
+  h->hcolb = m.get_n<double>(size_t(NR) * ldh);
+  h->t2b = m.get_n<double>(size_t(NR) * ldh);
+  h->partb = m.get_n<double>(size_t(NR) * ldh * 256);
+  h->sqb = m.get_n<double>(4 * NR);
+  h->yb = m.get_n<double>(size_t(NR) * ldh);
+  h->activeb = m.get_n<int>(NR);
+  h->itersb = m.get_n<int>(NR);
+  h->nonfb = m.get_n<int>(NR);
 }
 
 // Allocates every device buffer (or only counts the bytes when mem.counting_only is set).
@@ -393,6 +483,7 @@ void allocate_device(vk_hierarchy* h) {
   h->zbuf = m.get_n<double>(nf);
   h->wbuf = m.get_n<double>(nf);
   h->st = m.get_n<vk::gpu::FgState>(1);
+  if (h->opt.batch_prec != VK_BATCH_NONE) allocate_batch(h);
 }
 
 // Finest-level patch applications are bracketed by CUDA events on their stream when timing is on.
@@ -553,6 +644,17 @@ void setup_device(vk_hierarchy* h, cudaStream_t s) {
     h->n_launch += vk::gpu::gauss_jordan_inverse(h->Cinv, mdim, perm, fcol, h->iflag + 14, h->iflag, s);
     CK(cudaGetLastError());
   }
+  if (h->opt.batch_prec != VK_BATCH_NONE) {
+    const bool half = h->opt.batch_prec == VK_BATCH_FP16;
+    for (int l = 1; l < L; ++l) {
+      DevLevel& D = h->lv[l];
+      h->n_launch += vk::gpu::pack_mma(D.pat, static_cast<const double*>(D.pat.factors), D.foff16, D.frag, D.ascale,
+                                       half, s);
+    }
+    const int64_t mm = int64_t(h->nc + 1) * (h->nc + 1);
+    h->n_launch += vk::gpu::to_f32(h->Cinv, h->cinv_f, mm, s);
+    CK(cudaGetLastError());
+  }
   std::vector<int> st(16);
   CK(cudaMemcpyAsync(st.data(), h->iflag, 16 * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -573,6 +675,14 @@ void setup_device(vk_hierarchy* h, cudaStream_t s) {
     // inverse entries + slot DoF indices + gathered r + written delta + per-patch work/offset/pointers
     h->apply_bytes = fsz * sn2 + 20.0 * sn + 16.0 * np;
     h->apply_flops = 2.0 * sn2;
+    if (h->opt.batch_prec != VK_BATCH_NONE) {
+      // 16-bit fragments (padded to 16x16 tiles, as stored) + per patch DoF index, 16 FP32 residual
+      // values gathered and 16 FP32 corrections written per slot + per-patch scale/offsets
+      double frag = 0.0;
+      for (int p = 0; p < np; ++p) frag += 16.0 * vk::gpu::frag_size(F.patch_ptr[p + 1] - F.patch_ptr[p]);
+      h->bapply_bytes = frag + (4.0 + 64.0 + 64.0 + 4.0) * sn + 28.0 * np;
+      h->bapply_flops = 2.0 * 16.0 * sn2;
+    }
   }
   h->lambdas.assign(L, 0.0);
   for (int l = 1; l < L; ++l) {
@@ -841,6 +951,178 @@ int solve_graph(vk_hierarchy* h, const double* b, double* x, double rtol, int ma
   return status;
 }
 
+// ---- multi-right-hand-side solve ----------------------------------------------------------------
+void smooth_b(vk_hierarchy* h, int l, const float* b, float* x, bool zero_init, cudaStream_t s) {
+  DevLevel& D = h->lv[l];
+  const bool half = h->opt.batch_prec == VK_BATCH_FP16;
+  const double lam = D.lam;
+  const double emax = h->opt.cheb_hi * lam, emin = h->opt.cheb_lo * lam;
+  const double theta = 0.5 * (emax + emin), delta = 0.5 * (emax - emin);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  for (int step = 0; step < h->opt.sweeps; ++step) {
+    const float* rr = b;
+    if (!(step == 0 && zero_init)) {
+      h->n_launch += vk::gpu::mm_csr<float>(D.Acsr, D.aval_f, 0, b, nullptr, x, D.rb, s);
+      rr = D.rb;
+    }
+    const bool t = h->time_apply && l == h->prob.nlevels - 1;
+    if (t) {
+      if (h->ev_used + 2 > h->ev.size())
+        for (int i = 0; i < 64; ++i) {
+          cudaEvent_t e;
+          CK(cudaEventCreate(&e));
+          h->ev.push_back(e);
+        }
+      CK(cudaEventRecord(h->ev[h->ev_used], s));
+    }
+    h->n_launch += vk::gpu::patch_apply_mma(D.pat, D.foff16, D.frag, D.ascale, half, D.mt_max, rr, D.delta_f, s);
+    if (t) {
+      CK(cudaEventRecord(h->ev[h->ev_used + 1], s));
+      h->ev_used += 2;
+    }
+    int mode;
+    double c1 = 0.0, c2 = 0.0;
+    if (step == 0) {
+      mode = zero_init ? 1 : 2;
+    } else {
+      const double rho_new = 1.0 / (2.0 * sigma - rho);
+      c1 = rho_new * rho;
+      c2 = 2.0 * rho_new / delta;
+      rho = rho_new;
+      mode = 3;
+    }
+    h->n_launch += vk::gpu::scatter_mm(D.pat, D.ndof, D.dir, rr, D.delta_f, mode, float(theta), float(c1), float(c2),
+                                       nullptr, D.db, x, s);
+  }
+}
+
+void vcycle_b(vk_hierarchy* h, int l, const float* b, float* x, cudaStream_t s) {
+  if (l == 0) {
+    h->n_launch += vk::gpu::coarse_mm(h->cinv_f, h->nc, h->nc + 1, b, x, s);
+    return;
+  }
+  DevLevel& D = h->lv[l];
+  DevLevel& C = h->lv[l - 1];
+  smooth_b(h, l, b, x, true, s);
+  h->n_launch += vk::gpu::mm_csr<float>(D.Acsr, D.aval_f, 0, b, nullptr, x, D.rb, s);
+  h->n_launch += vk::gpu::mm_csr<float>(D.Rc, D.rval_f, 3, nullptr, C.dir, D.rb, C.bb, s);
+  vcycle_b(h, l - 1, C.bb, C.xb, s);
+  h->n_launch += vk::gpu::mm_csr<float>(D.Pc, D.pval_f, 2, x, nullptr, C.xb, x, s);
+  smooth_b(h, l, b, x, false, s);
+}
+
+int solve_batch_impl(vk_hierarchy* h, int nrhs, const double* B, int64_t ldb, double* X, double rtol, int maxit,
+                     vk_solve_info* infos, cudaStream_t s) {
+  check_device(h);
+  if (h->opt.batch_prec == VK_BATCH_NONE) raise(VK_ERR_ARG, "hierarchy built without batch_prec");
+  constexpr int NR = 16;
+  if (nrhs < 1 || nrhs > NR) raise(VK_ERR_ARG, "nrhs must be in 1..16");
+  if (maxit < 1 || maxit > h->kb) raise(VK_ERR_ARG, "maxit must be in 1..batch_max_iterations");
+  if (!B || !X) raise(VK_ERR_ARG, "null block vector");
+  const auto t0 = std::chrono::steady_clock::now();
+  const int L = h->prob.nlevels;
+  DevLevel& F = h->lv[L - 1];
+  const int n = F.ndof;
+  if (ldb < n) raise(VK_ERR_ARG, "ldb < ndof");
+  const int64_t ld = h->ldb;
+  const int ldh = h->kb + 1;
+  const int64_t hstride = int64_t(ldh) * h->kb;
+  // b_hat per column, beta, v_1
+  h->n_launch += vk::gpu::gather_cols(B, ldb, nrhs, h->wb, n, s);
+  h->n_launch += vk::gpu::project_mm(h->wb, F.n_u, F.n_p, h->partb, h->sqb + NR, s);
+  h->n_launch += vk::gpu::mdot_mm(h->wb, 0, 1, h->wb, n, h->partb, h->sqb, nullptr, s);
+  std::vector<double> sq(NR), beta(NR);
+  CK(cudaMemcpyAsync(sq.data(), h->sqb, NR * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<int> active(NR, 0), zeros(NR, 0);
+  std::vector<double> g0(size_t(NR) * ldh, 0.0);
+  bool bad_rhs = false;
+  for (int r = 0; r < NR; ++r) {
+    beta[r] = std::sqrt(sq[r]);
+    if (r < nrhs && !std::isfinite(beta[r])) bad_rhs = true;
+    active[r] = (r < nrhs && beta[r] > 0.0 && std::isfinite(beta[r])) ? 1 : 0;
+    g0[size_t(r) * ldh] = beta[r];
+  }
+  if (bad_rhs) raise(VK_ERR_NONFINITE, "a right-hand side is not finite");
+  CK(cudaMemcpyAsync(h->activeb, active.data(), NR * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->itersb, zeros.data(), NR * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->nonfb, zeros.data(), NR * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->gb, g0.data(), g0.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->histb, g0.data(), g0.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  h->n_launch += vk::gpu::normalize_mm(h->wb, h->sqb, h->activeb, h->Vb, n, s);
+  std::vector<int> act(NR);
+  for (int j = 0; j < maxit && std::count(active.begin(), active.end(), 1) > 0; ++j) {
+    double* vj = h->Vb + ld * j;
+    double* zj = h->Zb + ld * j;
+    h->n_launch += vk::gpu::to_f32(vj, F.bb, ld, s);
+    vcycle_b(h, L - 1, F.bb, F.xb, s);
+    ++h->n_vcycle;
+    h->n_launch += vk::gpu::to_f64(F.xb, zj, ld, s);
+    h->n_launch += vk::gpu::project_mm(zj, F.n_u, F.n_p, h->partb, h->sqb + NR, s);
+    h->n_launch += vk::gpu::mm_csr<double>(F.Acsr, F.Acsr.val, 1, nullptr, nullptr, zj, h->wb, s);
+    h->n_launch += vk::gpu::mdot_mm(h->Vb, ld, j + 1, h->wb, n, h->partb, h->hcolb, nullptr, s);
+    h->n_launch += vk::gpu::maxpy_mm(h->Vb, ld, j + 1, h->hcolb, h->wb, n, s);
+    h->n_launch += vk::gpu::mdot_mm(h->Vb, ld, j + 1, h->wb, n, h->partb, h->t2b, h->hcolb, s);
+    h->n_launch += vk::gpu::maxpy_mm(h->Vb, ld, j + 1, h->t2b, h->wb, n, s);
+    h->n_launch += vk::gpu::mdot_mm(h->wb, 0, 1, h->wb, n, h->partb, h->sqb, nullptr, s);
+    h->n_launch += vk::gpu::givens_mm(h->Hb, ldh, hstride, h->csb, h->snb, h->gb, h->histb, h->hcolb, h->sqb, j, rtol,
+                                      h->activeb, h->itersb, h->nonfb, s);
+    h->n_launch += vk::gpu::normalize_mm(h->wb, h->sqb, h->activeb, h->Vb + ld * (j + 1), n, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(act.data(), h->activeb, NR * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    active = act;
+  }
+  // per-column solutions
+  std::vector<int> iters(NR), nonf(NR);
+  std::vector<double> Hh(size_t(NR) * hstride), gh(size_t(NR) * ldh), hist(size_t(NR) * ldh);
+  CK(cudaMemcpyAsync(iters.data(), h->itersb, NR * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(nonf.data(), h->nonfb, NR * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(Hh.data(), h->Hb, Hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(gh.data(), h->gb, gh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hist.data(), h->histb, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<double> y(size_t(NR) * ldh, 0.0);
+  for (int r = 0; r < NR; ++r) {
+    const int mr = iters[r];
+    const double* Hr = Hh.data() + size_t(r) * hstride;
+    for (int i = mr - 1; i >= 0; --i) {
+      double acc = gh[size_t(r) * ldh + i];
+      for (int k = i + 1; k < mr; ++k) acc -= Hr[size_t(k) * ldh + i] * y[size_t(r) * ldh + k];
+      y[size_t(r) * ldh + i] = acc / Hr[size_t(i) * ldh + i];
+    }
+  }
+  CK(cudaMemcpyAsync(h->yb, y.data(), y.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  h->n_launch += vk::gpu::combine_mm(h->Zb, ld, h->itersb, h->yb, ldh, h->xob, n, s);
+  // true residuals of the projected systems
+  h->n_launch += vk::gpu::gather_cols(B, ldb, nrhs, h->wb, n, s);
+  h->n_launch += vk::gpu::project_mm(h->wb, F.n_u, F.n_p, h->partb, h->sqb + NR, s);
+  h->n_launch += vk::gpu::mm_csr<double>(F.Acsr, F.Acsr.val, 0, h->wb, nullptr, h->xob, h->Zb, s);
+  h->n_launch += vk::gpu::mdot_mm(h->Zb, 0, 1, h->Zb, n, h->partb, h->sqb, nullptr, s);
+  h->n_launch += vk::gpu::scatter_cols(h->xob, X, ldb, nrhs, n, s);
+  CK(cudaMemcpyAsync(sq.data(), h->sqb, NR * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int status = VK_OK;
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (int r = 0; r < nrhs; ++r) {
+    const bool conv = beta[r] == 0.0 || (!nonf[r] && hist[size_t(r) * ldh + iters[r]] <= rtol * beta[r]);
+    if (nonf[r]) status = VK_ERR_NONFINITE;
+    else if (!conv && status == VK_OK) status = VK_ERR_NOT_CONVERGED;
+    if (infos) {
+      infos[r].iterations = iters[r];
+      infos[r].converged = conv ? 1 : 0;
+      infos[r].res0 = beta[r];
+      infos[r].res_est = hist[size_t(r) * ldh + iters[r]];
+      infos[r].true_res = std::sqrt(sq[r]);
+      infos[r].solve_ms = ms;
+    }
+  }
+  if (status == VK_ERR_NONFINITE) g_err = "a column's residual estimate is not finite";
+  if (status == VK_ERR_NOT_CONVERGED) g_err = "a column did not reach rtol in maxit iterations";
+  return status;
+}
+
 const vk::HostCsr& pick_csr(const vk_hierarchy* h, int level, int which) {
   const vk::HostLevel& L = h->host[level];
   if (which == VK_CSR_A) return L.A;
@@ -869,6 +1151,8 @@ void vk_default_options(vk_options* o) {
   o->host_threads = 0;
   o->host_only = 0;
   o->max_iterations = 100;
+  o->batch_prec = VK_BATCH_NONE;
+  o->batch_max_iterations = 60;
 }
 
 const char* vk_last_error(void) { return g_err.c_str(); }
@@ -1048,6 +1332,11 @@ int vk_solve(vk_hierarchy* h, const double* b, double* x, double rtol, int maxit
   return guard([&] { return solve_impl(h, b, x, rtol, maxit, info, static_cast<cudaStream_t>(stream)); });
 }
 
+int vk_solve_batch(vk_hierarchy* h, int nrhs, const double* B, int64_t ldb, double* X, double rtol, int maxit,
+                   vk_solve_info* infos, void* stream) {
+  return guard([&] { return solve_batch_impl(h, nrhs, B, ldb, X, rtol, maxit, infos, static_cast<cudaStream_t>(stream)); });
+}
+
 int vk_solve_host(vk_hierarchy* h, const double* b_host, double* x_host, double rtol, int maxit,
                   vk_solve_info* info, void* stream) {
   return guard([&] {
@@ -1138,6 +1427,8 @@ int vk_stats_read(vk_hierarchy* h, vk_stats* out) {
     out->apply_ms = ms;
     out->apply_bytes = h->apply_bytes;
     out->apply_flops = h->apply_flops;
+    out->batch_apply_bytes = h->bapply_bytes;
+    out->batch_apply_flops = h->bapply_flops;
     return VK_OK;
   });
 }

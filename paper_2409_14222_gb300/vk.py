@@ -27,6 +27,7 @@ VK_PREC_F64 = 0
 VK_PREC_F32 = 1
 VK_PREC_F64E = 2
 VK_CSR_A, VK_CSR_P, VK_CSR_R = 0, 1, 2
+VK_BATCH_NONE, VK_BATCH_BF16, VK_BATCH_FP16 = 0, 1, 2
 
 STATUS_NAMES = {0: "VK_OK", 1: "VK_ERR_ARG", 2: "VK_ERR_NO_MEMORY", 3: "VK_ERR_SINGULAR",
                 4: "VK_ERR_NONFINITE", 5: "VK_ERR_NOT_CONVERGED", 6: "VK_ERR_TIMEOUT", 7: "VK_ERR_CUDA",
@@ -38,7 +39,7 @@ SYMBOLS = [
     "vk_level_info", "vk_lambda", "vk_residual", "vk_vanka", "vk_smooth", "vk_restrict", "vk_prolong",
     "vk_coarse_solve", "vk_vcycle", "vk_solve", "vk_solve_host", "vk_csr_dims", "vk_export_csr",
     "vk_export_patches", "vk_export_dirichlet", "vk_hessenberg_eigenvalues", "vk_stats_reset", "vk_stats_read",
-    "vk_vanka_noalloc", "vk_default_server_config", "vk_server_create", "vk_server_submit", "vk_server_wait",
+    "vk_vanka_noalloc", "vk_solve_batch", "vk_default_server_config", "vk_server_create", "vk_server_submit", "vk_server_wait",
     "vk_server_get_stats", "vk_server_destroy",
 ]
 
@@ -59,7 +60,8 @@ class vk_options(ctypes.Structure):
                 ("cheb_hi", ctypes.c_double), ("eig_steps", ctypes.c_int32), ("eig_seed", ctypes.c_uint64),
                 ("lambdas", ctypes.POINTER(ctypes.c_double)), ("factor_prec", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("host_threads", ctypes.c_int32), ("host_only", ctypes.c_int32),
-                ("max_iterations", ctypes.c_int32)]
+                ("max_iterations", ctypes.c_int32), ("batch_prec", ctypes.c_int32),
+                ("batch_max_iterations", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -78,7 +80,8 @@ class vk_solve_info(ctypes.Structure):
 
 class vk_stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("vcycles", ctypes.c_int64), ("apply_launches", ctypes.c_int64),
-                ("apply_ms", ctypes.c_double), ("apply_bytes", ctypes.c_double), ("apply_flops", ctypes.c_double)]
+                ("apply_ms", ctypes.c_double), ("apply_bytes", ctypes.c_double), ("apply_flops", ctypes.c_double),
+                ("batch_apply_bytes", ctypes.c_double), ("batch_apply_flops", ctypes.c_double)]
 
 
 class vk_server_config(ctypes.Structure):
@@ -134,6 +137,7 @@ def lib():
             "vk_vcycle": (I, [H, VP, VP, VP]),
             "vk_solve": (I, [H, VP, VP, D, I, P(vk_solve_info), VP]),
             "vk_solve_host": (I, [H, VP, VP, D, I, P(vk_solve_info), VP]),
+            "vk_solve_batch": (I, [H, I, VP, I64, VP, D, I, P(vk_solve_info), VP]),
             "vk_csr_dims": (I, [H, I, I, P(ctypes.c_int32), P(ctypes.c_int32), P(I64)]),
             "vk_export_csr": (I, [H, I, I, VP, VP, VP]),
             "vk_export_patches": (I, [H, I, VP, VP, VP]),
@@ -350,6 +354,17 @@ class Hierarchy:
         if code != VK_OK and not (code == VK_ERR_NOT_CONVERGED and not raise_on_nonconv):
             check(code)
         return self._result(info, hist, code)
+
+    def solve_batch(self, B, X, rtol=1e-8, maxit=60, stream=None):
+        """vk_solve_batch on column-major device blocks: B, X are (nrhs, ndof) contiguous tensors
+        (row r = right-hand side r, i.e. column-major ndof x nrhs).  Returns a list of per-column dicts."""
+        nrhs, n = B.shape
+        infos = (vk_solve_info * nrhs)()
+        code = lib().vk_solve_batch(self.handle, nrhs, _ptr(B), n, _ptr(X), float(rtol), int(maxit), infos,
+                                    _stream_handle(stream))
+        if code not in (VK_OK, VK_ERR_NOT_CONVERGED):
+            check(code)
+        return [self._result(infos[r], None, code) for r in range(nrhs)]
 
     def solve_host(self, b_host, x_host, rtol=1e-8, maxit=100, stream=None, history=False):
         info, hist = self._info(maxit, history)
