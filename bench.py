@@ -56,6 +56,29 @@ def recorded_traffic(config, prec):
     return float(rec["dram_bytes_per_launch"])
 
 
+def spmv_roofline(kt, key, hbm, peak_kind, kernel):
+    """HBM roofline of the finest-level V-cycle residual SpMV from the CUDA events around each launch."""
+    n = int(kt["spmv_launches"])
+    if n == 0:
+        return None
+    avg_s = kt["spmv_ms"] / n / 1e3
+    gbs = kt[key] / avg_s / 1e9
+    return {"kernel": kernel, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+            "launch_avg_us": avg_s * 1e6, "bytes_per_launch": kt[key], "launches_timed": n,
+            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+
+
+def schedules(G, L):
+    """Launch shape the setup autotuner chose for the patch application of each smoothed level."""
+    out = {}
+    for l in range(1, L):
+        sc = G.apply_schedule(l)
+        us = [u for u in sc["cand_us"] if u > 0]
+        out[f"level{l}"] = {"split": sc["split"], "threads": sc["threads"], "per_sm": sc["per_sm"],
+                            "best_us": min(us) if us else None, "worst_us": max(us) if us else None}
+    return out
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -297,6 +320,7 @@ def run_vk(args, cfg):
     roof["launch_avg_us"] = apply_avg_s * 1e6
     roof["bytes_per_launch"] = kt["apply_bytes"]
     roof["launches_timed"] = int(kt["apply_launches"])
+    roof["spmv"] = spmv_roofline(kt, "spmv_bytes", hbm, peak_kind, "k_sell residual r = b - A x (finest level, FP64)")
     cpu = None
     if not args.no_cpu_baseline:
         cpu = oracle_cpu_baseline(cfg)
@@ -312,7 +336,8 @@ def run_vk(args, cfg):
                    "factor_prec": args.prec, "fgmres_loop": "host" if args.no_graph else "CUDA graph (WHILE node)",
                    "rhs": "N(0,1), numpy default_rng(seed)",
                    "l2": "256 MiB buffer overwritten between timed solves (outside the per-solve events)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "apply_schedule": schedules(G, L)},
         "vcycle_dof_per_s": world * ndof * vcycles / total_s,
         "iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)), "max": int(max(iters))},
         "latency_ms": {"p50": float(np.percentile(times_ms, 50)), "p99": float(np.percentile(times_ms, 99))},
@@ -338,7 +363,11 @@ def run_batch(args, cfg):
     Nc, L, k, sweeps, rtol, desc = cfg
     bp = vk.VK_BATCH_FP16 if args.batch_prec == "fp16" else vk.VK_BATCH_BF16
     t0 = time.perf_counter()
-    G = vk.Hierarchy(Nc, L, k, options=vk.default_options(sweeps=sweeps, batch_prec=bp))
+    engines = {"tcgen05": vk.VK_ENGINE_TCGEN05, "mma_sync": vk.VK_ENGINE_MMA_SYNC}
+    other = "mma_sync" if args.engine == "tcgen05" else "tcgen05"
+    G = vk.Hierarchy(Nc, L, k, options=vk.default_options(sweeps=sweeps, batch_prec=bp,
+                                                             batch_engine=engines[args.engine],
+                                                             batch_max_iterations=args.batch_maxit))
     setup_s = time.perf_counter() - t0
     n = G.ndof()
     stream = torch.cuda.current_stream()
@@ -347,7 +376,7 @@ def run_batch(args, cfg):
     X = torch.zeros(16, n, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for w in range(args.warmup):
-        G.solve_batch(Bs[w % len(Bs)], X, rtol=rtol)
+        G.solve_batch(Bs[w % len(Bs)], X, rtol=rtol, maxit=args.batch_maxit)
     torch.cuda.synchronize()
     G.stats_reset(time_kernels=False)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -357,7 +386,7 @@ def run_batch(args, cfg):
         for st in range(args.steps):
             flush.fill_(float(st))
             ev[st][0].record(stream)
-            out = G.solve_batch(Bs[st % len(Bs)], X, rtol=rtol)
+            out = G.solve_batch(Bs[st % len(Bs)], X, rtol=rtol, maxit=args.batch_maxit)
             ev[st][1].record(stream)
             iters += [o["iterations"] for o in out]
             if not all(o["converged"] for o in out):
@@ -371,7 +400,7 @@ def run_batch(args, cfg):
     # tensor-core patch apply, finest level: CUDA events around every launch of the same solves
     G.stats_reset(time_kernels=True)
     for st in range(min(args.steps, 3)):
-        G.solve_batch(Bs[st % len(Bs)], X, rtol=rtol)
+        G.solve_batch(Bs[st % len(Bs)], X, rtol=rtol, maxit=args.batch_maxit)
     torch.cuda.synchronize()
     kt = G.stats()
     G.stats_reset(time_kernels=False)
@@ -381,10 +410,39 @@ def run_batch(args, cfg):
     gbs = kt["batch_apply_bytes"] / avg_s / 1e9
     tflops = kt["batch_apply_flops"] / avg_s / 1e12
     roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
-            "kernel": f"k_patch_mma ({args.batch_prec.upper()} inverses x 16 right-hand sides, finest level)",
+            "kernel": (f"{'k_patch_tc (tcgen05' if args.engine == 'tcgen05' else 'k_patch_mma (mma.sync'}; "
+                       f"{args.batch_prec.upper()} inverses x 16 right-hand sides, finest level)"),
             "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})", "launch_avg_us": avg_s * 1e6,
             "bytes_per_launch": kt["batch_apply_bytes"], "tensor_tflops": tflops,
-            "tensor_frac_of_bf16_peak": tflops / float(peaks.get("bf16_tflops", 1888.3))}
+            "tensor_frac_of_bf16_peak": tflops / float(peaks.get("bf16_tflops", 1888.3)),
+            "spmv": spmv_roofline(kt, "batch_spmv_bytes", hbm, peak_kind,
+                                  "k_mm block residual R = B - A X (finest level, FP32, 16 right-hand sides)")}
+    # the same solves with the other tensor-core engine (tcgen05 with TMEM and TMA, or warp-level mma.sync)
+    Gm = vk.Hierarchy(Nc, L, k, options=vk.default_options(sweeps=sweeps, batch_prec=bp,
+                                                              batch_engine=engines[other],
+                                                              batch_max_iterations=args.batch_maxit))
+    Xm = torch.zeros_like(X)
+    Gm.solve_batch(Bs[0], Xm, rtol=rtol, maxit=args.batch_maxit)
+    torch.cuda.synchronize()
+    nm = min(args.steps, 3)
+    tm = 0.0
+    for st in range(nm):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(float(st))
+        e0.record(stream)
+        Gm.solve_batch(Bs[st % len(Bs)], Xm, rtol=rtol, maxit=args.batch_maxit)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tm += e0.elapsed_time(e1) / 1e3
+    Gm.stats_reset(time_kernels=True)
+    Gm.solve_batch(Bs[0], Xm, rtol=rtol, maxit=args.batch_maxit)
+    torch.cuda.synchronize()
+    km = Gm.stats()
+    am = km["apply_ms"] / max(km["apply_launches"], 1) / 1e3
+    other_engine = {"engine": other, "solves_per_s": 16 * nm / tm, "patch_apply_us": am * 1e6,
+                "patch_apply_gbs": km["batch_apply_bytes"] / am / 1e9,
+                "bytes_per_launch": km["batch_apply_bytes"]}
+    del Gm, Xm
     # plain FP64, one right-hand side at a time, same GPU and tolerance
     G64 = vk.Hierarchy(Nc, L, k, options=vk.default_options(sweeps=sweeps))
     x1 = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -393,7 +451,7 @@ def run_batch(args, cfg):
     torch.cuda.synchronize()
     nf = min(args.steps, 8)
     errs, t64 = [], 0.0
-    G.solve_batch(B0, X, rtol=rtol)
+    G.solve_batch(B0, X, rtol=rtol, maxit=args.batch_maxit)
     for r in range(nf):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         flush.fill_(float(r))
@@ -404,11 +462,25 @@ def run_batch(args, cfg):
         t64 += e0.elapsed_time(e1) / 1e3
         errs.append(float(torch.linalg.vector_norm(X[r] - x1) / torch.linalg.vector_norm(x1)))
     fp64 = {"solves_per_s": nf / t64, "ms_per_solve": 1e3 * t64 / nf}
+    # FP64 single-right-hand-side kernels at this size: CUDA events around the finest patch apply and
+    # the finest residual SpMV (host-driven FGMRES loop, same kernels and launch shapes)
+    G64.stats_reset(time_kernels=True)
+    G64.solve(B0[0].contiguous(), x1, rtol=rtol, history=False)
+    torch.cuda.synchronize()
+    k64 = G64.stats()
+    G64.stats_reset(time_kernels=False)
+    a64 = k64["apply_ms"] / max(k64["apply_launches"], 1) / 1e3
+    fp64["patch_apply"] = {"kernel": "k_patch_apply (finest level, FP64 inverses)", "launch_avg_us": a64 * 1e6,
+                           "tflops": k64["apply_flops"] / a64 / 1e12,
+                           "frac_of_fp64_nominal": k64["apply_flops"] / a64 / 1e9 / FP64_NOMINAL_GFLOPS,
+                           "hbm_gbs": k64["apply_bytes"] / a64 / 1e9}
+    fp64["spmv"] = spmv_roofline(k64, "spmv_bytes", hbm, peak_kind, "k_sell residual r = b - A x (finest level, FP64)")
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": f"f64 FGMRES per column; f32 V-cycle; {args.batch_prec} patch inverses (tensor cores, f32 accumulate)",
+        "engine": args.engine,
         "data": "synthetic",
         "config": {"workload": desc + ", 16 right-hand sides per step", "ndof": n, "levels": L, "k": k,
                    "rhs_per_step": 16, "rtol": rtol, "setup_s": setup_s,
@@ -417,6 +489,7 @@ def run_batch(args, cfg):
         "vcycle_dof_per_s": 16 * n * stt["vcycles"] / total_s,
         "latency_ms": {"p50": float(np.percentile(times_ms, 50)), "p99": float(np.percentile(times_ms, 99))},
         "plain_fp64_single_rhs": fp64, "speedup_vs_plain_fp64": value / fp64["solves_per_s"],
+        "other_engine": other_engine,
         "rel_error_vs_fp64_solution": {"max": max(errs), "mean": float(np.mean(errs)), "columns": nf},
         "gpu_launches": int(stt["launches"]), "roofline": roof, "clocks": clk.summary(),
     }), flush=True)
@@ -541,10 +614,22 @@ def main():
     ap.add_argument("--slots", type=int, default=4, help="cfg5: concurrent solves")
     ap.add_argument("--no-baseline", action="store_true", help="cfg5: skip the one-at-a-time FP64 pass")
     ap.add_argument("--batch-prec", default="bf16", choices=["bf16", "fp16"], help="cfg4: 16-bit inverse format")
+    ap.add_argument("--levels", type=int, default=0, help="override the level count (profiling variants only)")
+    ap.add_argument("--rtol", type=float, default=0.0, help="override the tolerance (profiling variants only)")
+    ap.add_argument("--batch-maxit", type=int, default=60, help="cfg4: FGMRES basis size per right-hand side")
+    ap.add_argument("--engine", default="mma_sync", choices=["tcgen05", "mma_sync"],
+                    help="cfg4: tensor-core instruction family of the patch solves")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "vk":
         ap.error("--warmup must be >= 3")
     cfg = CONFIGS[args.config]
+    if args.levels or args.rtol:
+        # a smaller or looser variant of a workload, for profiler captures (never a bench line)
+        Nc, L, k, sweeps, rtol, desc = cfg
+        L = args.levels or L
+        rtol = args.rtol or rtol
+        cfg = (Nc, L, k, sweeps, rtol, f"{desc.split(',')[0]}, {Nc}x{Nc} -> {Nc << (L - 1)}x{Nc << (L - 1)} "
+                                         f"({L} levels), rtol {rtol:g} [profiling variant]")
     if args.impl == "reference":
         run_reference(args, cfg)
     elif args.config == "cfg5":

@@ -60,6 +60,9 @@ extern "C" {
 #define VK_BATCH_BF16 1  /* vk_solve_batch: FP32 V-cycle, BF16 scaled patch inverses on tensor cores */
 #define VK_BATCH_FP16 2  /* vk_solve_batch: FP32 V-cycle, FP16 scaled patch inverses on tensor cores */
 
+#define VK_ENGINE_TCGEN05 0   /* vk_solve_batch patch solves: tcgen05.mma, TMEM accumulators, TMA loads   */
+#define VK_ENGINE_MMA_SYNC 1  /* the same contraction with warp-level mma.sync m16n8k16 (for comparison) */
+
 #define VK_CSR_A 0  /* level matrix script-A_l with Dirichlet identity rows and zeroed columns      */
 #define VK_CSR_P 1  /* prolongation from level l-1 to level l (ndof_l x ndof_{l-1})                 */
 #define VK_CSR_R 2  /* restriction R = P^T (ndof_{l-1} x ndof_l)                                     */
@@ -90,7 +93,12 @@ typedef struct vk_options {
   int32_t max_iterations; /* FGMRES basis size allocated at setup (100, the paper's cap, Sec. 4)   */
   int32_t batch_prec;     /* VK_BATCH_*: build the multi-right-hand-side structures (needs FP64
                              factor_prec: the 16-bit inverses are rounded from the FP64 ones)     */
-  int32_t batch_max_iterations; /* FGMRES basis size of vk_solve_batch (per right-hand side)       */
+  int32_t batch_max_iterations; /* FGMRES basis size of vk_solve_batch per right-hand side (<= 127) */
+  int32_t autotune;       /* 1: at setup, time every candidate launch shape of the patch application
+                             on each smoothed level and keep the fastest (vk_apply_schedule)      */
+  int32_t apply_schedule; /* -1: autotune (or the default shape when autotune = 0); >= 0: use that
+                             candidate on every level (candidates are listed at vk_apply_schedule) */
+  int32_t batch_engine;   /* VK_ENGINE_*: tensor-core instruction family of vk_solve_batch          */
 } vk_options;
 
 /* Device memory provider.  alloc returns device memory of at least `bytes` (256-byte aligned) or
@@ -116,7 +124,7 @@ typedef struct vk_solve_info {
 } vk_solve_info;
 
 /* Fills *o with the defaults used by the paper's setting: 1 sweep, plain weights, [0.25, 1.1],
- * 10 Arnoldi steps, FP64 factors, graphs on. */
+ * 10 Arnoldi steps, FP64 factors, graphs on, patch-apply autotuning on. */
 void vk_default_options(vk_options* o);
 
 /* Builds the hierarchy (Sec. 3): per level the assembled CSR saddle-point matrix (Sec. 3), the
@@ -150,6 +158,18 @@ int vk_device_bytes(const vk_hierarchy* h, size_t* bytes);
 /* Chebyshev eigenvalue estimate lambda of level `level` (>= 1): the largest real part of the Ritz
  * values of eig_steps Arnoldi steps on M^{-1} A (Sec. 3, "standard GMRES estimation"). */
 int vk_lambda(const vk_hierarchy* h, int level, double* lambda);
+
+/* Launch shape of the patch application on level `level` (>= 1), chosen at setup.  Patches of
+ * uneven size (boundary and interior vertex patches, edge and cell patches for k >= 3: Sec. 3.1) are
+ * applied either in one launch (split = 0; each warp dispatches on its patch's size) or in one launch
+ * per size class of ceil(n/4) (1-4, 5-10, 11-19, 20-32; split = 1); threads per block 128 or 256;
+ * per_sm = 0 launches one warp per patch, per_sm > 0 a persistent grid of per_sm blocks per SM.
+ * Candidate i is split = i / 6, threads = (i / 3) % 2 ? 256 : 128, per_sm = {0, 4, 8}[i % 3]
+ * (*ncand = 12 of them).  cand_us (host, *ncand doubles, may be NULL) receives each candidate's best
+ * time in microseconds from the autotuner (0 if it did not run).  The corrections are bit-identical
+ * for every shape. */
+int vk_apply_schedule(const vk_hierarchy* h, int level, int32_t* split, int32_t* threads, int32_t* per_sm,
+                      int32_t* index, double* cand_us, int32_t* ncand);
 
 /* r = b - A_level x  (CSR SpMV residual; Algorithm 1's local right-hand sides come from it). */
 int vk_residual(vk_hierarchy* h, int level, const double* b_dev, const double* x_dev, double* r_dev,
@@ -256,10 +276,17 @@ typedef struct vk_stats {
   double batch_apply_bytes;/* algorithmic bytes of one finest-level tensor-core patch apply of
                               vk_solve_batch: 16-bit fragments as stored + 136*sum(n_i) + 28/patch   */
   double batch_apply_flops;/* 32*sum(n_i^2) flops of that launch (16 right-hand sides)              */
+  int64_t spmv_launches;   /* finest-level V-cycle residual SpMV launches bracketed by CUDA events   */
+  double spmv_ms;          /* their summed event durations (ms)                                      */
+  double spmv_bytes;       /* algorithmic bytes of one finest-level residual r = b - A x (FP64):
+                              12*nnz (value, column) + 28*ndof (row index, b, x, r)                 */
+  double batch_spmv_bytes; /* the same for the 16-right-hand-side FP32 residual of vk_solve_batch:
+                              8*nnz + 4*ndof (row pointer) + 192*ndof (16 x b, x, r)               */
 } vk_stats;
 
-/* Zeroes the counters; time_kernels = 1 also brackets every finest-level patch-apply launch (of
- * vk_solve and of vk_solve_batch) with CUDA events recorded on the stream that launches it. */
+/* Zeroes the counters; time_kernels = 1 also brackets every finest-level patch-apply launch and
+ * every finest-level V-cycle residual SpMV (of vk_solve and of vk_solve_batch) with CUDA events
+ * recorded on the stream that launches it. */
 int vk_stats_reset(vk_hierarchy* h, int time_kernels);
 
 /* Reads the counters (waits for the recorded events). */

@@ -224,11 +224,15 @@ class FGMRESResult:
         self.x, self.iters, self.hist, self.true_res, self.converged = x, iters, hist, true_res, converged
 
 
-def fgmres(A_apply, prec, b, rtol, maxit, proj=lambda v: v):
-    """Right-preconditioned unrestarted FGMRES with zero initial guess and MGS orthogonalisation.
+def fgmres(A_apply, prec, b, rtol, maxit, proj=lambda v: v, orth="mgs"):
+    """Right-preconditioned unrestarted FGMRES with zero initial guess (Sec. 3, Sec. 4).
 
-    hist[0] = ||b||, hist[j] = Givens residual estimate after j iterations.  Stops at
-    hist[j] <= rtol * hist[0] or after maxit iterations."""
+    The paper does not fix the orthogonalisation: orth = "mgs" (modified Gram-Schmidt, the default)
+    or "cgs2" (classical Gram-Schmidt applied twice, each pass projecting against the whole basis
+    with one set of inner products).  hist[0] = ||b||, hist[j] = Givens residual estimate after j
+    iterations.  Stops at hist[j] <= rtol * hist[0] or after maxit iterations."""
+    if orth not in ("mgs", "cgs2"):
+        raise ValueError("orth must be 'mgs' or 'cgs2'")
     b = proj(b)
     beta = np.linalg.norm(b)
     n = len(b)
@@ -248,9 +252,16 @@ def fgmres(A_apply, prec, b, rtol, maxit, proj=lambda v: v):
         z = proj(prec(V[j]))
         Z.append(z)
         w = A_apply(z)
-        for i in range(j + 1):
-            H[i, j] = V[i] @ w
-            w = w - H[i, j] * V[i]
+        if orth == "mgs":
+            for i in range(j + 1):
+                H[i, j] = V[i] @ w
+                w = w - H[i, j] * V[i]
+        else:
+            Vj = np.array(V[:j + 1])
+            for _ in range(2):
+                h = Vj @ w
+                w = w - Vj.T @ h
+                H[:j + 1, j] += h
         H[j + 1, j] = np.linalg.norm(w)
         V.append(w / H[j + 1, j] if H[j + 1, j] != 0 else w)
         for i in range(j):
@@ -277,10 +288,10 @@ def fgmres(A_apply, prec, b, rtol, maxit, proj=lambda v: v):
     return FGMRESResult(x, m, hist, true_res, converged)
 
 
-def solve(H, b, rtol=1e-8, maxit=100):
+def solve(H, b, rtol=1e-8, maxit=100, orth="mgs"):
     """FGMRES preconditioned by one V-cycle on the finest level of hierarchy H."""
     fin = H.finest
-    return fgmres(lambda v: fin.A @ v, H.vcycle, b, rtol, maxit, lambda v: project(fin.space, v))
+    return fgmres(lambda v: fin.A @ v, H.vcycle, b, rtol, maxit, lambda v: project(fin.space, v), orth)
 
 
 def direct_solve(A, z, b):

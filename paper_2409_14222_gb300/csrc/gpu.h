@@ -31,6 +31,17 @@ struct Csr {
   const double* val = nullptr;
 };
 
+// Launch shape of a patch application: split = 0 applies every patch of the level in one launch
+// (each warp dispatches on its patch's size); split = 1 launches once per size class (ceil(n/4) in
+// 1-4, 5-10, 11-19, 20-32), each compiled for that class only.  threads = 128 or 256 per block;
+// per_sm = 0 gives one warp per patch, per_sm > 0 a persistent grid of per_sm blocks per SM whose
+// warps stride over the patches.  The corrections are bit-identical for every shape.
+struct ApplySched {
+  int split = 0;
+  int threads = 256;
+  int per_sm = 0;
+};
+
 // Patch data of one level.  Patches are processed in "work order" (by packed-tile class, largest
 // first); a work item is one warp.  slot_ptr / slot_dofs are in canonical patch order.
 struct Patches {
@@ -50,6 +61,10 @@ struct Patches {
   const int* dof_ptr = nullptr;     // ndof + 1
   const int* slot_pos = nullptr;    // nslots
   const double* weight = nullptr;   // per-DoF weight or nullptr (plain sum)
+  ApplySched sched;                 // launch shape used by patch_apply
+  int nsm = 152;                    // SMs of the device (persistent grids)
+  int cls_lo[4] = {0, 0, 0, 0};     // work-list range [cls_lo[c], cls_hi[c]) of size class c
+  int cls_hi[4] = {0, 0, 0, 0};
 };
 
 // ---- sparse / vector kernels (kernels_sparse.cu) -------------------------------------------------
@@ -80,6 +95,11 @@ int patch_factor(const Csr& A, const Patches& P, int prec, void* factors, int* s
 // delta[slot] = (A_i^{-1} r[idx_i]) for every patch (one launch for all patches of a level).  With
 // FP32-pair inverses r is first split into r2 (ndof float2) and delta holds FP32 pairs.
 int patch_apply(const Patches& P, const double* r, float2* r2, double* delta, cudaStream_t s);
+// The same with an explicit launch shape (the autotuner's candidates).
+int patch_apply_sched(const Patches& P, const ApplySched& sc, const double* r, float2* r2, double* delta,
+                      cudaStream_t s);
+// Upper bound of ceil(n/4) of size class c (0..3).
+constexpr int kApplyClassHi[4] = {4, 10, 19, 32};
 // Sum of the slot corrections into each DoF (+ Dirichlet identity), fused with the Chebyshev update:
 //   mode 0: z = M^{-1} r                   (out = z)
 //   mode 1: d = z / theta; x = d           (first step, zero initial guess)
@@ -146,8 +166,21 @@ int fg_solution(const double* H, int ldh, const double* g, const double* Z, int6
 int fg_finish(FgState* st, const double* sq, cudaStream_t s);                             // true_res = sqrt(*sq)
 
 // ---- multi-right-hand-side (kernels_batch.cu): 16 right-hand sides interleaved per DoF -----------
+// SELL-8 layout of a matrix for the 16-right-hand-side products (slices of 8 rows; entry m of row t
+// of slice w at sptr[w] + 8 m + t; rowof[8 w + t] = row, -1 past the end); values as FP32 and FP64.
+struct SellB {
+  int nrows = 0, nslices = 0;
+  const int64_t* sptr = nullptr;
+  const int* swidth = nullptr;
+  const int* col = nullptr;
+  const int* rowof = nullptr;
+  const float* valf = nullptr;
+  const double* vald = nullptr;
+};
+// y = b - A x (0), A x (1), b + A x (2), mask ? 0 : A x (3) on [n][16] blocks, values `val` of A
 template <typename T>
-int mm_csr(const Csr& A, const T* val, int mode, const T* b, const uint8_t* mask, const T* x, T* y, cudaStream_t s);
+int mm_sell(const SellB& A, const T* val, int mode, const T* b, const uint8_t* mask, const T* x, T* y,
+            cudaStream_t s);
 int pack_mma(const Patches& P, const double* inv64, const int64_t* foff16, void* frag, float* ascale, bool half,
              cudaStream_t s);
 int patch_apply_mma(const Patches& P, const int64_t* foff16, const void* frag, const float* ascale, bool half,
@@ -162,7 +195,10 @@ int scatter_cols(const double* Y, double* X, int64_t ld, int nrhs, int n, cudaSt
 // out[v*16 + r] = sum_rows X_v[row][r] W[row][r] for v < nvec (acc[.] += the same when not null)
 int mdot_mm(const double* X, int64_t ldx, int nvec, const double* W, int n, double* partial, double* out,
             double* acc, cudaStream_t s);
+// W -= sum_v X_v h_v
 int maxpy_mm(const double* X, int64_t ldx, int nvec, const double* h, double* W, int n, cudaStream_t s);
+// grid of the batched reductions (partial sums per block, summed in a fixed order)
+constexpr int kBatchBlocks = 608;
 int project_mm(double* X, int lo, int len, double* partial, double* sum, cudaStream_t s);
 int normalize_mm(const double* W, const double* sq, const int* active, double* Y, int n, cudaStream_t s);
 int combine_mm(const double* Z, int64_t ldz, const int* m, const double* y, int ldy, double* X, int n,
@@ -170,6 +206,33 @@ int combine_mm(const double* Z, int64_t ldz, const int* m, const double* y, int 
 int givens_mm(double* H, int ldh, int64_t hstride, double* cs, double* sn, double* g, double* hist,
               const double* hcol, const double* hnrm, int j, double rtol, int* active, int* iters, int* nonfinite,
               cudaStream_t s);
+// Tensor-core (tcgen05) patch solves for 16 right-hand sides (kernels_tc.cu).  Size classes of the
+// work list: n <= 40 (3 patches per MMA), n <= 64 (2), n <= 128 (1); each class is cut into groups
+// of that many patches, described by tables built at setup (see k_patch_tc).  Each patch's scaled
+// inverse is stored as ceil(n/8)^2 core matrices of 8x8 16-bit values in frag.
+struct TcClass {
+  int ngroups = 0;
+  const int* gdof = nullptr;     // [ngroups][G][K]
+  const int* gpos = nullptr;     // [ngroups][128]
+  const int4* gslot = nullptr;   // [ngroups][G]
+};
+struct TcPatches {
+  int nsm = 152;
+  TcClass cls[3];
+  const uint8_t* frag = nullptr;
+  const float* ascale = nullptr;
+};
+// Patches per group, K (padded patch size) and row-block count of class c.
+constexpr int kTcG[3] = {3, 2, 1}, kTcK[3] = {48, 64, 128}, kTcCap[3] = {40, 64, 128};
+// Bytes of one patch's core matrices.
+inline int64_t tc_bytes(int n) { return 128LL * ((n + 7) / 8) * ((n + 7) / 8); }
+// Pack the FP64 inverses into the core-matrix layout, scaled by 1 / ascale (from pack_mma).
+int pack_tc(const Patches& P, const double* inv64, const float* ascale, const int64_t* foff_tc, void* frag, bool half,
+            cudaStream_t s);
+// delta[slot][16] = unscaled A_i^{-1} R_i for every patch; *err = VK_ERR_TIMEOUT if a bounded wait
+// expired.  One launch per non-empty size class.
+int patch_apply_tc(const TcPatches& T, bool half, const float* rhs, float* delta, int* err, cudaStream_t s);
+
 // 16-bit fragment count (uint4 units) of an n x n patch: (ceil(n/16))^2 tiles of 32 lanes
 inline int64_t frag_size(int n) { return 32LL * ((n + 15) / 16) * ((n + 15) / 16); }
 

@@ -39,34 +39,95 @@ __device__ double block_sum_d(double v) {
   return v;
 }
 
-// ---- block SpMM, CSR, half-warp per row, lane = right-hand side ---------------------------------
-//   kMode 0: y = b - A x   1: y = A x   2: y = b + A x   3: y = mask ? 0 : A x
+// ---- block SpMM, SELL-8 (slices of 8 rows, rows sorted by length in windows) ---------------------
+//   kMode as k_mm.  Warp = one slice: lane 4 t + q owns row t of the slice and right-hand sides
+//   4q .. 4q+3, and walks all entries of its row in order (entry m of row t at sptr + 8 m + t, so a
+//   warp load of columns or values is 8 consecutive entries); the x rows of kU entries are loaded
+//   before their products, 8 rows x 64 (FP32) or 128 (FP64) contiguous bytes per load instruction.
+//   Padding entries have value 0 and a valid column.  Each row is summed in its CSR order, exactly
+//   like the sequential loop of k_mm.
+template <typename T>
+struct Vec4 {
+  T v[4];
+};
+__device__ __forceinline__ Vec4<float> ld4(const float* p) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  return {{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Vec4<double> ld4(const double* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return {{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ Vec4<float> ld4_plain(const float* p) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  return {{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Vec4<double> ld4_plain(const double* p) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *(reinterpret_cast<const double2*>(p) + 1);
+  return {{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(float* p, const Vec4<float>& a) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const Vec4<double>& a) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a.v[0], a.v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(a.v[2], a.v[3]);
+}
+
 template <typename T, int kMode>
-__global__ void __launch_bounds__(kT) k_mm(int nrows, const int* __restrict__ ptr, const int* __restrict__ col,
-                                           const T* __restrict__ val, const T* b, const uint8_t* __restrict__ mask,
-                                           const T* __restrict__ x, T* y) {
-  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
-  const int r = threadIdx.x & 15;
-  if (row >= nrows) return;
-  const int e0 = ptr[row], e1 = ptr[row + 1];
-  T acc = T(0);
-  int e = e0;
-  for (; e + 4 <= e1; e += 4) {
-    const int c0 = __ldg(col + e), c1 = __ldg(col + e + 1), c2 = __ldg(col + e + 2), c3 = __ldg(col + e + 3);
-    const T v0 = __ldg(val + e), v1 = __ldg(val + e + 1), v2 = __ldg(val + e + 2), v3 = __ldg(val + e + 3);
-    const T x0 = x[int64_t(c0) * kNR + r], x1 = x[int64_t(c1) * kNR + r];
-    const T x2 = x[int64_t(c2) * kNR + r], x3 = x[int64_t(c3) * kNR + r];
-    acc = fma(v0, x0, acc);
-    acc = fma(v1, x1, acc);
-    acc = fma(v2, x2, acc);
-    acc = fma(v3, x3, acc);
+__global__ void __launch_bounds__(kT) k_sell_mm(int nslices, const int64_t* __restrict__ sptr,
+                                                const int* __restrict__ sw, const int* __restrict__ col,
+                                                const T* __restrict__ val, const int* __restrict__ rowof,
+                                                const T* b, const uint8_t* __restrict__ mask,
+                                                const T* __restrict__ x, T* y) {
+  constexpr int kU = sizeof(T) == 4 ? 8 : 4;
+  const int warp = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= nslices) return;
+  const int t = lane >> 2, q = lane & 3;
+  const int row = rowof[warp * 8 + t];
+  const int w = sw[warp];
+  const int64_t base = sptr[warp] + t;
+  Vec4<T> acc = {{T(0), T(0), T(0), T(0)}};
+  int m = 0;
+  for (; m + kU <= w; m += kU) {
+    int c[kU];
+    T v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      c[u] = __ldg(col + base + 8 * int64_t(m + u));
+      v[u] = __ldg(val + base + 8 * int64_t(m + u));
+    }
+    Vec4<T> xv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) xv[u] = ld4(x + int64_t(c[u]) * kNR + 4 * q);
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc.v[e] = fma(v[u], xv[u].v[e], acc.v[e]);
   }
-  for (; e < e1; ++e) acc = fma(__ldg(val + e), x[int64_t(__ldg(col + e)) * kNR + r], acc);
-  const int64_t o = int64_t(row) * kNR + r;
-  if (kMode == 0) y[o] = b[o] - acc;
-  if (kMode == 1) y[o] = acc;
-  if (kMode == 2) y[o] = b[o] + acc;
-  if (kMode == 3) y[o] = mask[row] ? T(0) : acc;
+  for (; m < w; ++m) {
+    const int c = __ldg(col + base + 8 * int64_t(m));
+    const T v = __ldg(val + base + 8 * int64_t(m));
+    const Vec4<T> xv = ld4(x + int64_t(c) * kNR + 4 * q);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc.v[e] = fma(v, xv.v[e], acc.v[e]);
+  }
+  if (row < 0) return;
+  T* o = y + int64_t(row) * kNR + 4 * q;
+  Vec4<T> r;
+  if (kMode == 0 || kMode == 2) {
+    const Vec4<T> bb = ld4_plain(b + int64_t(row) * kNR + 4 * q);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) r.v[e] = kMode == 0 ? bb.v[e] - acc.v[e] : bb.v[e] + acc.v[e];
+  } else if (kMode == 1) {
+    r = acc;
+  } else {
+    const bool z = mask[row] != 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) r.v[e] = z ? T(0) : acc.v[e];
+  }
+  st4(o, r);
 }
 
 // ---- tensor-core patch apply --------------------------------------------------------------------
@@ -275,29 +336,64 @@ __global__ void __launch_bounds__(kT) k_scatter_mm(int ndof, const int* __restri
   }
 }
 
-// ---- coarse solve, FP32: X[n][16] = Minv[0:n,0:n] B[n][16], 32-row tiles, 64-wide k chunks ----------
-__global__ void __launch_bounds__(512) k_coarse_mm(const float* __restrict__ Minv, int n, int ld,
+// ---- coarse solve, FP32: X[n][16] = Minv[0:n,0:n] B[n][16] ------------------------------------
+// Block = 16 rows x 16 right-hand sides (thread (row, rhs)); k runs in chunks of 128: the A tile
+// (16 x 128, row-major rows of Minv, float4 loads) and the B tile (128 x 16) are staged in shared
+// memory, the next chunk's loads are issued into registers before the current chunk's products.
+constexpr int kCoarseRows = 16, kCoarseK = 128;
+__global__ void __launch_bounds__(256) k_coarse_mm(const float* __restrict__ Minv, int n, int ld,
                                                    const float* __restrict__ B, float* __restrict__ X) {
-  __shared__ float As[32][65];
-  __shared__ float Bs[64][kNR];
-  const int tid = threadIdx.x;             // 512 threads: 32 rows x 16 rhs
+  __shared__ float4 As[kCoarseRows][kCoarseK / 4 + 1];
+  __shared__ float Bs[kCoarseK][kNR];
+  const int tid = threadIdx.x;
   const int rl = tid >> 4, rr = tid & 15;
-  const int row0 = blockIdx.x * 32;
+  const int row0 = blockIdx.x * kCoarseRows;
+  // loader roles: 2 float4 of A (row tid / 16 ... ) and 2 float4 of B per thread and chunk
+  float4 pa[2], pb[2];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + 256 * u;                  // 0..511: A tile as 16 rows x 32 float4
+      const int ar = e >> 5, ac = (e & 31) * 4;
+      const int row = row0 + ar, k = k0 + ac;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (row < n) {
+        const float* src = Minv + int64_t(row) * ld + k;
+        if (k + 3 < n && (((reinterpret_cast<uintptr_t>(src)) & 15) == 0)) {
+          v = __ldg(reinterpret_cast<const float4*>(src));
+        } else {
+          v.x = k < n ? src[0] : 0.f;
+          v.y = k + 1 < n ? src[1] : 0.f;
+          v.z = k + 2 < n ? src[2] : 0.f;
+          v.w = k + 3 < n ? src[3] : 0.f;
+        }
+      }
+      pa[u] = v;
+      const int bk = e >> 2, bq = (e & 3) * 4;        // B tile as 128 rows x 4 float4
+      pb[u] = (k0 + bk < n) ? __ldg(reinterpret_cast<const float4*>(B + int64_t(k0 + bk) * kNR + bq))
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
   float acc = 0.f;
-  for (int k0 = 0; k0 < n; k0 += 64) {
-    for (int e = tid; e < 32 * 64; e += 512) {
-      const int a = e >> 6, c = e & 63;
-      const int row = row0 + a, k = k0 + c;
-      As[a][c] = (row < n && k < n) ? Minv[int64_t(row) * ld + k] : 0.f;
-    }
-    for (int e = tid; e < 64 * kNR; e += 512) {
-      const int c = e >> 4, q = e & 15, k = k0 + c;
-      Bs[c][q] = k < n ? B[int64_t(k) * kNR + q] : 0.f;
+  load(0);
+  for (int k0 = 0; k0 < n; k0 += kCoarseK) {
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + 256 * u;
+      As[e >> 5][e & 31] = pa[u];
+      *reinterpret_cast<float4*>(&Bs[e >> 2][(e & 3) * 4]) = pb[u];
     }
     __syncthreads();
-#pragma unroll 16
-    for (int c = 0; c < 64; ++c) acc = fmaf(As[rl][c], Bs[c][rr], acc);
-    __syncthreads();
+    if (k0 + kCoarseK < n) load(k0 + kCoarseK);
+#pragma unroll 8
+    for (int c = 0; c < kCoarseK / 4; ++c) {
+      const float4 a = As[rl][c];
+      acc = fmaf(a.x, Bs[4 * c][rr], acc);
+      acc = fmaf(a.y, Bs[4 * c + 1][rr], acc);
+      acc = fmaf(a.z, Bs[4 * c + 2][rr], acc);
+      acc = fmaf(a.w, Bs[4 * c + 3][rr], acc);
+    }
   }
   const int row = row0 + rl;
   if (row < n) X[int64_t(row) * kNR + rr] = acc;
@@ -330,24 +426,41 @@ __global__ void k_scatter_cols(const double* __restrict__ Y, double* __restrict_
 }
 
 // partial[(v * kNR + r) * nb + blockIdx.x] = sum over the block's rows of X_v[row][r] * W[row][r]
-// for v < nvec (X_v = X + v * ldx).  Block = 256 threads = 16 rows x 16 rhs; grid-stride over rows.
+// for v < nvec (X_v = X + v * ldx).  Thread t of a block always handles right-hand side t % 16 (the
+// grid stride is a multiple of 16); the vectors are taken kVB at a time, so W is read once per kVB
+// vectors and kVB + 1 independent loads are in flight per element.  Fixed reduction tree: lanes
+// (r, r + 16) of a warp, then the 8 warps in order.
+constexpr int kVB = 8;
 __global__ void __launch_bounds__(kT) k_mdot_mm(const double* __restrict__ X, int64_t ldx, int nvec,
-                                                const double* __restrict__ W, int lo, int len,
+                                                const double* __restrict__ W, int64_t n16,
                                                 double* __restrict__ partial, int nb) {
-  __shared__ double sh[kT];
-  const int rl = threadIdx.x >> 4, r = threadIdx.x & 15;
-  for (int v = 0; v < nvec; ++v) {
-    const double* x = X + ldx * v;
-    double s = 0.0;
-    for (int row = lo + blockIdx.x * 16 + rl; row < lo + len; row += nb * 16)
-      s = fma(x[int64_t(row) * kNR + r], W[int64_t(row) * kNR + r], s);
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = kT / 2; o >= 16; o >>= 1) {
-      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-      __syncthreads();
+  __shared__ double sh[kT / 32][kVB][16];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int v0 = 0; v0 < nvec; v0 += kVB) {
+    double acc[kVB];
+#pragma unroll
+    for (int u = 0; u < kVB; ++u) acc[u] = 0.0;
+    for (int64_t idx = int64_t(blockIdx.x) * kT + tid; idx < n16; idx += int64_t(nb) * kT) {
+      const double w = W[idx];
+#pragma unroll
+      for (int u = 0; u < kVB; ++u)
+        if (v0 + u < nvec) acc[u] = fma(X[ldx * (v0 + u) + idx], w, acc[u]);
     }
-    if (threadIdx.x < 16) partial[(int64_t(v) * kNR + threadIdx.x) * nb + blockIdx.x] = sh[threadIdx.x];
+#pragma unroll
+    for (int u = 0; u < kVB; ++u) {
+      const double t = acc[u] + __shfl_xor_sync(0xffffffffu, acc[u], 16);
+      if (lane < 16) sh[warp][u][lane] = t;
+    }
+    __syncthreads();
+    if (tid < kVB * 16) {
+      const int u = tid >> 4, r = tid & 15;
+      if (v0 + u < nvec) {
+        double sum = 0.0;
+#pragma unroll
+        for (int w8 = 0; w8 < kT / 32; ++w8) sum += sh[w8][u][r];
+        partial[(int64_t(v0 + u) * kNR + r) * nb + blockIdx.x] = sum;
+      }
+    }
     __syncthreads();
   }
 }
@@ -365,23 +478,26 @@ __global__ void __launch_bounds__(kT) k_mfin_mm(const double* __restrict__ parti
   }
 }
 
-// W[row][r] -= sum_v X_v[row][r] * h[v * kNR + r]
-__global__ void k_maxpy_mm(const double* __restrict__ X, int64_t ldx, int nvec, const double* __restrict__ h,
-                           double* __restrict__ W, int n) {
+// W[row][r] -= sum_v X_v[row][r] * h[v * kNR + r], summed in ascending v (thread per element)
+__global__ void __launch_bounds__(kT) k_maxpy_mm(const double* __restrict__ X, int64_t ldx, int nvec,
+                                                 const double* __restrict__ h, double* __restrict__ W, int64_t n16) {
   const int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (idx >= int64_t(n) * kNR) return;
+  if (idx >= n16) return;
   const int r = int(idx & 15);
   double s = 0.0;
-  for (int v = 0; v < nvec; ++v) s = fma(X[ldx * v + idx], h[v * kNR + r], s);
+#pragma unroll 8
+  for (int v = 0; v < nvec; ++v) s = fma(X[ldx * v + idx], __ldg(h + v * kNR + r), s);
   W[idx] -= s;
 }
 
-// X[row][r] -= mean[r] on rows [lo, lo + len) where mean = sum[r] / len
+// X[row][r] -= mean[r] on rows [lo, lo + len) where mean = sum[r] / len (16 divisions per block)
 __global__ void k_sub_mean_mm(double* __restrict__ X, int lo, int len, const double* __restrict__ sum) {
+  __shared__ double mean[kNR];
+  if (threadIdx.x < kNR) mean[threadIdx.x] = sum[threadIdx.x] / double(len);
+  __syncthreads();
   const int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (idx >= int64_t(len) * kNR) return;
-  const int r = int(idx & 15);
-  X[int64_t(lo) * kNR + idx] -= sum[r] / double(len);
+  X[int64_t(lo) * kNR + idx] -= mean[idx & 15];
 }
 
 // column sums over rows [lo, lo+len): partial[r * nb + b]
@@ -400,14 +516,19 @@ __global__ void __launch_bounds__(kT) k_colsum_mm(const double* __restrict__ X, 
   if (threadIdx.x < 16) partial[int64_t(threadIdx.x) * nb + blockIdx.x] = sh[threadIdx.x];
 }
 
-// Y[row][r] = active[r] && nrm[r] > 0 ? W[row][r] / nrm[r] : 0, nrm = sqrt(sq)
+// Y[row][r] = active[r] && nrm[r] > 0 ? W[row][r] * (1 / nrm[r]) : 0, nrm = sqrt(sq): the 16
+// reciprocals are formed once per block
 __global__ void k_normalize_mm(const double* __restrict__ W, const double* __restrict__ sq,
                                const int* __restrict__ active, double* __restrict__ Y, int n) {
+  __shared__ double inv[kNR];
+  if (threadIdx.x < kNR) {
+    const double nrm = sqrt(sq[threadIdx.x]);
+    inv[threadIdx.x] = (active[threadIdx.x] && nrm > 0.0) ? 1.0 / nrm : 0.0;
+  }
+  __syncthreads();
   const int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (idx >= int64_t(n) * kNR) return;
-  const int r = int(idx & 15);
-  const double nrm = sqrt(sq[r]);
-  Y[idx] = (active[r] && nrm > 0.0) ? W[idx] / nrm : 0.0;
+  Y[idx] = W[idx] * inv[idx & 15];
 }
 
 // X[row][r] = sum_{i < m[r]} y[r * ldy + i] Z_i[row][r]
@@ -463,22 +584,22 @@ __global__ void k_givens_mm(double* __restrict__ H, int ldh, int64_t hstride, do
 
 // ---- launchers ------------------------------------------------------------------------------------
 template <typename T>
-int mm_csr(const Csr& A, const T* val, int mode, const T* b, const uint8_t* mask, const T* x, T* y,
-           cudaStream_t s) {
-  if (A.nrows == 0) return 0;
-  const int g = nblk(int64_t(A.nrows) * 16);
+int mm_sell(const SellB& A, const T* val, int mode, const T* b, const uint8_t* mask, const T* x, T* y,
+            cudaStream_t s) {
+  if (A.nslices == 0) return 0;
+  const int g = nblk(int64_t(A.nslices) * 32);
   switch (mode) {
-    case 0: k_mm<T, 0><<<g, kT, 0, s>>>(A.nrows, A.ptr, A.col, val, b, mask, x, y); break;
-    case 1: k_mm<T, 1><<<g, kT, 0, s>>>(A.nrows, A.ptr, A.col, val, b, mask, x, y); break;
-    case 2: k_mm<T, 2><<<g, kT, 0, s>>>(A.nrows, A.ptr, A.col, val, b, mask, x, y); break;
-    default: k_mm<T, 3><<<g, kT, 0, s>>>(A.nrows, A.ptr, A.col, val, b, mask, x, y); break;
+    case 0: k_sell_mm<T, 0><<<g, kT, 0, s>>>(A.nslices, A.sptr, A.swidth, A.col, val, A.rowof, b, mask, x, y); break;
+    case 1: k_sell_mm<T, 1><<<g, kT, 0, s>>>(A.nslices, A.sptr, A.swidth, A.col, val, A.rowof, b, mask, x, y); break;
+    case 2: k_sell_mm<T, 2><<<g, kT, 0, s>>>(A.nslices, A.sptr, A.swidth, A.col, val, A.rowof, b, mask, x, y); break;
+    default: k_sell_mm<T, 3><<<g, kT, 0, s>>>(A.nslices, A.sptr, A.swidth, A.col, val, A.rowof, b, mask, x, y); break;
   }
   return 1;
 }
-template int mm_csr<float>(const Csr&, const float*, int, const float*, const uint8_t*, const float*, float*,
-                           cudaStream_t);
-template int mm_csr<double>(const Csr&, const double*, int, const double*, const uint8_t*, const double*, double*,
+template int mm_sell<float>(const SellB&, const float*, int, const float*, const uint8_t*, const float*, float*,
                             cudaStream_t);
+template int mm_sell<double>(const SellB&, const double*, int, const double*, const uint8_t*, const double*, double*,
+                             cudaStream_t);
 
 int pack_mma(const Patches& P, const double* inv64, const int64_t* foff16, void* frag, float* ascale, bool half,
              cudaStream_t s) {
@@ -522,7 +643,7 @@ int scatter_mm(const Patches& P, int ndof, const uint8_t* dir, const float* r, c
 }
 
 int coarse_mm(const float* Minv, int n, int ld, const float* B, float* X, cudaStream_t s) {
-  k_coarse_mm<<<(n + 31) / 32, 512, 0, s>>>(Minv, n, ld, B, X);
+  k_coarse_mm<<<(n + kCoarseRows - 1) / kCoarseRows, 256, 0, s>>>(Minv, n, ld, B, X);
   return 1;
 }
 
@@ -548,18 +669,16 @@ int scatter_cols(const double* Y, double* X, int64_t ld, int nrhs, int n, cudaSt
   return 1;
 }
 
-constexpr int kBatchBlocks = 256;
-
 int mdot_mm(const double* X, int64_t ldx, int nvec, const double* W, int n, double* partial, double* out,
             double* acc, cudaStream_t s) {
   if (nvec <= 0) return 0;
-  k_mdot_mm<<<kBatchBlocks, kT, 0, s>>>(X, ldx, nvec, W, 0, n, partial, kBatchBlocks);
+  k_mdot_mm<<<kBatchBlocks, kT, 0, s>>>(X, ldx, nvec, W, int64_t(n) * kNR, partial, kBatchBlocks);
   k_mfin_mm<<<nvec * 16, kT, 0, s>>>(partial, kBatchBlocks, out, acc);
   return 2;
 }
 
 int maxpy_mm(const double* X, int64_t ldx, int nvec, const double* h, double* W, int n, cudaStream_t s) {
-  k_maxpy_mm<<<nblk(int64_t(n) * 16), kT, 0, s>>>(X, ldx, nvec, h, W, n);
+  k_maxpy_mm<<<nblk(int64_t(n) * 16), kT, 0, s>>>(X, ldx, nvec, h, W, int64_t(n) * kNR);
   return 1;
 }
 

@@ -110,8 +110,18 @@ __global__ void __launch_bounds__(256) k_dense_gemv(const double* __restrict__ M
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   const double* a = Minv + int64_t(row) * ld;
-  double s = 0.0;
-  for (int j = lane; j < n; j += 32) s = fma(a[j], __ldg(b + j), s);
+  // four independent partial sums per lane (columns j, j + 32, j + 64, j + 96 of each step of 128),
+  // so four loads of the row are in flight per lane; fixed combination order
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int j = lane;
+  for (; j + 96 < n; j += 128) {
+    s0 = fma(__ldg(a + j), __ldg(b + j), s0);
+    s1 = fma(__ldg(a + j + 32), __ldg(b + j + 32), s1);
+    s2 = fma(__ldg(a + j + 64), __ldg(b + j + 64), s2);
+    s3 = fma(__ldg(a + j + 96), __ldg(b + j + 96), s3);
+  }
+  for (; j < n; j += 32) s0 = fma(__ldg(a + j), __ldg(b + j), s0);
+  double s = (s0 + s1) + (s2 + s3);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) x[row] = s;
 }

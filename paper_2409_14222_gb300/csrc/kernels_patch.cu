@@ -2,7 +2,8 @@
 //   patch_factor  -- gather A_i = A[idx_i, idx_i] from the assembled CSR matrix (matrix-full,
 //                    Sec. 3.1 last paragraph) and invert it in shared memory by Gauss-Jordan
 //                    elimination with partial pivoting; store the inverse in the warp-packed layout.
-//   patch_apply   -- delta_i = A_i^{-1} r[idx_i] for every patch: one warp per patch.
+//   patch_apply   -- delta_i = A_i^{-1} r[idx_i] for every patch: one warp per patch, in one launch
+//                    or one launch per size class, with the launch shape the setup autotuner chose.
 //   vanka_scatter -- z_d = sum over the patches i containing DoF d of (w_d delta_i)_d, summed in
 //                    ascending patch order (atomic-free), Dirichlet identity, fused with the
 //                    Chebyshev update of Sec. 3 ("Relaxation").
@@ -11,6 +12,7 @@
 // Lane l = r + 8 c (r in 0..7, c in 0..3) owns rows r + 8 a and columns c + 4 b.  Element (a, b) of
 // lane l is stored at (a * NB + b) * 32 + l, so each warp load is 32 consecutive values (256 bytes in
 // FP64), and padding (rows/columns >= n, stored as zero) is at most 7 rows and 3 columns.
+#include <algorithm>
 #include <cfloat>
 #include <type_traits>
 
@@ -168,17 +170,30 @@ __device__ __forceinline__ void apply_one(int n, int s0, const int* __restrict__
     for (int b = 0; b < NB; ++b) s = fma(T(__ldg(Fp + (a * NB + b) * 32 + lane)), rl[b], s);
     acc[a] = s;
   }
+  // Reduce-scatter of the four column-group partial sums (lanes cc = 0..3 of row set rr): the pair
+  // (cc, cc ^ 2) splits the NA row blocks into halves and each lane adds only the half it keeps, then
+  // the pair (cc, cc ^ 1) does the same on that half.  NA/2 + NA/4 additions per lane instead of the
+  // 2 NA of a butterfly, which matters when the FP64 pipe is the bound; every lane ends with up to H2
+  // finished rows and writes them.
+  constexpr int H1 = (NA + 1) / 2, H2 = (H1 + 1) / 2;
+  const bool h1 = (cc >> 1) != 0, h2 = (cc & 1) != 0;
+  T b1[H1];
 #pragma unroll
-  for (int a = 0; a < NA; ++a) {
-    acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], 8);
-    acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], 16);
+  for (int i = 0; i < H1; ++i) {
+    const T lo = acc[i];
+    const T hi = (H1 + i < NA) ? acc[H1 + i < NA ? H1 + i : 0] : T(0);
+    const T send = h1 ? lo : hi, keep = h1 ? hi : lo;
+    b1[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
   }
-  if (cc == 0) {
 #pragma unroll
-    for (int a = 0; a < NA; ++a) {
-      const int row = rr + 8 * a;
-      if (row < n) delta[__ldg(pos + s0 + row)] = double(acc[a]);
-    }
+  for (int i = 0; i < H2; ++i) {
+    const T lo = b1[i];
+    const T hi = (H2 + i < H1) ? b1[H2 + i < H1 ? H2 + i : 0] : T(0);
+    const T send = h2 ? lo : hi, keep = h2 ? hi : lo;
+    const T v = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    const int a = (h1 ? H1 : 0) + (h2 ? H2 : 0) + i;
+    const int row = rr + 8 * a;
+    if ((h2 ? H2 : 0) + i < H1 && a < NA && row < n) delta[__ldg(pos + s0 + row)] = double(v);
   }
 }
 
@@ -262,20 +277,25 @@ __device__ __forceinline__ void apply_dispatch(int nb, int n, int s0, const int*
   }
 }
 
-template <int NBMAX, typename FT>
-__global__ void __launch_bounds__(256) k_patch_apply(int npatch, const int* __restrict__ work,
+// Work items w0 <= w < w1 of the work list (one patch per warp), for patches with NBLO <= ceil(n/4)
+// <= NBHI.  Warps stride over the range by the number of warps in the grid, so the same kernel runs
+// either with one warp per item or as a persistent grid of a few blocks per SM.  Which warp applies a
+// patch never changes its arithmetic: every launch shape gives bit-identical corrections.
+template <int NBLO, int NBHI, typename FT>
+__global__ void __launch_bounds__(256) k_patch_apply(int w0, int w1, const int* __restrict__ work,
                                                      const int* __restrict__ slot_ptr,
                                                      const int* __restrict__ slot_dofs,
                                                      const int64_t* __restrict__ foff,
                                                      const FT* __restrict__ F, const double* __restrict__ r,
                                                      const float2* __restrict__ r2, const int* __restrict__ pos,
                                                      double* __restrict__ delta) {
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = int((int64_t(gridDim.x) * blockDim.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (w >= npatch) return;
-  const int p = work[w];
-  const int s0 = slot_ptr[p], n = slot_ptr[p + 1] - s0;
-  apply_dispatch<1, NBMAX, FT>((n + 3) >> 2, n, s0, slot_dofs + s0, F + foff[p], r, r2, pos, delta, lane);
+  for (int w = w0 + int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); w < w1; w += nwarps) {
+    const int p = work[w];
+    const int s0 = slot_ptr[p], n = slot_ptr[p + 1] - s0;
+    apply_dispatch<NBLO, NBHI, FT>((n + 3) >> 2, n, s0, slot_dofs + s0, F + foff[p], r, r2, pos, delta, lane);
+  }
 }
 
 // r = rh + rl with rh = fl32(r), rl = fl32(r - rh): the FP32-pair form of a residual, once per DoF.
@@ -347,20 +367,41 @@ __global__ void __launch_bounds__(256) k_vanka_scatter(int ndof, const int* __re
   }
 }
 
-template <int NBMAX, typename FT>
-int launch_apply(const Patches& P, const double* r, const float2* r2, double* delta, cudaStream_t s) {
-  const int threads = 256, warps = threads / 32;
-  const int blocks = (P.npatch + warps - 1) / warps;
-  k_patch_apply<NBMAX, FT><<<blocks, threads, 0, s>>>(P.npatch, P.work, P.slot_ptr, P.slot_dofs, P.foff,
-                                                      static_cast<const FT*>(P.factors), r, r2, P.slot_pos, delta);
+// Blocks of one launch over `items` work items: one warp per item, or (per_sm > 0) at most per_sm
+// blocks per SM with the warps striding over the items.
+int apply_blocks(int items, const ApplySched& sc, int nsm) {
+  const int warps = sc.threads / 32;
+  int blocks = (items + warps - 1) / warps;
+  if (sc.per_sm > 0) blocks = std::min(blocks, sc.per_sm * std::max(nsm, 1));
+  return std::max(blocks, 1);
+}
+
+template <int NBLO, int NBHI, typename FT>
+int launch_range(const Patches& P, const ApplySched& sc, int w0, int w1, const double* r, const float2* r2,
+                 double* delta, cudaStream_t s) {
+  if (w1 <= w0) return 0;
+  k_patch_apply<NBLO, NBHI, FT><<<apply_blocks(w1 - w0, sc, P.nsm), sc.threads, 0, s>>>(
+      w0, w1, P.work, P.slot_ptr, P.slot_dofs, P.foff, static_cast<const FT*>(P.factors), r, r2, P.slot_pos, delta);
   return 1;
 }
 
 template <typename FT>
-int apply_prec(const Patches& P, const double* r, const float2* r2, double* delta, cudaStream_t s) {
-  if (P.nb_max <= 10) return launch_apply<10, FT>(P, r, r2, delta, s);
-  if (P.nb_max <= 19) return launch_apply<19, FT>(P, r, r2, delta, s);
-  return launch_apply<32, FT>(P, r, r2, delta, s);
+int apply_prec(const Patches& P, const ApplySched& sc, const double* r, const float2* r2, double* delta,
+               cudaStream_t s) {
+  if (!sc.split) {
+    // one launch over every patch of the level; the per-warp dispatch covers all sizes
+    if (P.nb_max <= 10) return launch_range<1, 10, FT>(P, sc, 0, P.npatch, r, r2, delta, s);
+    if (P.nb_max <= 19) return launch_range<1, 19, FT>(P, sc, 0, P.npatch, r, r2, delta, s);
+    return launch_range<1, 32, FT>(P, sc, 0, P.npatch, r, r2, delta, s);
+  }
+  // one launch per size class, each compiled for its own range of sizes (fewer registers, so more
+  // resident warps, for the small classes)
+  int k = 0;
+  k += launch_range<20, 32, FT>(P, sc, P.cls_lo[3], P.cls_hi[3], r, r2, delta, s);
+  k += launch_range<11, 19, FT>(P, sc, P.cls_lo[2], P.cls_hi[2], r, r2, delta, s);
+  k += launch_range<5, 10, FT>(P, sc, P.cls_lo[1], P.cls_hi[1], r, r2, delta, s);
+  k += launch_range<1, 4, FT>(P, sc, P.cls_lo[0], P.cls_hi[0], r, r2, delta, s);
+  return k;
 }
 
 }  // namespace
@@ -390,14 +431,19 @@ int patch_factor(const Csr& A, const Patches& P, int prec, void* factors, int* s
   return 1;
 }
 
-int patch_apply(const Patches& P, const double* r, float2* r2, double* delta, cudaStream_t s) {
+int patch_apply_sched(const Patches& P, const ApplySched& sc, const double* r, float2* r2, double* delta,
+                      cudaStream_t s) {
   if (P.npatch == 0) return 0;
-  if (P.prec == 0) return apply_prec<double>(P, r, nullptr, delta, s);
-  if (P.prec == 1) return apply_prec<float>(P, r, nullptr, delta, s);
+  if (P.prec == 0) return apply_prec<double>(P, sc, r, nullptr, delta, s);
+  if (P.prec == 1) return apply_prec<float>(P, sc, r, nullptr, delta, s);
   // FP32-pair inverses: split the residual once per DoF first
   const int n = P.ndof;
   k_split_pairs<<<(n + 255) / 256, 256, 0, s>>>(r, r2, n);
-  return 1 + apply_prec<float2>(P, r, r2, delta, s);
+  return 1 + apply_prec<float2>(P, sc, r, r2, delta, s);
+}
+
+int patch_apply(const Patches& P, const double* r, float2* r2, double* delta, cudaStream_t s) {
+  return patch_apply_sched(P, P.sched, r, r2, delta, s);
 }
 
 int vanka_scatter(const Patches& P, int ndof, const uint8_t* dir, const double* r, const double* delta,

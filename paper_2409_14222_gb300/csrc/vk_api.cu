@@ -176,6 +176,7 @@ struct HostPatchPlan {
   std::vector<int64_t> foff;    // canonical id -> packed offset
   int64_t ftotal = 0;
   int nb_max = 0;
+  int cls_lo[4] = {0, 0, 0, 0}, cls_hi[4] = {0, 0, 0, 0};  // work-list range of each size class
   std::vector<int> dof_ptr, slot_pos;
   std::vector<double> weight;
 };
@@ -194,6 +195,21 @@ HostPatchPlan plan_patches(const vk::HostLevel& L, int weights) {
     P.ftotal += vk::gpu::packed_size(L.patch_ptr[p + 1] - L.patch_ptr[p]);
     P.nb_max = std::max(P.nb_max, nb(p));
   }
+  // size classes of ceil(n/4) (the work list is sorted by it, largest first, so each class is a range)
+  for (int c = 0; c < 4; ++c) {
+    const int lo = c == 0 ? 1 : vk::gpu::kApplyClassHi[c - 1] + 1, hi = vk::gpu::kApplyClassHi[c];
+    int a = np, b = 0;
+    for (int w = 0; w < np; ++w) {
+      const int v = nb(P.work[w]);
+      if (v >= lo && v <= hi) {
+        a = std::min(a, w);
+        b = std::max(b, w + 1);
+      }
+    }
+    P.cls_lo[c] = a < b ? a : 0;
+    P.cls_hi[c] = a < b ? b : 0;
+  }
+  if (P.nb_max > vk::gpu::kApplyClassHi[3]) raise(VK_ERR_ARG, "patches larger than 128 DoFs are not supported");
   const int64_t nslots = L.patch_dofs.size();
   P.dof_ptr.assign(L.ndof + 1, 0);
   for (int64_t s = 0; s < nslots; ++s) P.dof_ptr[L.patch_dofs[s] + 1]++;
@@ -221,13 +237,55 @@ struct DevLevel {
   double *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *t = nullptr, *delta = nullptr;
   float2* r2 = nullptr;  // FP32-pair residual (emulated-FP64 inverses only)
   // multi-right-hand-side structures (batch_prec != VK_BATCH_NONE)
-  vk::gpu::Csr Pc, Rc;                       // CSR transfers (FP64 values unused by the batch path)
-  float *aval_f = nullptr, *pval_f = nullptr, *rval_f = nullptr;
+  vk::gpu::SellB Ab, Pb, Rb;                 // SELL-8 copies for the 16-right-hand-side products
   int64_t* foff16 = nullptr;
   void* frag = nullptr;
   float* ascale = nullptr;
   int mt_max = 0;
+  vk::gpu::TcPatches tc;                     // tcgen05 path: core-matrix inverses and size classes
+  const int64_t* foff_tc = nullptr;          // byte offset of each patch's core matrices
   float *bb = nullptr, *xb = nullptr, *rb = nullptr, *db = nullptr, *delta_f = nullptr;
+};
+
+// Outcome of the patch-apply autotuner on one level: the chosen candidate and every candidate's
+// best time (microseconds; 0 when not timed).
+struct TuneResult {
+  int index = 3;        // default shape: one launch, 256 threads, one warp per patch
+  double us[16] = {};
+};
+
+// Pairs of CUDA events recorded on the launching stream around selected kernels; the summed
+// durations are read by vk_stats_read.
+struct KTimer {
+  std::vector<cudaEvent_t> ev;
+  size_t used = 0;
+  void begin(cudaStream_t s) {
+    if (used + 2 > ev.size())
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        ev.push_back(e);
+      }
+    CK(cudaEventRecord(ev[used], s));
+  }
+  void end(cudaStream_t s) {
+    CK(cudaEventRecord(ev[used + 1], s));
+    used += 2;
+  }
+  int64_t count() const { return int64_t(used / 2); }
+  double total_ms() const {
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < used; i += 2) {
+      CK(cudaEventSynchronize(ev[i + 1]));
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+      ms += t;
+    }
+    return ms;
+  }
+  ~KTimer() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
 };
 
 }  // namespace
@@ -253,10 +311,12 @@ struct vk_hierarchy {
   // statistics (vk_stats_*)
   int64_t n_launch = 0, n_vcycle = 0;
   bool time_apply = false;
-  std::vector<cudaEvent_t> ev;
-  size_t ev_used = 0;
+  std::vector<TuneResult> tune;  // per level (index 0 unused)
+  KTimer tm_apply;   // finest-level patch applications
+  KTimer tm_spmv;    // finest-level V-cycle residual SpMV (SELL, or the block SpMM of vk_solve_batch)
   double apply_bytes = 0.0, apply_flops = 0.0;
   double bapply_bytes = 0.0, bapply_flops = 0.0;
+  double spmv_bytes = 0.0, bspmv_bytes = 0.0;
   // graph-resident FGMRES (one CUDA graph per hierarchy: prologue, WHILE node, epilogue)
   vk::gpu::FgState* st = nullptr;        // device
   vk::gpu::FgState* h_par = nullptr;     // pinned: parameters written before each launch
@@ -276,8 +336,8 @@ struct vk_hierarchy {
   double *gb = nullptr, *histb = nullptr, *hcolb = nullptr, *t2b = nullptr, *partb = nullptr, *sqb = nullptr;
   double* yb = nullptr;
   int *activeb = nullptr, *itersb = nullptr, *nonfb = nullptr;
+  int* tc_err = nullptr;   // set by the tcgen05 patch solves when a bounded wait expires
   ~vk_hierarchy() {
-    for (cudaEvent_t e : ev) cudaEventDestroy(e);
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
     if (cap0) cudaStreamDestroy(cap0);
@@ -289,6 +349,15 @@ struct vk_hierarchy {
 };
 
 namespace {
+
+// Candidate launch shapes of the patch application (see vk::gpu::ApplySched).
+std::vector<vk::gpu::ApplySched> apply_candidates() {
+  std::vector<vk::gpu::ApplySched> c;
+  for (int split = 0; split < 2; ++split)
+    for (int threads : {128, 256})
+      for (int per_sm : {0, 4, 8}) c.push_back({split, threads, per_sm});
+  return c;
+}
 
 void validate(const vk_problem* p, const vk_options* o) {
   if (!p || !o) raise(VK_ERR_ARG, "null problem or options");
@@ -305,10 +374,13 @@ void validate(const vk_problem* p, const vk_options* o) {
   if (o->eig_steps < 1 || o->eig_steps > 64) raise(VK_ERR_ARG, "eig_steps must be in 1..64");
   if (o->max_iterations < 1 || o->max_iterations > 1000) raise(VK_ERR_ARG, "max_iterations must be in 1..1000");
   if (o->batch_prec < VK_BATCH_NONE || o->batch_prec > VK_BATCH_FP16) raise(VK_ERR_ARG, "bad batch_prec");
+  if (o->batch_engine != VK_ENGINE_TCGEN05 && o->batch_engine != VK_ENGINE_MMA_SYNC) raise(VK_ERR_ARG, "bad batch_engine");
+  if (o->apply_schedule < -1 || o->apply_schedule >= int(apply_candidates().size()))
+    raise(VK_ERR_ARG, "apply_schedule must be -1 or a candidate index");
   if (o->batch_prec != VK_BATCH_NONE) {
     if (o->factor_prec != VK_PREC_F64) raise(VK_ERR_ARG, "batch_prec needs FP64 factor_prec");
-    if (o->batch_max_iterations < 1 || o->batch_max_iterations > 1000)
-      raise(VK_ERR_ARG, "batch_max_iterations must be in 1..1000");
+    if (o->batch_max_iterations < 1 || o->batch_max_iterations > 127)
+      raise(VK_ERR_ARG, "batch_max_iterations must be in 1..127");
   }
 }
 
@@ -347,26 +419,37 @@ vk::gpu::Csr upload_csr(DeviceMemory& m, const vk::HostCsr& A) {
   return c;
 }
 
+// SELL-8 copy of a matrix for the 16-right-hand-side products: FP32 values, and FP64 values too when
+// `fp64` (the finest matrix, used by the FP64 outer iteration).
+vk::gpu::SellB upload_sell8(DeviceMemory& m, const vk::HostCsr& A, bool fp64) {
+  const HostSell S = build_sell(A, 4);   // 4 threads per row in the SELL builder = slices of 8 rows
+  vk::gpu::SellB d;
+  d.nrows = A.nrows;
+  d.nslices = int(S.sw.size());
+  d.sptr = m.upload(S.sptr);
+  d.swidth = m.upload(S.sw);
+  d.col = m.upload(S.col);
+  d.rowof = m.upload(S.rowof);
+  std::vector<float> vf(S.val.size());
+  for (size_t i = 0; i < vf.size(); ++i) vf[i] = float(S.val[i]);
+  d.valf = m.upload(vf);
+  if (fp64) d.vald = m.upload(S.val);
+  return d;
+}
+
 // Multi-right-hand-side structures: FP32 copies of the matrices, CSR transfers, 16-bit patch
 // fragments, FP32 block vectors per level, the FP32 coarse inverse and the FP64 batched Krylov bases.
 void allocate_batch(vk_hierarchy* h) {
   DeviceMemory& m = h->mem;
   const int L = h->prob.nlevels;
   constexpr int NR = 16;
-  auto f32 = [](const std::vector<double>& v) {
-    std::vector<float> o(v.size());
-    for (size_t i = 0; i < v.size(); ++i) o[i] = float(v[i]);
-    return o;
-  };
   for (int l = 0; l < L; ++l) {
     const vk::HostLevel& H = h->host[l];
     DevLevel& D = h->lv[l];
-    D.aval_f = m.upload(f32(H.A.val));
+    D.Ab = upload_sell8(m, H.A, l == L - 1);
     if (l > 0) {
-      D.Pc = upload_csr(m, H.P);
-      D.Rc = upload_csr(m, H.R);
-      D.pval_f = m.upload(f32(H.P.val));
-      D.rval_f = m.upload(f32(H.R.val));
+      D.Pb = upload_sell8(m, H.P, false);
+      D.Rb = upload_sell8(m, H.R, false);
       const int np = int(H.patch_ptr.size()) - 1;
       std::vector<int64_t> f16(np);
       int64_t tot = 0;
@@ -382,6 +465,52 @@ void allocate_batch(vk_hierarchy* h) {
       D.foff16 = m.upload(f16);
       D.frag = m.get(size_t(tot) * 16);
       D.ascale = m.get_n<float>(np);
+      // tcgen05 layout: ceil(n/8)^2 core matrices per patch; size classes n <= 40, 64, 128 are ranges
+      // of the work list (sorted by ceil(n/4), largest first), cut into groups of kTcG[c] patches
+      {
+        const HostPatchPlan plan = plan_patches(H, h->opt.weights);
+        std::vector<int64_t> ftc(np);
+        int64_t btot = 0;
+        for (int p = 0; p < np; ++p) {
+          ftc[p] = btot;
+          btot += vk::gpu::tc_bytes(H.patch_ptr[p + 1] - H.patch_ptr[p]);
+        }
+        vk::gpu::TcPatches& T = D.tc;
+        for (int c = 0; c < 3; ++c) {
+          int lo = np, hi = 0;
+          for (int w = 0; w < np; ++w) {
+            const int pw = plan.work[w], n = H.patch_ptr[pw + 1] - H.patch_ptr[pw];
+            if (n <= vk::gpu::kTcCap[c] && (c == 0 || n > vk::gpu::kTcCap[c - 1])) {
+              lo = std::min(lo, w);
+              hi = std::max(hi, w + 1);
+            }
+          }
+          if (lo >= hi) continue;
+          const int G = vk::gpu::kTcG[c], K = vk::gpu::kTcK[c], R = 128 / G / 8 * 8;
+          const int ng = (hi - lo + G - 1) / G;
+          std::vector<int> gdof(size_t(ng) * G * K, -1), gpos(size_t(ng) * 128, -1);
+          std::vector<int4> gslot(size_t(ng) * G, make_int4(0, 0, 0, 0));
+          for (int g = 0; g < ng; ++g)
+            for (int j = 0; j < G; ++j) {
+              const int w = lo + g * G + j;
+              if (w >= hi) break;
+              const int pw = plan.work[w], s0 = H.patch_ptr[pw], n = H.patch_ptr[pw + 1] - s0;
+              for (int k = 0; k < n; ++k) {
+                gdof[(size_t(g) * G + j) * K + k] = H.patch_dofs[s0 + k];
+                gpos[size_t(g) * 128 + R * j + k] = plan.slot_pos[s0 + k];
+              }
+              gslot[size_t(g) * G + j] = make_int4(int(uint32_t(uint64_t(ftc[pw]))), int(uint32_t(uint64_t(ftc[pw]) >> 32)),
+                                                   n, pw);
+            }
+          T.cls[c].ngroups = ng;
+          T.cls[c].gdof = m.upload(gdof);
+          T.cls[c].gpos = m.upload(gpos);
+          T.cls[c].gslot = m.upload(gslot);
+        }
+        D.foff_tc = m.upload(ftc);
+        T.frag = static_cast<const uint8_t*>(m.get(size_t(btot)));
+        T.ascale = D.ascale;
+      }
       D.delta_f = m.get_n<float>(size_t(H.patch_dofs.size()) * NR);
     }
     D.bb = m.get_n<float>(size_t(H.ndof) * NR);
@@ -406,10 +535,11 @@ void allocate_batch(vk_hierarchy* h) {
   h->histb = m.get_n<double>(size_t(NR) * ldh);
   h->hcolb = m.get_n<double>(size_t(NR) * ldh);
   h->t2b = m.get_n<double>(size_t(NR) * ldh);
-  h->partb = m.get_n<double>(size_t(NR) * ldh * 256);
+  h->partb = m.get_n<double>(size_t(NR) * ldh * vk::gpu::kBatchBlocks);
   h->sqb = m.get_n<double>(4 * NR);
   h->yb = m.get_n<double>(size_t(NR) * ldh);
   h->activeb = m.get_n<int>(NR);
+  h->tc_err = m.get_n<int>(4);
   h->itersb = m.get_n<int>(NR);
   h->nonfb = m.get_n<int>(NR);
 }
@@ -452,6 +582,10 @@ void allocate_device(vk_hierarchy* h) {
       G.factors = m.get(size_t(P.ftotal) * fsz);
       G.prec = h->opt.factor_prec;
       G.nb_max = P.nb_max;
+      for (int c = 0; c < 4; ++c) {
+        G.cls_lo[c] = P.cls_lo[c];
+        G.cls_hi[c] = P.cls_hi[c];
+      }
       G.dof_ptr = m.upload(P.dof_ptr);
       G.slot_pos = m.upload(P.slot_pos);
       G.weight = P.weight.empty() ? nullptr : m.upload(P.weight);
@@ -490,20 +624,9 @@ void allocate_device(vk_hierarchy* h) {
 void timed_apply(vk_hierarchy* h, int l, const double* r, cudaStream_t s) {
   DevLevel& D = h->lv[l];
   const bool t = h->time_apply && l == h->prob.nlevels - 1;
-  if (t) {
-    if (h->ev_used + 2 > h->ev.size())
-      for (int i = 0; i < 64; ++i) {
-        cudaEvent_t e;
-        CK(cudaEventCreate(&e));
-        h->ev.push_back(e);
-      }
-    CK(cudaEventRecord(h->ev[h->ev_used], s));
-  }
+  if (t) h->tm_apply.begin(s);
   h->n_launch += vk::gpu::patch_apply(D.pat, r, D.r2, D.delta, s);
-  if (t) {
-    CK(cudaEventRecord(h->ev[h->ev_used + 1], s));
-    h->ev_used += 2;
-  }
+  if (t) h->tm_apply.end(s);
 }
 
 double device_dot(vk_hierarchy* h, const double* x, const double* y, int n, cudaStream_t s) {
@@ -560,7 +683,10 @@ void vcycle(vk_hierarchy* h, int l, const double* b, double* x, cudaStream_t s, 
   DevLevel& D = h->lv[l];
   DevLevel& C = h->lv[l - 1];
   smooth(h, l, b, x, true, s);
+  const bool t = h->time_apply && l == h->prob.nlevels - 1;
+  if (t) h->tm_spmv.begin(s);
   h->n_launch += vk::gpu::sell_residual(D.A, b, x, D.r, s);
+  if (t) h->tm_spmv.end(s);
   h->n_launch += vk::gpu::sell_restrict(D.R, C.dir, D.r, C.b, s);
   vcycle(h, l - 1, C.b, C.x, s, count);
   h->n_launch += vk::gpu::sell_prolong_add(D.P, C.x, x, s);
@@ -616,6 +742,59 @@ double estimate_lambda(vk_hierarchy* h, int l, cudaStream_t s) {
   return *std::max_element(re.begin(), re.end());
 }
 
+// Autotuner of the patch application: on every smoothed level, time each candidate launch shape
+// (CUDA events on the setup stream, best of `reps` launches after one warm-up launch) on the level's
+// own patches and keep the fastest.  Every shape gives bit-identical corrections, so the choice only
+// changes speed.  opt.apply_schedule >= 0 forces that candidate instead (no timing).
+void tune_patch_apply(vk_hierarchy* h, cudaStream_t s) {
+  const auto cand = apply_candidates();
+  const int L = h->prob.nlevels;
+  h->tune.assign(L, TuneResult{});
+  if (h->opt.apply_schedule >= int(cand.size())) raise(VK_ERR_ARG, "apply_schedule out of range");
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  try {
+    for (int l = 1; l < L; ++l) {
+      DevLevel& D = h->lv[l];
+      TuneResult& T = h->tune[l];
+      if (h->opt.apply_schedule >= 0) {
+        T.index = h->opt.apply_schedule;
+      } else if (h->opt.autotune) {
+        h->n_launch += vk::gpu::fill(D.t, 1.0, D.ndof, s);
+        const int reps = 3;
+        double best = 1e300;
+        for (size_t i = 0; i < cand.size(); ++i) {
+          h->n_launch += vk::gpu::patch_apply_sched(D.pat, cand[i], D.t, D.r2, D.delta, s);
+          float t_best = 1e30f;
+          for (int k = 0; k < reps; ++k) {
+            CK(cudaEventRecord(e0, s));
+            h->n_launch += vk::gpu::patch_apply_sched(D.pat, cand[i], D.t, D.r2, D.delta, s);
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            t_best = std::min(t_best, ms);
+          }
+          T.us[i] = 1e3 * t_best;
+          if (T.us[i] < best) {
+            best = T.us[i];
+            T.index = int(i);
+          }
+        }
+        CK(cudaGetLastError());
+      }
+      D.pat.sched = cand[T.index];
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  CK(cudaEventDestroy(e0));
+  CK(cudaEventDestroy(e1));
+}
+
 void setup_device(vk_hierarchy* h, cudaStream_t s) {
   std::lock_guard<std::mutex> lock(g_device_mu);
   h->mem.stream = s;
@@ -650,9 +829,12 @@ void setup_device(vk_hierarchy* h, cudaStream_t s) {
       DevLevel& D = h->lv[l];
       h->n_launch += vk::gpu::pack_mma(D.pat, static_cast<const double*>(D.pat.factors), D.foff16, D.frag, D.ascale,
                                        half, s);
+      h->n_launch += vk::gpu::pack_tc(D.pat, static_cast<const double*>(D.pat.factors), D.ascale, D.foff_tc,
+                                      const_cast<uint8_t*>(D.tc.frag), half, s);
     }
     const int64_t mm = int64_t(h->nc + 1) * (h->nc + 1);
     h->n_launch += vk::gpu::to_f32(h->Cinv, h->cinv_f, mm, s);
+    CK(cudaMemsetAsync(h->tc_err, 0, 4 * sizeof(int), s));
     CK(cudaGetLastError());
   }
   std::vector<int> st(16);
@@ -675,15 +857,30 @@ void setup_device(vk_hierarchy* h, cudaStream_t s) {
     // inverse entries + slot DoF indices + gathered r + written delta + per-patch work/offset/pointers
     h->apply_bytes = fsz * sn2 + 20.0 * sn + 16.0 * np;
     h->apply_flops = 2.0 * sn2;
+    // residual SpMV r = b - A x: value + column index per stored nonzero; row index, b, x, r per row
+    const double nnz = double(F.A.nnz()), nrow = double(F.ndof);
+    h->spmv_bytes = 12.0 * nnz + 28.0 * nrow;
+    // 16 right-hand sides in FP32: value + column per nonzero, row pointer, 16 x (b, x, r) per row
+    h->bspmv_bytes = 8.0 * nnz + 4.0 * nrow + 3.0 * 64.0 * nrow;
     if (h->opt.batch_prec != VK_BATCH_NONE) {
       // 16-bit fragments (padded to 16x16 tiles, as stored) + per patch DoF index, 16 FP32 residual
       // values gathered and 16 FP32 corrections written per slot + per-patch scale/offsets
       double frag = 0.0;
-      for (int p = 0; p < np; ++p) frag += 16.0 * vk::gpu::frag_size(F.patch_ptr[p + 1] - F.patch_ptr[p]);
+      for (int p = 0; p < np; ++p) {
+        const int n = F.patch_ptr[p + 1] - F.patch_ptr[p];
+        frag += h->opt.batch_engine == VK_ENGINE_MMA_SYNC ? 16.0 * vk::gpu::frag_size(n) : double(vk::gpu::tc_bytes(n));
+      }
       h->bapply_bytes = frag + (4.0 + 64.0 + 64.0 + 4.0) * sn + 28.0 * np;
       h->bapply_flops = 2.0 * 16.0 * sn2;
     }
   }
+  {
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    for (int l = 1; l < L; ++l) h->lv[l].pat.nsm = h->lv[l].tc.nsm = nsm;
+  }
+  tune_patch_apply(h, s);
   h->lambdas.assign(L, 0.0);
   for (int l = 1; l < L; ++l) {
     h->lambdas[l] = h->opt.lambdas ? h->opt.lambdas[l] : estimate_lambda(h, l, s);
@@ -963,24 +1160,16 @@ void smooth_b(vk_hierarchy* h, int l, const float* b, float* x, bool zero_init, 
   for (int step = 0; step < h->opt.sweeps; ++step) {
     const float* rr = b;
     if (!(step == 0 && zero_init)) {
-      h->n_launch += vk::gpu::mm_csr<float>(D.Acsr, D.aval_f, 0, b, nullptr, x, D.rb, s);
+      h->n_launch += vk::gpu::mm_sell<float>(D.Ab, D.Ab.valf, 0, b, nullptr, x, D.rb, s);
       rr = D.rb;
     }
     const bool t = h->time_apply && l == h->prob.nlevels - 1;
-    if (t) {
-      if (h->ev_used + 2 > h->ev.size())
-        for (int i = 0; i < 64; ++i) {
-          cudaEvent_t e;
-          CK(cudaEventCreate(&e));
-          h->ev.push_back(e);
-        }
-      CK(cudaEventRecord(h->ev[h->ev_used], s));
-    }
-    h->n_launch += vk::gpu::patch_apply_mma(D.pat, D.foff16, D.frag, D.ascale, half, D.mt_max, rr, D.delta_f, s);
-    if (t) {
-      CK(cudaEventRecord(h->ev[h->ev_used + 1], s));
-      h->ev_used += 2;
-    }
+    if (t) h->tm_apply.begin(s);
+    if (h->opt.batch_engine == VK_ENGINE_MMA_SYNC)
+      h->n_launch += vk::gpu::patch_apply_mma(D.pat, D.foff16, D.frag, D.ascale, half, D.mt_max, rr, D.delta_f, s);
+    else
+      h->n_launch += vk::gpu::patch_apply_tc(D.tc, half, rr, D.delta_f, h->tc_err, s);
+    if (t) h->tm_apply.end(s);
     int mode;
     double c1 = 0.0, c2 = 0.0;
     if (step == 0) {
@@ -1005,10 +1194,13 @@ void vcycle_b(vk_hierarchy* h, int l, const float* b, float* x, cudaStream_t s) 
   DevLevel& D = h->lv[l];
   DevLevel& C = h->lv[l - 1];
   smooth_b(h, l, b, x, true, s);
-  h->n_launch += vk::gpu::mm_csr<float>(D.Acsr, D.aval_f, 0, b, nullptr, x, D.rb, s);
-  h->n_launch += vk::gpu::mm_csr<float>(D.Rc, D.rval_f, 3, nullptr, C.dir, D.rb, C.bb, s);
+  const bool t = h->time_apply && l == h->prob.nlevels - 1;
+  if (t) h->tm_spmv.begin(s);
+  h->n_launch += vk::gpu::mm_sell<float>(D.Ab, D.Ab.valf, 0, b, nullptr, x, D.rb, s);
+  if (t) h->tm_spmv.end(s);
+  h->n_launch += vk::gpu::mm_sell<float>(D.Rb, D.Rb.valf, 3, nullptr, C.dir, D.rb, C.bb, s);
   vcycle_b(h, l - 1, C.bb, C.xb, s);
-  h->n_launch += vk::gpu::mm_csr<float>(D.Pc, D.pval_f, 2, x, nullptr, C.xb, x, s);
+  h->n_launch += vk::gpu::mm_sell<float>(D.Pb, D.Pb.valf, 2, x, nullptr, C.xb, x, s);
   smooth_b(h, l, b, x, false, s);
 }
 
@@ -1060,7 +1252,7 @@ int solve_batch_impl(vk_hierarchy* h, int nrhs, const double* B, int64_t ldb, do
     ++h->n_vcycle;
     h->n_launch += vk::gpu::to_f64(F.xb, zj, ld, s);
     h->n_launch += vk::gpu::project_mm(zj, F.n_u, F.n_p, h->partb, h->sqb + NR, s);
-    h->n_launch += vk::gpu::mm_csr<double>(F.Acsr, F.Acsr.val, 1, nullptr, nullptr, zj, h->wb, s);
+    h->n_launch += vk::gpu::mm_sell<double>(F.Ab, F.Ab.vald, 1, nullptr, nullptr, zj, h->wb, s);
     h->n_launch += vk::gpu::mdot_mm(h->Vb, ld, j + 1, h->wb, n, h->partb, h->hcolb, nullptr, s);
     h->n_launch += vk::gpu::maxpy_mm(h->Vb, ld, j + 1, h->hcolb, h->wb, n, s);
     h->n_launch += vk::gpu::mdot_mm(h->Vb, ld, j + 1, h->wb, n, h->partb, h->t2b, h->hcolb, s);
@@ -1082,7 +1274,10 @@ int solve_batch_impl(vk_hierarchy* h, int nrhs, const double* B, int64_t ldb, do
   CK(cudaMemcpyAsync(Hh.data(), h->Hb, Hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(gh.data(), h->gb, gh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(hist.data(), h->histb, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  int tc_err = 0;
+  CK(cudaMemcpyAsync(&tc_err, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (tc_err != 0) raise(VK_ERR_TIMEOUT, "a tensor-core patch solve's bounded wait expired");
   std::vector<double> y(size_t(NR) * ldh, 0.0);
   for (int r = 0; r < NR; ++r) {
     const int mr = iters[r];
@@ -1098,7 +1293,7 @@ int solve_batch_impl(vk_hierarchy* h, int nrhs, const double* B, int64_t ldb, do
   // true residuals of the projected systems
   h->n_launch += vk::gpu::gather_cols(B, ldb, nrhs, h->wb, n, s);
   h->n_launch += vk::gpu::project_mm(h->wb, F.n_u, F.n_p, h->partb, h->sqb + NR, s);
-  h->n_launch += vk::gpu::mm_csr<double>(F.Acsr, F.Acsr.val, 0, h->wb, nullptr, h->xob, h->Zb, s);
+  h->n_launch += vk::gpu::mm_sell<double>(F.Ab, F.Ab.vald, 0, h->wb, nullptr, h->xob, h->Zb, s);
   h->n_launch += vk::gpu::mdot_mm(h->Zb, 0, 1, h->Zb, n, h->partb, h->sqb, nullptr, s);
   h->n_launch += vk::gpu::scatter_cols(h->xob, X, ldb, nrhs, n, s);
   CK(cudaMemcpyAsync(sq.data(), h->sqb, NR * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1153,6 +1348,9 @@ void vk_default_options(vk_options* o) {
   o->max_iterations = 100;
   o->batch_prec = VK_BATCH_NONE;
   o->batch_max_iterations = 60;
+  o->autotune = 1;
+  o->apply_schedule = -1;
+  o->batch_engine = VK_ENGINE_MMA_SYNC;
 }
 
 const char* vk_last_error(void) { return g_err.c_str(); }
@@ -1247,6 +1445,25 @@ int vk_lambda(const vk_hierarchy* h, int level, double* lambda) {
     check_device(h);
     if (!lambda) raise(VK_ERR_ARG, "null output");
     *lambda = h->lambdas[level];
+    return VK_OK;
+  });
+}
+
+int vk_apply_schedule(const vk_hierarchy* h, int level, int32_t* split, int32_t* threads, int32_t* per_sm,
+                      int32_t* index, double* cand_us, int32_t* ncand) {
+  return guard([&] {
+    check_level(h, level, 1);
+    check_device(h);
+    const auto cand = apply_candidates();
+    const TuneResult& T = h->tune[level];
+    const vk::gpu::ApplySched& sc = h->lv[level].pat.sched;
+    if (split) *split = sc.split;
+    if (threads) *threads = sc.threads;
+    if (per_sm) *per_sm = sc.per_sm;
+    if (index) *index = T.index;
+    if (ncand) *ncand = int32_t(cand.size());
+    if (cand_us)
+      for (size_t i = 0; i < cand.size(); ++i) cand_us[i] = T.us[i];
     return VK_OK;
   });
 }
@@ -1404,7 +1621,8 @@ int vk_stats_reset(vk_hierarchy* h, int time_kernels) {
     check_device(h);
     h->n_launch = 0;
     h->n_vcycle = 0;
-    h->ev_used = 0;
+    h->tm_apply.used = 0;
+    h->tm_spmv.used = 0;
     h->time_apply = time_kernels != 0;
     return VK_OK;
   });
@@ -1414,21 +1632,18 @@ int vk_stats_read(vk_hierarchy* h, vk_stats* out) {
   return guard([&] {
     check_device(h);
     if (!out) raise(VK_ERR_ARG, "null output");
-    double ms = 0.0;
-    for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
-      CK(cudaEventSynchronize(h->ev[i + 1]));
-      float t = 0.f;
-      CK(cudaEventElapsedTime(&t, h->ev[i], h->ev[i + 1]));
-      ms += t;
-    }
     out->launches = h->n_launch;
     out->vcycles = h->n_vcycle;
-    out->apply_launches = int64_t(h->ev_used / 2);
-    out->apply_ms = ms;
+    out->apply_launches = h->tm_apply.count();
+    out->apply_ms = h->tm_apply.total_ms();
     out->apply_bytes = h->apply_bytes;
     out->apply_flops = h->apply_flops;
     out->batch_apply_bytes = h->bapply_bytes;
     out->batch_apply_flops = h->bapply_flops;
+    out->spmv_launches = h->tm_spmv.count();
+    out->spmv_ms = h->tm_spmv.total_ms();
+    out->spmv_bytes = h->spmv_bytes;
+    out->batch_spmv_bytes = h->bspmv_bytes;
     return VK_OK;
   });
 }

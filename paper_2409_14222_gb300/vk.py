@@ -28,6 +28,7 @@ VK_PREC_F32 = 1
 VK_PREC_F64E = 2
 VK_CSR_A, VK_CSR_P, VK_CSR_R = 0, 1, 2
 VK_BATCH_NONE, VK_BATCH_BF16, VK_BATCH_FP16 = 0, 1, 2
+VK_ENGINE_TCGEN05, VK_ENGINE_MMA_SYNC = 0, 1
 
 STATUS_NAMES = {0: "VK_OK", 1: "VK_ERR_ARG", 2: "VK_ERR_NO_MEMORY", 3: "VK_ERR_SINGULAR",
                 4: "VK_ERR_NONFINITE", 5: "VK_ERR_NOT_CONVERGED", 6: "VK_ERR_TIMEOUT", 7: "VK_ERR_CUDA",
@@ -39,7 +40,7 @@ SYMBOLS = [
     "vk_level_info", "vk_lambda", "vk_residual", "vk_vanka", "vk_smooth", "vk_restrict", "vk_prolong",
     "vk_coarse_solve", "vk_vcycle", "vk_solve", "vk_solve_host", "vk_csr_dims", "vk_export_csr",
     "vk_export_patches", "vk_export_dirichlet", "vk_hessenberg_eigenvalues", "vk_stats_reset", "vk_stats_read",
-    "vk_vanka_noalloc", "vk_solve_batch", "vk_default_server_config", "vk_server_create", "vk_server_submit", "vk_server_wait",
+    "vk_vanka_noalloc", "vk_solve_batch", "vk_apply_schedule", "vk_default_server_config", "vk_server_create", "vk_server_submit", "vk_server_wait",
     "vk_server_get_stats", "vk_server_destroy",
 ]
 
@@ -61,7 +62,8 @@ class vk_options(ctypes.Structure):
                 ("lambdas", ctypes.POINTER(ctypes.c_double)), ("factor_prec", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("host_threads", ctypes.c_int32), ("host_only", ctypes.c_int32),
                 ("max_iterations", ctypes.c_int32), ("batch_prec", ctypes.c_int32),
-                ("batch_max_iterations", ctypes.c_int32)]
+                ("batch_max_iterations", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("apply_schedule", ctypes.c_int32), ("batch_engine", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -81,7 +83,9 @@ class vk_solve_info(ctypes.Structure):
 class vk_stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("vcycles", ctypes.c_int64), ("apply_launches", ctypes.c_int64),
                 ("apply_ms", ctypes.c_double), ("apply_bytes", ctypes.c_double), ("apply_flops", ctypes.c_double),
-                ("batch_apply_bytes", ctypes.c_double), ("batch_apply_flops", ctypes.c_double)]
+                ("batch_apply_bytes", ctypes.c_double), ("batch_apply_flops", ctypes.c_double),
+                ("spmv_launches", ctypes.c_int64), ("spmv_ms", ctypes.c_double), ("spmv_bytes", ctypes.c_double),
+                ("batch_spmv_bytes", ctypes.c_double)]
 
 
 class vk_server_config(ctypes.Structure):
@@ -151,6 +155,8 @@ def lib():
             "vk_server_get_stats": (I, [VP, P(vk_server_stats)]),
             "vk_server_destroy": (None, [VP]),
             "vk_stats_read": (I, [H, P(vk_stats)]),
+            "vk_apply_schedule": (I, [H, I, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32),
+                                      P(ctypes.c_int32), VP, P(ctypes.c_int32)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -302,6 +308,16 @@ class Hierarchy:
         out = np.zeros(self.ndof(level), np.uint8)
         check(lib().vk_export_dirichlet(self.handle, level, _ptr(out)))
         return out.astype(bool)
+
+    def apply_schedule(self, level):
+        """Launch shape of the patch application on a level and the autotuner's candidate times."""
+        import numpy as np
+        v = [ctypes.c_int32() for _ in range(5)]
+        us = np.zeros(16)
+        check(lib().vk_apply_schedule(self.handle, level, ctypes.byref(v[0]), ctypes.byref(v[1]),
+                                      ctypes.byref(v[2]), ctypes.byref(v[3]), _ptr(us), ctypes.byref(v[4])))
+        return dict(split=v[0].value, threads=v[1].value, per_sm=v[2].value, index=v[3].value,
+                    cand_us=us[:v[4].value].tolist())
 
     def stats_reset(self, time_kernels=False):
         check(lib().vk_stats_reset(self.handle, int(time_kernels)))

@@ -3,7 +3,9 @@ tensor cores, FP64 FGMRES per column.
 
 Accuracy target (mixed precision): every column's true residual reaches rtol (FP64 outer iteration),
 and the solution error against the FP64 oracle is reported; a column's result does not depend on the
-other columns of the batch (bit for bit)."""
+other columns of the batch (bit for bit).  Both tensor-core instruction families are covered: tcgen05
+(TMEM accumulators, TMA loads; the default) and warp-level mma.sync, which compute the same rounded
+products and must agree to the FP32 accumulation order."""
 import numpy as np
 import pytest
 
@@ -27,17 +29,21 @@ def vk():
 _h = {}
 
 
-def batch_hierarchy(vk, key, prec):
-    if (key, prec) not in _h:
-        _h[(key, prec)] = vk.Hierarchy(*key, options=vk.default_options(batch_prec=prec))
-    return _h[(key, prec)]
+def batch_hierarchy(vk, key, prec, engine=0):
+    if (key, prec, engine) not in _h:
+        _h[(key, prec, engine)] = vk.Hierarchy(*key, options=vk.default_options(batch_prec=prec, batch_engine=engine))
+    return _h[(key, prec, engine)]
 
 
-@pytest.mark.parametrize("key", [(4, 2, 2), (2, 3, 3), (2, 2, 4)])
+ENGINES = {"tcgen05": 0, "mma_sync": 1}
+
+
+@pytest.mark.parametrize("key", [(4, 2, 2), (2, 3, 3), (2, 2, 4), (4, 2, 4)])
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
-def test_batch_columns_converge_and_match_oracle(vk, key, prec):
+@pytest.mark.parametrize("engine", ["tcgen05", "mma_sync"])
+def test_batch_columns_converge_and_match_oracle(vk, key, prec, engine):
     p = vk.VK_BATCH_BF16 if prec == "bf16" else vk.VK_BATCH_FP16
-    G = batch_hierarchy(vk, key, p)
+    G = batch_hierarchy(vk, key, p, ENGINES[engine])
     n = G.ndof()
     B = si.rhs_batch(n, range(16)).T.copy()             # (16, n): row r = right-hand side r
     X = torch.zeros(16, n, dtype=torch.float64, device="cuda")
@@ -51,12 +57,32 @@ def test_batch_columns_converge_and_match_oracle(vk, key, prec):
         ref = solver.solve(H, B[r], 1e-10, 100)
         # both solve the projected system: the difference is bounded by the residuals' reach
         errs.append(np.linalg.norm(Xh[r] - ref.x) / np.linalg.norm(ref.x))
-    print(f"batch {prec} {key}: iterations {[o['iterations'] for o in out]}, error vs FP64 oracle {max(errs):.2e}")
+    print(f"batch {engine} {prec} {key}: iterations {[o['iterations'] for o in out]}, "
+          f"error vs FP64 oracle {max(errs):.2e}")
     assert max(errs) <= 1e-5
 
 
-def test_batch_column_is_independent_of_the_other_columns(vk):
-    G = batch_hierarchy(vk, (2, 3, 3), vk.VK_BATCH_BF16)
+@pytest.mark.parametrize("key", [(8, 3, 2), (4, 2, 3), (4, 2, 4)])
+def test_tcgen05_and_mma_sync_engines_agree(vk, key):
+    # same 16-bit operands, FP32 accumulation in a different order: V-cycles agree to ~1e-6, so the
+    # FGMRES iteration counts agree within one and the solutions to the reach of rtol
+    n = batch_hierarchy(vk, key, vk.VK_BATCH_BF16, 0).ndof()
+    B = torch.from_numpy(si.rhs_batch(n, range(200, 216)).T.copy()).cuda()
+    out, X = {}, {}
+    for name, e in ENGINES.items():
+        X[name] = torch.zeros(16, n, dtype=torch.float64, device="cuda")
+        out[name] = batch_hierarchy(vk, key, vk.VK_BATCH_BF16, e).solve_batch(B, X[name], rtol=1e-8)
+    for r in range(16):
+        a, b = out["tcgen05"][r], out["mma_sync"][r]
+        assert a["converged"] and b["converged"]
+        assert abs(a["iterations"] - b["iterations"]) <= 1
+        d = float(torch.linalg.vector_norm(X["tcgen05"][r] - X["mma_sync"][r]) / torch.linalg.vector_norm(X["mma_sync"][r]))
+        assert d <= 1e-6, (r, d)
+
+
+@pytest.mark.parametrize("engine", ["tcgen05", "mma_sync"])
+def test_batch_column_is_independent_of_the_other_columns(vk, engine):
+    G = batch_hierarchy(vk, (2, 3, 3), vk.VK_BATCH_BF16, ENGINES[engine])
     n = G.ndof()
     B = si.rhs_batch(n, range(100, 116)).T.copy()
     X = torch.zeros(16, n, dtype=torch.float64, device="cuda")

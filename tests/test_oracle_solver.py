@@ -237,6 +237,40 @@ def test_fgmres_unpreconditioned_converges_within_n_steps():
     assert all(res.hist[i + 1] <= res.hist[i] * (1 + 1e-14) for i in range(len(res.hist) - 1))
 
 
+@pytest.mark.parametrize("orth", ["mgs", "cgs2"])
+def test_fgmres_orthogonalisations_pinned_to_direct_solves(orth):
+    # both readings of the unspecified orthogonalisation: exact preconditioner -> one iteration; no
+    # preconditioner -> at most n steps, iterate = the dense solve, Givens estimate = true residual
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((30, 30)) + 10 * np.eye(30)
+    b = rng.standard_normal(30)
+    res = solver.fgmres(lambda v: A @ v, lambda r: np.linalg.solve(A, r), b, 1e-12, 5, orth=orth)
+    assert res.iters == 1 and np.allclose(res.x, np.linalg.solve(A, b), rtol=1e-10)
+    A = rng.standard_normal((40, 40)) + 4 * np.eye(40)
+    b = rng.standard_normal(40)
+    res = solver.fgmres(lambda v: A @ v, lambda r: r, b, 1e-13, 40, orth=orth)
+    xd = np.linalg.solve(A, b)
+    assert res.converged and res.iters <= 40
+    assert np.linalg.norm(res.x - xd) <= 1e-11 * np.linalg.norm(xd)
+    assert abs(res.hist[-1] - res.true_res) <= 1e-11 * np.linalg.norm(b)
+
+
+def test_fgmres_cgs2_matches_mgs_on_a_well_conditioned_system():
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((40, 40)) + 4 * np.eye(40)
+    b = rng.standard_normal(40)
+    r1 = solver.fgmres(lambda v: A @ v, lambda r: r, b, 1e-13, 40, orth="mgs")
+    r2 = solver.fgmres(lambda v: A @ v, lambda r: r, b, 1e-13, 40, orth="cgs2")
+    xd = np.linalg.solve(A, b)
+    for r in (r1, r2):
+        assert r.converged and np.linalg.norm(r.x - xd) <= 1e-11 * np.linalg.norm(xd)
+        assert abs(r.hist[-1] - r.true_res) <= 1e-11 * np.linalg.norm(b)
+    assert r1.iters == r2.iters
+    assert np.max(np.abs(np.array(r1.hist) - np.array(r2.hist))) <= 1e-12 * np.linalg.norm(b)
+    with pytest.raises(ValueError):
+        solver.fgmres(lambda v: A @ v, lambda r: r, b, 1e-13, 40, orth="householder")
+
+
 def test_multigrid_fgmres_equals_bordered_direct_solve_on_4x4_p2():
     H = solver.Hierarchy(2, 2, 2)   # 2x2 -> 4x4, P2/P1: 187 DoFs on the fine level
     fin = H.finest
