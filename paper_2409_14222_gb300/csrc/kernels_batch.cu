@@ -440,7 +440,25 @@ __global__ void __launch_bounds__(kT) k_mdot_mm(const double* __restrict__ X, in
     double acc[kVB];
 #pragma unroll
     for (int u = 0; u < kVB; ++u) acc[u] = 0.0;
-    for (int64_t idx = int64_t(blockIdx.x) * kT + tid; idx < n16; idx += int64_t(nb) * kT) {
+    // four grid strides per step: 4 (kVB + 1) independent loads in flight per thread
+    const int64_t stride = int64_t(nb) * kT;
+    int64_t idx = int64_t(blockIdx.x) * kT + tid;
+    for (; idx + 3 * stride < n16; idx += 4 * stride) {
+      double w[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) w[e] = W[idx + e * stride];
+#pragma unroll
+      for (int u = 0; u < kVB; ++u)
+        if (v0 + u < nvec) {
+          const double* x = X + ldx * (v0 + u) + idx;
+          const double x0 = x[0], x1 = x[stride], x2 = x[2 * stride], x3 = x[3 * stride];
+          acc[u] = fma(x0, w[0], acc[u]);
+          acc[u] = fma(x1, w[1], acc[u]);
+          acc[u] = fma(x2, w[2], acc[u]);
+          acc[u] = fma(x3, w[3], acc[u]);
+        }
+    }
+    for (; idx < n16; idx += stride) {
       const double w = W[idx];
 #pragma unroll
       for (int u = 0; u < kVB; ++u)
@@ -478,16 +496,28 @@ __global__ void __launch_bounds__(kT) k_mfin_mm(const double* __restrict__ parti
   }
 }
 
-// W[row][r] -= sum_v X_v[row][r] * h[v * kNR + r], summed in ascending v (thread per element)
+// W[row][r] -= sum_v X_v[row][r] * h[v * kNR + r], summed in ascending v.  Each thread takes four
+// elements one block-width apart (same right-hand side r), so four independent loads are in flight
+// for every vector even when there are only a few vectors.
+constexpr int kAxpyE = 4;
 __global__ void __launch_bounds__(kT) k_maxpy_mm(const double* __restrict__ X, int64_t ldx, int nvec,
                                                  const double* __restrict__ h, double* __restrict__ W, int64_t n16) {
-  const int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (idx >= n16) return;
-  const int r = int(idx & 15);
-  double s = 0.0;
-#pragma unroll 8
-  for (int v = 0; v < nvec; ++v) s = fma(X[ldx * v + idx], __ldg(h + v * kNR + r), s);
-  W[idx] -= s;
+  const int64_t base = int64_t(blockIdx.x) * kT * kAxpyE + threadIdx.x;
+  const int r = threadIdx.x & 15;
+  double s[kAxpyE];
+#pragma unroll
+  for (int e = 0; e < kAxpyE; ++e) s[e] = 0.0;
+#pragma unroll 4
+  for (int v = 0; v < nvec; ++v) {
+    const double hv = __ldg(h + v * kNR + r);
+    const double* x = X + ldx * v + base;
+#pragma unroll
+    for (int e = 0; e < kAxpyE; ++e)
+      if (base + e * kT < n16) s[e] = fma(x[e * kT], hv, s[e]);
+  }
+#pragma unroll
+  for (int e = 0; e < kAxpyE; ++e)
+    if (base + e * kT < n16) W[base + e * kT] -= s[e];
 }
 
 // X[row][r] -= mean[r] on rows [lo, lo + len) where mean = sum[r] / len (16 divisions per block)
@@ -678,7 +708,7 @@ int mdot_mm(const double* X, int64_t ldx, int nvec, const double* W, int n, doub
 }
 
 int maxpy_mm(const double* X, int64_t ldx, int nvec, const double* h, double* W, int n, cudaStream_t s) {
-  k_maxpy_mm<<<nblk(int64_t(n) * 16), kT, 0, s>>>(X, ldx, nvec, h, W, int64_t(n) * kNR);
+  k_maxpy_mm<<<nblk(int64_t(n) * 16, kT * kAxpyE), kT, 0, s>>>(X, ldx, nvec, h, W, int64_t(n) * kNR);
   return 1;
 }
 

@@ -30,6 +30,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "gpu.h"
@@ -183,7 +184,7 @@ struct TcShape {
 //   gpos[g 128 + t]        delta row of accumulator lane t = 8 MB j + r (-1: no patch row)
 //   gslot[g G + j]         (byte offset of the core matrices: low, high word; n; patch id), n = 0: empty
 template <int MB, int G, int KS, bool kHalf>
-__global__ void __launch_bounds__(kTcThreads) k_patch_tc(TcClass C, const uint8_t* __restrict__ frag,
+__global__ void __launch_bounds__(kTcThreads, 6) k_patch_tc(TcClass C, const uint8_t* __restrict__ frag,
                                                          const float* __restrict__ ascale,
                                                          const float* __restrict__ rhs, float* __restrict__ delta,
                                                          int* __restrict__ err) {
@@ -444,13 +445,21 @@ int launch_tc(const TcPatches& T, int c, const float* rhs, float* delta, int* er
   const TcClass& C = T.cls[c];
   if (C.ngroups <= 0) return 0;
   static_assert(S::SMEM <= 227 * 1024, "shared memory");
-  cudaFuncSetAttribute(k_patch_tc<MB, G, KS, kHalf>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_patch_tc<MB, G, KS, kHalf>, kTcThreads, S::SMEM);
-  // tensor memory: at most 512 columns per SM are held at once
-  occ = occ < 1 ? 1 : (occ > 512 / S::TCOLS ? 512 / S::TCOLS : occ);
+  auto kern = k_patch_tc<MB, G, KS, kHalf>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  // resident CTAs per SM, from the kernel's registers and shared memory (228 KB per SM, 1 KB of it
+  // reserved per CTA), 2048 threads, and the 512 tensor-memory columns
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, kern);
+  const int regs = fa.numRegs > 0 ? (fa.numRegs + 7) / 8 * 8 : 64;
+  int occ = 65536 / (regs * kTcThreads);
+  occ = std::min(occ, (228 * 1024) / (S::SMEM + int(fa.sharedSizeBytes) + 1024));
+  occ = std::min(occ, 2048 / kTcThreads);
+  occ = std::min(occ, 512 / S::TCOLS);
+  occ = std::max(occ, 1);
   const int grid = C.ngroups < occ * T.nsm ? C.ngroups : occ * T.nsm;
-  k_patch_tc<MB, G, KS, kHalf><<<grid, kTcThreads, S::SMEM, s>>>(C, T.frag, T.ascale, rhs, delta, err);
+  kern<<<grid, kTcThreads, S::SMEM, s>>>(C, T.frag, T.ascale, rhs, delta, err);
   return 1;
 }
 
