@@ -234,8 +234,9 @@ int vk_solve(vk_hierarchy* h, const double* b_dev, double* x_dev, double rtol, i
  * leading dimension ldb >= ndof).  Each column is an independent FGMRES solve with the vk_solve
  * semantics in FP64 (projection, CGS2, Givens, its own convergence test and iteration count); the
  * V-cycle preconditioner runs on all columns together in FP32, with every patch solve of Algorithm 1
- * applied as a small dense product on the tensor cores (BF16 or FP16 inverses scaled per patch,
- * right-hand-side columns scaled separately, FP32 accumulation).  A column's result does not depend
+ * applied as a small dense product on the tensor cores (BF16 or FP16 inverses scaled per patch; with
+ * FP16 each right-hand-side column is also scaled to its largest magnitude over the patch, which
+ * BF16's FP32-sized exponent does not need; FP32 accumulation).  A column's result does not depend
  * on the other columns.  Needs a hierarchy set up with batch_prec != VK_BATCH_NONE.  infos (host,
  * nrhs entries, may be NULL) receive the per-column results; histories are not recorded.
  * Returns VK_ERR_NOT_CONVERGED if a column reached maxit, VK_ERR_NONFINITE if a column diverged. */

@@ -177,6 +177,10 @@ struct SellB {
   const float* valf = nullptr;
   const double* vald = nullptr;
 };
+// y = A (x - m e_p) = A x - m aep with x the FP32 block (gathered as FP32), FP64 values and sums,
+// m[r] = sum[r] / len (the per-column pressure mean), aep = A e_p.  Needs A.vald.
+int mm_sell_zf(const SellB& A, const double* aep, const float* x, const double* sum, int len, double* y,
+               cudaStream_t s);
 // y = b - A x (0), A x (1), b + A x (2), mask ? 0 : A x (3) on [n][16] blocks, values `val` of A
 template <typename T>
 int mm_sell(const SellB& A, const T* val, int mode, const T* b, const uint8_t* mask, const T* x, T* y,
@@ -208,27 +212,29 @@ int givens_mm(double* H, int ldh, int64_t hstride, double* cs, double* sn, doubl
               cudaStream_t s);
 // Tensor-core (tcgen05) patch solves for 16 right-hand sides (kernels_tc.cu).  Size classes of the
 // work list: n <= 40 (3 patches per MMA), n <= 64 (2), n <= 128 (1); each class is cut into groups
-// of that many patches, described by tables built at setup (see k_patch_tc).  Each patch's scaled
-// inverse is stored as ceil(n/8)^2 core matrices of 8x8 16-bit values in frag.
+// of that many patches.  A group's scaled 16-bit inverses are stored as the exact shared-memory image
+// of the MMA's A operand (128 rows = the G patches stacked, 8x8 core matrices), K chunk by K chunk, so
+// one bulk copy of 2048 bytes per K chunk of 8 columns moves a whole group.
 struct TcClass {
   int ngroups = 0;
-  const int* gdof = nullptr;     // [ngroups][G][K]
-  const int* gpos = nullptr;     // [ngroups][128]
-  const int4* gslot = nullptr;   // [ngroups][G]
+  const int* gdof = nullptr;     // [ngroups][G][K] DoF of row k of slot j (-1 past the patch)
+  const int* gpos = nullptr;     // [ngroups][128] delta row of accumulator lane t (-1: none)
+  const int2* gslot = nullptr;   // [ngroups][G] (n, patch id); n = 0: empty slot
+  const int4* gmeta = nullptr;   // [ngroups] (byte offset of the A image: low, high word; bytes; 0)
+  const float* gscale = nullptr; // [ngroups][G] the patch's inverse scale, filled by tc_fill_scale
 };
 struct TcPatches {
   int nsm = 152;
   TcClass cls[3];
   const uint8_t* frag = nullptr;
-  const float* ascale = nullptr;
 };
-// Patches per group, K (padded patch size) and row-block count of class c.
+// Patches per group, K (padded patch size) and size cap of class c.
 constexpr int kTcG[3] = {3, 2, 1}, kTcK[3] = {48, 64, 128}, kTcCap[3] = {40, 64, 128};
-// Bytes of one patch's core matrices.
-inline int64_t tc_bytes(int n) { return 128LL * ((n + 7) / 8) * ((n + 7) / 8); }
-// Pack the FP64 inverses into the core-matrix layout, scaled by 1 / ascale (from pack_mma).
-int pack_tc(const Patches& P, const double* inv64, const float* ascale, const int64_t* foff_tc, void* frag, bool half,
-            cudaStream_t s);
+// Bytes of the A image of a group whose largest patch has n DoFs: ceil(n/8) K chunks of 2048 bytes.
+inline int64_t tc_group_bytes(int nmax) { return 2048LL * ((nmax + 7) / 8); }
+// Pack every group's A image from the FP64 inverses (warp-packed layout), scaled by 1 / ascale[p]
+// (ascale from pack_mma); gscale of every slot as well.
+int pack_tc(const Patches& P, const TcPatches& T, const double* inv64, const float* ascale, bool half, cudaStream_t s);
 // delta[slot][16] = unscaled A_i^{-1} R_i for every patch; *err = VK_ERR_TIMEOUT if a bounded wait
 // expired.  One launch per non-empty size class.
 int patch_apply_tc(const TcPatches& T, bool half, const float* rhs, float* delta, int* err, cudaStream_t s);

@@ -5,9 +5,11 @@
 // The V-cycle preconditioner runs in FP32 (FP32 matrices, FP32 block vectors); the patch solves of
 // Algorithm 1 become a dense contraction delta_i[n x 16] = A_i^{-1}[n x n] R_i[n x 16] per patch,
 // done on the tensor cores with 16-bit inputs (BF16 or FP16) and FP32 accumulation: mma.sync
-// m16n8k16.  A_i^{-1} is stored scaled by its largest magnitude, pre-packed in the A-fragment order
-// of the instruction (one 16-byte load per lane per 16x16 tile); each right-hand-side column of R_i
-// is scaled by its own largest magnitude, so a column's result does not depend on the other columns.
+// m16n8k16 here, tcgen05 in kernels_tc.cu.  A_i^{-1} is stored scaled by its largest magnitude,
+// pre-packed in the A-fragment order of the instruction (one 16-byte load per lane per 16x16 tile);
+// with FP16 each right-hand-side column of R_i is scaled by its own largest magnitude over the patch
+// (FP16's exponent range), with BF16 (FP32's exponent range) the columns are rounded as they are.
+// Either way a column's result does not depend on the other columns.
 // The outer FGMRES (residual w = A z, orthogonalisation, Givens) stays in FP64.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -130,6 +132,62 @@ __global__ void __launch_bounds__(kT) k_sell_mm(int nslices, const int64_t* __re
   st4(o, r);
 }
 
+// y = A z for the FP64 outer iteration, where z = x - m e_p is the FP32 V-cycle output x (exact in
+// FP64) with the per-column pressure mean m removed: y = A x - m (A e_p), A e_p = aep (A's row sums
+// over the pressure columns, zero up to rounding).  The x rows are gathered as FP32 (64 bytes per
+// entry instead of 128), the products and sums are FP64.  m[r] = sum[r] / len.
+__global__ void __launch_bounds__(kT) k_sell_mm_zf(int nslices, const int64_t* __restrict__ sptr,
+                                                   const int* __restrict__ sw, const int* __restrict__ col,
+                                                   const double* __restrict__ val, const int* __restrict__ rowof,
+                                                   const double* __restrict__ aep, const float* __restrict__ x,
+                                                   const double* __restrict__ sum, int len, double* __restrict__ y) {
+  constexpr int kU = 8;
+  const int warp = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= nslices) return;
+  const int t = lane >> 2, q = lane & 3;
+  const int row = rowof[warp * 8 + t];
+  const int w = sw[warp];
+  const int64_t base = sptr[warp] + t;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  int m = 0;
+  for (; m + kU <= w; m += kU) {
+    int c[kU];
+    double v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      c[u] = __ldg(col + base + 8 * int64_t(m + u));
+      v[u] = __ldg(val + base + 8 * int64_t(m + u));
+    }
+    float4 xv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) xv[u] = __ldg(reinterpret_cast<const float4*>(x + int64_t(c[u]) * kNR) + q);
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      acc[0] = fma(v[u], double(xv[u].x), acc[0]);
+      acc[1] = fma(v[u], double(xv[u].y), acc[1]);
+      acc[2] = fma(v[u], double(xv[u].z), acc[2]);
+      acc[3] = fma(v[u], double(xv[u].w), acc[3]);
+    }
+  }
+  for (; m < w; ++m) {
+    const int c = __ldg(col + base + 8 * int64_t(m));
+    const double v = __ldg(val + base + 8 * int64_t(m));
+    const float4 xv = __ldg(reinterpret_cast<const float4*>(x + int64_t(c) * kNR) + q);
+    acc[0] = fma(v, double(xv.x), acc[0]);
+    acc[1] = fma(v, double(xv.y), acc[1]);
+    acc[2] = fma(v, double(xv.z), acc[2]);
+    acc[3] = fma(v, double(xv.w), acc[3]);
+  }
+  if (row < 0) return;
+  const double a = aep[row];
+  double* o = y + int64_t(row) * kNR + 4 * q;
+  reinterpret_cast<double2*>(o)[0] =
+      make_double2(acc[0] - (sum[4 * q] / len) * a, acc[1] - (sum[4 * q + 1] / len) * a);
+  reinterpret_cast<double2*>(o)[1] =
+      make_double2(acc[2] - (sum[4 * q + 2] / len) * a, acc[3] - (sum[4 * q + 3] / len) * a);
+}
+
 // ---- tensor-core patch apply --------------------------------------------------------------------
 template <bool kHalf>
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
@@ -181,11 +239,17 @@ __device__ __forceinline__ void mma_patch(int n, int s0, const int* __restrict__
         rv[kt][nt][q] = v;
         cmax[nt] = fmaxf(cmax[nt], fabsf(v));
       }
-  // per-column scale: lanes 4g .. 4g+3 hold the rows of column nt*8 + g
+  // per-column scale (FP16 only: its 5-bit exponent needs the column in range; BF16 keeps FP32's
+  // exponent range, so its columns are rounded unscaled): lanes 4g .. 4g+3 hold the rows of column
+  // nt*8 + g
+  if constexpr (kHalf) {
 #pragma unroll
-  for (int nt = 0; nt < 2; ++nt) {
-    cmax[nt] = fmaxf(cmax[nt], __shfl_xor_sync(0xffffffffu, cmax[nt], 1));
-    cmax[nt] = fmaxf(cmax[nt], __shfl_xor_sync(0xffffffffu, cmax[nt], 2));
+    for (int nt = 0; nt < 2; ++nt) {
+      cmax[nt] = fmaxf(cmax[nt], __shfl_xor_sync(0xffffffffu, cmax[nt], 1));
+      cmax[nt] = fmaxf(cmax[nt], __shfl_xor_sync(0xffffffffu, cmax[nt], 2));
+    }
+  } else {
+    cmax[0] = cmax[1] = 1.f;
   }
   const float cinv[2] = {cmax[0] > 0.f ? 1.f / cmax[0] : 0.f, cmax[1] > 0.f ? 1.f / cmax[1] : 0.f};
   uint32_t bf[MT][2][2];
@@ -630,6 +694,14 @@ template int mm_sell<float>(const SellB&, const float*, int, const float*, const
                             cudaStream_t);
 template int mm_sell<double>(const SellB&, const double*, int, const double*, const uint8_t*, const double*, double*,
                              cudaStream_t);
+
+int mm_sell_zf(const SellB& A, const double* aep, const float* x, const double* sum, int len, double* y,
+               cudaStream_t s) {
+  if (A.nslices == 0) return 0;
+  k_sell_mm_zf<<<nblk(int64_t(A.nslices) * 32), kT, 0, s>>>(A.nslices, A.sptr, A.swidth, A.col, A.vald, A.rowof, aep,
+                                                            x, sum, len, y);
+  return 1;
+}
 
 int pack_mma(const Patches& P, const double* inv64, const int64_t* foff16, void* frag, float* ascale, bool half,
              cudaStream_t s) {

@@ -104,26 +104,25 @@ __global__ void k_gj_unscramble(double* __restrict__ M, int m, const int* __rest
 }
 
 // x[i] = sum_j Minv[i][j] b[j]: one warp per row, lane-strided partial sums, fixed-order tree.
-__global__ void __launch_bounds__(256) k_dense_gemv(const double* __restrict__ Minv, int n, int ld,
+// x[row] = Minv[row][0:n] . b: one block of 128 threads per row (enough warps per SM for the FP64
+// pipe and the loads), two partial sums per thread, fixed combination order.
+__global__ void __launch_bounds__(128) k_dense_gemv(const double* __restrict__ Minv, int n, int ld,
                                                     const double* __restrict__ b, double* __restrict__ x) {
-  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (row >= n) return;
+  __shared__ double sh[4];
+  const int row = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
   const double* a = Minv + int64_t(row) * ld;
-  // four independent partial sums per lane (columns j, j + 32, j + 64, j + 96 of each step of 128),
-  // so four loads of the row are in flight per lane; fixed combination order
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int j = lane;
-  for (; j + 96 < n; j += 128) {
+  double s0 = 0.0, s1 = 0.0;
+  int j = tid;
+  for (; j + 128 < n; j += 256) {
     s0 = fma(__ldg(a + j), __ldg(b + j), s0);
-    s1 = fma(__ldg(a + j + 32), __ldg(b + j + 32), s1);
-    s2 = fma(__ldg(a + j + 64), __ldg(b + j + 64), s2);
-    s3 = fma(__ldg(a + j + 96), __ldg(b + j + 96), s3);
+    s1 = fma(__ldg(a + j + 128), __ldg(b + j + 128), s1);
   }
-  for (; j < n; j += 32) s0 = fma(__ldg(a + j), __ldg(b + j), s0);
-  double s = (s0 + s1) + (s2 + s3);
+  if (j < n) s0 = fma(__ldg(a + j), __ldg(b + j), s0);
+  double s = s0 + s1;
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) x[row] = s;
+  if (lane == 0) sh[tid >> 5] = s;
+  __syncthreads();
+  if (tid == 0) x[row] = (sh[0] + sh[1]) + (sh[2] + sh[3]);
 }
 
 }  // namespace
@@ -150,7 +149,7 @@ int gauss_jordan_inverse(double* M, int m, int* perm, double* fcol, int* piv, in
 }
 
 int dense_gemv(const double* Minv, int n, int ld, const double* b, double* x, cudaStream_t s) {
-  k_dense_gemv<<<(n * 32 + 255) / 256, 256, 0, s>>>(Minv, n, ld, b, x);
+  k_dense_gemv<<<n, 128, 0, s>>>(Minv, n, ld, b, x);
   return 1;
 }
 

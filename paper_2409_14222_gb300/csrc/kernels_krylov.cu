@@ -172,16 +172,39 @@ __global__ void k_fg_col_put(const double* __restrict__ in, double* __restrict__
 
 // Fixed grid of kReduceBlocks blocks; block b forms the partial dots of rows {b*kT + t + k*kReduceBlocks*kT}
 // for every basis vector i <= j (same partition and order as k_multi_dot).
+// Block b's partial dots of w with V[0..j], kFgVB vectors per pass (w read once per pass).  Each
+// vector's partial is summed in the same element order and combined by the same tree as block_sum,
+// so the values equal those of k_multi_dot.
+constexpr int kFgVB = 8;
 __global__ void __launch_bounds__(kT) k_fg_mdot(const double* __restrict__ V, int64_t ld,
                                                 const FgState* __restrict__ st, const double* __restrict__ w,
                                                 int n, double* __restrict__ partial) {
-  const int j = st->j;
-  for (int i = 0; i <= j; ++i) {
-    const double* v = V + ld * i;
-    double s = 0.0;
-    for (int r = blockIdx.x * kT + threadIdx.x; r < n; r += kReduceBlocks * kT) s = fma(v[r], w[r], s);
-    s = block_sum<kT>(s);
-    if (threadIdx.x == 0) partial[int64_t(i) * kReduceBlocks + blockIdx.x] = s;
+  __shared__ double sh[kFgVB][kT / 32];
+  const int j = st->j, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = 0; i0 <= j; i0 += kFgVB) {
+    double s[kFgVB];
+#pragma unroll
+    for (int u = 0; u < kFgVB; ++u) s[u] = 0.0;
+    for (int r = blockIdx.x * kT + threadIdx.x; r < n; r += kReduceBlocks * kT) {
+      const double wr = w[r];
+#pragma unroll
+      for (int u = 0; u < kFgVB; ++u)
+        if (i0 + u <= j) s[u] = fma(V[ld * (i0 + u) + r], wr, s[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kFgVB; ++u) {
+      for (int o = 16; o > 0; o >>= 1) s[u] += __shfl_xor_sync(0xffffffffu, s[u], o);
+      if (lane == 0) sh[u][warp] = s[u];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int u = 0; u < kFgVB; ++u) {
+        double v = lane < kT / 32 ? sh[u][lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && i0 + u <= j) partial[int64_t(i0 + u) * kReduceBlocks + blockIdx.x] = v;
+      }
+    }
     __syncthreads();
   }
 }
@@ -212,6 +235,7 @@ __global__ void k_fg_maxpy(const double* __restrict__ V, int64_t ld, const FgSta
   const int j = st->j;
   const double* h = mode == 0 ? H + int64_t(j) * ldh : t2;
   double s = 0.0;
+#pragma unroll 4
   for (int i = 0; i <= j; ++i) s = fma(V[ld * i + r], h[i], s);
   w[r] -= s;
 }

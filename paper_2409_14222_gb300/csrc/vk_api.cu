@@ -243,7 +243,7 @@ struct DevLevel {
   float* ascale = nullptr;
   int mt_max = 0;
   vk::gpu::TcPatches tc;                     // tcgen05 path: core-matrix inverses and size classes
-  const int64_t* foff_tc = nullptr;          // byte offset of each patch's core matrices
+  double tc_bytes = 0.0;                     // bytes of all A images of the level
   float *bb = nullptr, *xb = nullptr, *rb = nullptr, *db = nullptr, *delta_f = nullptr;
 };
 
@@ -337,6 +337,7 @@ struct vk_hierarchy {
   double* yb = nullptr;
   int *activeb = nullptr, *itersb = nullptr, *nonfb = nullptr;
   int* tc_err = nullptr;   // set by the tcgen05 patch solves when a bounded wait expires
+  double* aep = nullptr;   // A e_p of the finest level (e_p: 1 on the pressure DoFs)
   ~vk_hierarchy() {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
@@ -465,16 +466,12 @@ void allocate_batch(vk_hierarchy* h) {
       D.foff16 = m.upload(f16);
       D.frag = m.get(size_t(tot) * 16);
       D.ascale = m.get_n<float>(np);
-      // tcgen05 layout: ceil(n/8)^2 core matrices per patch; size classes n <= 40, 64, 128 are ranges
-      // of the work list (sorted by ceil(n/4), largest first), cut into groups of kTcG[c] patches
+      // tcgen05 layout: size classes n <= 40, 64, 128 are ranges of the work list (sorted by ceil(n/4),
+      // largest first), cut into groups of kTcG[c] patches; each group's A image holds ceil(nmax/8)
+      // K chunks of 2048 bytes
       {
         const HostPatchPlan plan = plan_patches(H, h->opt.weights);
-        std::vector<int64_t> ftc(np);
         int64_t btot = 0;
-        for (int p = 0; p < np; ++p) {
-          ftc[p] = btot;
-          btot += vk::gpu::tc_bytes(H.patch_ptr[p + 1] - H.patch_ptr[p]);
-        }
         vk::gpu::TcPatches& T = D.tc;
         for (int c = 0; c < 3; ++c) {
           int lo = np, hi = 0;
@@ -489,8 +486,10 @@ void allocate_batch(vk_hierarchy* h) {
           const int G = vk::gpu::kTcG[c], K = vk::gpu::kTcK[c], R = 128 / G / 8 * 8;
           const int ng = (hi - lo + G - 1) / G;
           std::vector<int> gdof(size_t(ng) * G * K, -1), gpos(size_t(ng) * 128, -1);
-          std::vector<int4> gslot(size_t(ng) * G, make_int4(0, 0, 0, 0));
-          for (int g = 0; g < ng; ++g)
+          std::vector<int2> gslot(size_t(ng) * G, make_int2(0, 0));
+          std::vector<int4> gmeta(size_t(ng), make_int4(0, 0, 0, 0));
+          for (int g = 0; g < ng; ++g) {
+            int nmax = 0;
             for (int j = 0; j < G; ++j) {
               const int w = lo + g * G + j;
               if (w >= hi) break;
@@ -499,17 +498,22 @@ void allocate_batch(vk_hierarchy* h) {
                 gdof[(size_t(g) * G + j) * K + k] = H.patch_dofs[s0 + k];
                 gpos[size_t(g) * 128 + R * j + k] = plan.slot_pos[s0 + k];
               }
-              gslot[size_t(g) * G + j] = make_int4(int(uint32_t(uint64_t(ftc[pw]))), int(uint32_t(uint64_t(ftc[pw]) >> 32)),
-                                                   n, pw);
+              gslot[size_t(g) * G + j] = make_int2(n, pw);
+              nmax = std::max(nmax, n);
             }
+            const int64_t bytes = vk::gpu::tc_group_bytes(nmax);
+            gmeta[g] = make_int4(int(uint32_t(uint64_t(btot))), int(uint32_t(uint64_t(btot) >> 32)), int(bytes), 0);
+            btot += bytes;
+          }
           T.cls[c].ngroups = ng;
           T.cls[c].gdof = m.upload(gdof);
           T.cls[c].gpos = m.upload(gpos);
           T.cls[c].gslot = m.upload(gslot);
+          T.cls[c].gmeta = m.upload(gmeta);
+          T.cls[c].gscale = m.get_n<float>(size_t(ng) * G);
         }
-        D.foff_tc = m.upload(ftc);
         T.frag = static_cast<const uint8_t*>(m.get(size_t(btot)));
-        T.ascale = D.ascale;
+        D.tc_bytes = double(btot);
       }
       D.delta_f = m.get_n<float>(size_t(H.patch_dofs.size()) * NR);
     }
@@ -540,6 +544,15 @@ void allocate_batch(vk_hierarchy* h) {
   h->yb = m.get_n<double>(size_t(NR) * ldh);
   h->activeb = m.get_n<int>(NR);
   h->tc_err = m.get_n<int>(4);
+  {
+    // A e_p of the finest level: each row's sum over the pressure columns
+    const vk::HostLevel& H = h->host[L - 1];
+    std::vector<double> aep(H.ndof, 0.0);
+    for (int i = 0; i < H.ndof; ++i)
+      for (int e = H.A.ptr[i]; e < H.A.ptr[i + 1]; ++e)
+        if (H.A.col[e] >= H.n_u) aep[i] += H.A.val[e];
+    h->aep = m.upload(aep);
+  }
   h->itersb = m.get_n<int>(NR);
   h->nonfb = m.get_n<int>(NR);
 }
@@ -829,8 +842,7 @@ void setup_device(vk_hierarchy* h, cudaStream_t s) {
       DevLevel& D = h->lv[l];
       h->n_launch += vk::gpu::pack_mma(D.pat, static_cast<const double*>(D.pat.factors), D.foff16, D.frag, D.ascale,
                                        half, s);
-      h->n_launch += vk::gpu::pack_tc(D.pat, static_cast<const double*>(D.pat.factors), D.ascale, D.foff_tc,
-                                      const_cast<uint8_t*>(D.tc.frag), half, s);
+      h->n_launch += vk::gpu::pack_tc(D.pat, D.tc, static_cast<const double*>(D.pat.factors), D.ascale, half, s);
     }
     const int64_t mm = int64_t(h->nc + 1) * (h->nc + 1);
     h->n_launch += vk::gpu::to_f32(h->Cinv, h->cinv_f, mm, s);
@@ -866,10 +878,10 @@ void setup_device(vk_hierarchy* h, cudaStream_t s) {
       // 16-bit fragments (padded to 16x16 tiles, as stored) + per patch DoF index, 16 FP32 residual
       // values gathered and 16 FP32 corrections written per slot + per-patch scale/offsets
       double frag = 0.0;
-      for (int p = 0; p < np; ++p) {
-        const int n = F.patch_ptr[p + 1] - F.patch_ptr[p];
-        frag += h->opt.batch_engine == VK_ENGINE_MMA_SYNC ? 16.0 * vk::gpu::frag_size(n) : double(vk::gpu::tc_bytes(n));
-      }
+      if (h->opt.batch_engine == VK_ENGINE_MMA_SYNC)
+        for (int p = 0; p < np; ++p) frag += 16.0 * vk::gpu::frag_size(F.patch_ptr[p + 1] - F.patch_ptr[p]);
+      else
+        frag = h->lv[L - 1].tc_bytes;
       h->bapply_bytes = frag + (4.0 + 64.0 + 64.0 + 4.0) * sn + 28.0 * np;
       h->bapply_flops = 2.0 * 16.0 * sn2;
     }
@@ -1252,7 +1264,9 @@ int solve_batch_impl(vk_hierarchy* h, int nrhs, const double* B, int64_t ldb, do
     ++h->n_vcycle;
     h->n_launch += vk::gpu::to_f64(F.xb, zj, ld, s);
     h->n_launch += vk::gpu::project_mm(zj, F.n_u, F.n_p, h->partb, h->sqb + NR, s);
-    h->n_launch += vk::gpu::mm_sell<double>(F.Ab, F.Ab.vald, 1, nullptr, nullptr, zj, h->wb, s);
+    // w = A z from the FP32 V-cycle output and the projection's column sums (z itself is kept for
+    // the solution update)
+    h->n_launch += vk::gpu::mm_sell_zf(F.Ab, h->aep, F.xb, h->sqb + NR, F.n_p, h->wb, s);
     h->n_launch += vk::gpu::mdot_mm(h->Vb, ld, j + 1, h->wb, n, h->partb, h->hcolb, nullptr, s);
     h->n_launch += vk::gpu::maxpy_mm(h->Vb, ld, j + 1, h->hcolb, h->wb, n, s);
     h->n_launch += vk::gpu::mdot_mm(h->Vb, ld, j + 1, h->wb, n, h->partb, h->t2b, h->hcolb, s);
