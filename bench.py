@@ -617,7 +617,7 @@ def main():
     ap.add_argument("--levels", type=int, default=0, help="override the level count (profiling variants only)")
     ap.add_argument("--rtol", type=float, default=0.0, help="override the tolerance (profiling variants only)")
     ap.add_argument("--batch-maxit", type=int, default=60, help="cfg4: FGMRES basis size per right-hand side")
-    ap.add_argument("--engine", default="mma_sync", choices=["tcgen05", "mma_sync"],
+    ap.add_argument("--engine", default="tcgen05", choices=["tcgen05", "mma_sync"],
                     help="cfg4: tensor-core instruction family of the patch solves")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "vk":

@@ -99,6 +99,11 @@ typedef struct vk_options {
   int32_t apply_schedule; /* -1: autotune (or the default shape when autotune = 0); >= 0: use that
                              candidate on every level (candidates are listed at vk_apply_schedule) */
   int32_t batch_engine;   /* VK_ENGINE_*: tensor-core instruction family of vk_solve_batch          */
+  int32_t test_expire_wait; /* test of the bounded device waits: 1 makes the first finest-level
+                               tcgen05 patch sweep after setup announce one bulk copy without
+                               issuing it, so its wait expires (about 2 s), the kernel ends cleanly
+                               and vk_solve_batch returns VK_ERR_TIMEOUT; later calls run normally.
+                               0 (default) in normal use                                           */
 } vk_options;
 
 /* Device memory provider.  alloc returns device memory of at least `bytes` (256-byte aligned) or
@@ -274,8 +279,10 @@ typedef struct vk_stats {
                               s*sum(n_i^2) inverse entries (s = 8 FP64, 4 FP32) + 20*sum(n_i)
                               (DoF index, gathered residual, written correction) + 16 per patch     */
   double apply_flops;      /* 2*sum(n_i^2) flops of one finest-level patch-apply launch             */
-  double batch_apply_bytes;/* algorithmic bytes of one finest-level tensor-core patch apply of
-                              vk_solve_batch: 16-bit fragments as stored + 136*sum(n_i) + 28/patch   */
+  double batch_apply_bytes;/* compulsory bytes of one finest-level tensor-core patch apply of
+                              vk_solve_batch: 16-bit inverses as stored + index tables as read +
+                              64 per DoF (its 16 FP32 residual values, read once) + 64 per slot
+                              (16 FP32 corrections written)                                          */
   double batch_apply_flops;/* 32*sum(n_i^2) flops of that launch (16 right-hand sides)              */
   int64_t spmv_launches;   /* finest-level V-cycle residual SpMV launches bracketed by CUDA events   */
   double spmv_ms;          /* their summed event durations (ms)                                      */

@@ -132,62 +132,6 @@ __global__ void __launch_bounds__(kT) k_sell_mm(int nslices, const int64_t* __re
   st4(o, r);
 }
 
-// y = A z for the FP64 outer iteration, where z = x - m e_p is the FP32 V-cycle output x (exact in
-// FP64) with the per-column pressure mean m removed: y = A x - m (A e_p), A e_p = aep (A's row sums
-// over the pressure columns, zero up to rounding).  The x rows are gathered as FP32 (64 bytes per
-// entry instead of 128), the products and sums are FP64.  m[r] = sum[r] / len.
-__global__ void __launch_bounds__(kT) k_sell_mm_zf(int nslices, const int64_t* __restrict__ sptr,
-                                                   const int* __restrict__ sw, const int* __restrict__ col,
-                                                   const double* __restrict__ val, const int* __restrict__ rowof,
-                                                   const double* __restrict__ aep, const float* __restrict__ x,
-                                                   const double* __restrict__ sum, int len, double* __restrict__ y) {
-  constexpr int kU = 8;
-  const int warp = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (warp >= nslices) return;
-  const int t = lane >> 2, q = lane & 3;
-  const int row = rowof[warp * 8 + t];
-  const int w = sw[warp];
-  const int64_t base = sptr[warp] + t;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  int m = 0;
-  for (; m + kU <= w; m += kU) {
-    int c[kU];
-    double v[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      c[u] = __ldg(col + base + 8 * int64_t(m + u));
-      v[u] = __ldg(val + base + 8 * int64_t(m + u));
-    }
-    float4 xv[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) xv[u] = __ldg(reinterpret_cast<const float4*>(x + int64_t(c[u]) * kNR) + q);
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      acc[0] = fma(v[u], double(xv[u].x), acc[0]);
-      acc[1] = fma(v[u], double(xv[u].y), acc[1]);
-      acc[2] = fma(v[u], double(xv[u].z), acc[2]);
-      acc[3] = fma(v[u], double(xv[u].w), acc[3]);
-    }
-  }
-  for (; m < w; ++m) {
-    const int c = __ldg(col + base + 8 * int64_t(m));
-    const double v = __ldg(val + base + 8 * int64_t(m));
-    const float4 xv = __ldg(reinterpret_cast<const float4*>(x + int64_t(c) * kNR) + q);
-    acc[0] = fma(v, double(xv.x), acc[0]);
-    acc[1] = fma(v, double(xv.y), acc[1]);
-    acc[2] = fma(v, double(xv.z), acc[2]);
-    acc[3] = fma(v, double(xv.w), acc[3]);
-  }
-  if (row < 0) return;
-  const double a = aep[row];
-  double* o = y + int64_t(row) * kNR + 4 * q;
-  reinterpret_cast<double2*>(o)[0] =
-      make_double2(acc[0] - (sum[4 * q] / len) * a, acc[1] - (sum[4 * q + 1] / len) * a);
-  reinterpret_cast<double2*>(o)[1] =
-      make_double2(acc[2] - (sum[4 * q + 2] / len) * a, acc[3] - (sum[4 * q + 3] / len) * a);
-}
-
 // ---- tensor-core patch apply --------------------------------------------------------------------
 template <bool kHalf>
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
@@ -694,14 +638,6 @@ template int mm_sell<float>(const SellB&, const float*, int, const float*, const
                             cudaStream_t);
 template int mm_sell<double>(const SellB&, const double*, int, const double*, const uint8_t*, const double*, double*,
                              cudaStream_t);
-
-int mm_sell_zf(const SellB& A, const double* aep, const float* x, const double* sum, int len, double* y,
-               cudaStream_t s) {
-  if (A.nslices == 0) return 0;
-  k_sell_mm_zf<<<nblk(int64_t(A.nslices) * 32), kT, 0, s>>>(A.nslices, A.sptr, A.swidth, A.col, A.vald, A.rowof, aep,
-                                                            x, sum, len, y);
-  return 1;
-}
 
 int pack_mma(const Patches& P, const double* inv64, const int64_t* foff16, void* frag, float* ascale, bool half,
              cudaStream_t s) {

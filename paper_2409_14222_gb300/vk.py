@@ -63,7 +63,8 @@ class vk_options(ctypes.Structure):
                 ("use_graph", ctypes.c_int32), ("host_threads", ctypes.c_int32), ("host_only", ctypes.c_int32),
                 ("max_iterations", ctypes.c_int32), ("batch_prec", ctypes.c_int32),
                 ("batch_max_iterations", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("apply_schedule", ctypes.c_int32), ("batch_engine", ctypes.c_int32)]
+                ("apply_schedule", ctypes.c_int32), ("batch_engine", ctypes.c_int32),
+                ("test_expire_wait", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)

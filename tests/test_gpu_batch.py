@@ -6,6 +6,8 @@ and the solution error against the FP64 oracle is reported; a column's result do
 other columns of the batch (bit for bit).  Both tensor-core instruction families are covered: tcgen05
 (TMEM accumulators, TMA loads; the default) and warp-level mma.sync, which compute the same rounded
 products and must agree to the FP32 accumulation order."""
+import time
+
 import numpy as np
 import pytest
 
@@ -130,3 +132,26 @@ def test_batch_full_size_512_p2_residuals_on_oracle_matrix(vk):
         print(f"512^2 column {r}: {out[r]['iterations']} iterations, oracle-matrix residual {res:.2e}")
         assert res <= 1.5e-8
         assert abs(Xh[r][s.n_u:].sum()) <= 1e-8 * np.abs(Xh[r]).sum()
+
+
+def test_tcgen05_bounded_wait_expires_and_recovers(vk):
+    # failure detection without a fault: the test hook makes the first finest sweep announce one bulk
+    # copy without issuing it; the producer's bounded wait expires, every role of that CTA stops, the
+    # kernel drains and frees its tensor memory, and the call reports VK_ERR_TIMEOUT.  The context and
+    # the hierarchy stay usable: the next call runs normally and converges.
+    G = vk.Hierarchy(4, 2, 2, options=vk.default_options(batch_prec=vk.VK_BATCH_BF16,
+                                                         batch_engine=vk.VK_ENGINE_TCGEN05, test_expire_wait=1))
+    n = G.ndof()
+    B = torch.from_numpy(si.rhs_batch(n, range(16)).T.copy()).cuda()
+    X = torch.zeros(16, n, dtype=torch.float64, device="cuda")
+    t0 = time.time()
+    with pytest.raises(vk.VkError) as e:
+        G.solve_batch(B, X, rtol=1e-8)
+    assert e.value.code == vk.vk.VK_ERR_TIMEOUT
+    assert time.time() - t0 < 60
+    out = G.solve_batch(B, X, rtol=1e-8)
+    assert all(o["converged"] for o in out)
+    ref = batch_hierarchy(vk, (4, 2, 2), vk.VK_BATCH_BF16, ENGINES["tcgen05"])
+    X2 = torch.zeros_like(X)
+    ref.solve_batch(B, X2, rtol=1e-8)
+    assert torch.equal(X, X2)
