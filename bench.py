@@ -244,6 +244,8 @@ def run_vk(args, cfg):
         opts.factor_prec = vk.VK_PREC_F64E
     if args.no_graph:
         opts.use_graph = 0
+    if args.spmv_warps:
+        opts.spmv_warps = args.spmv_warps
     stream = torch.cuda.current_stream()
     G = vk.Hierarchy(Nc, L, k, options=opts)
     ndof = G.ndof()
@@ -614,6 +616,7 @@ def main():
     ap.add_argument("--slots", type=int, default=4, help="cfg5: concurrent solves")
     ap.add_argument("--no-baseline", action="store_true", help="cfg5: skip the one-at-a-time FP64 pass")
     ap.add_argument("--batch-prec", default="bf16", choices=["bf16", "fp16"], help="cfg4: 16-bit inverse format")
+    ap.add_argument("--spmv-warps", type=int, default=0, help="SELL threads-per-row rule (warps per SM); 0 = default")
     ap.add_argument("--levels", type=int, default=0, help="override the level count (profiling variants only)")
     ap.add_argument("--rtol", type=float, default=0.0, help="override the tolerance (profiling variants only)")
     ap.add_argument("--batch-maxit", type=int, default=60, help="cfg4: FGMRES basis size per right-hand side")

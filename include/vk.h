@@ -104,6 +104,8 @@ typedef struct vk_options {
                                issuing it, so its wait expires (about 2 s), the kernel ends cleanly
                                and vk_solve_batch returns VK_ERR_TIMEOUT; later calls run normally.
                                0 (default) in normal use                                           */
+  int32_t spmv_warps;     /* SELL layout of the sparse products: threads per row = the smallest of
+                             1, 2, 4, 8 that gives at least this many warps per SM (default 48)    */
 } vk_options;
 
 /* Device memory provider.  alloc returns device memory of at least `bytes` (256-byte aligned) or

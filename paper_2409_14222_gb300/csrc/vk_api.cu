@@ -111,10 +111,11 @@ struct HostSell {
   std::vector<double> val;
 };
 
-// Threads per row for a SELL matrix: the smallest of 1, 2, 4, 8 that gives at least 48 warps per SM
-// (GB300: 152 SMs), so load latency is hidden without an over-long per-thread dependency chain.
-int sell_tpr(int nrows) {
-  const int64_t want = 152LL * 48 * 32;
+// Threads per row for a SELL matrix: the smallest of 1, 2, 4, 8 that gives at least `warps_per_sm`
+// warps per SM (GB300: 152 SMs), so load latency is hidden without an over-long per-thread
+// dependency chain.
+int sell_tpr(int nrows, int warps_per_sm) {
+  const int64_t want = 152LL * warps_per_sm * 32;
   for (int t = 1; t < 8; t *= 2)
     if (int64_t(nrows) * t >= want) return t;
   return 8;
@@ -377,6 +378,7 @@ void validate(const vk_problem* p, const vk_options* o) {
   if (o->batch_prec < VK_BATCH_NONE || o->batch_prec > VK_BATCH_FP16) raise(VK_ERR_ARG, "bad batch_prec");
   if (o->batch_engine != VK_ENGINE_TCGEN05 && o->batch_engine != VK_ENGINE_MMA_SYNC) raise(VK_ERR_ARG, "bad batch_engine");
   if (o->test_expire_wait != 0 && o->test_expire_wait != 1) raise(VK_ERR_ARG, "test_expire_wait must be 0 or 1");
+  if (o->spmv_warps < 1 || o->spmv_warps > 4096) raise(VK_ERR_ARG, "spmv_warps must be in 1..4096");
   if (o->apply_schedule < -1 || o->apply_schedule >= int(apply_candidates().size()))
     raise(VK_ERR_ARG, "apply_schedule must be -1 or a candidate index");
   if (o->batch_prec != VK_BATCH_NONE) {
@@ -397,8 +399,8 @@ void build_host(vk_hierarchy* h) {
   }
 }
 
-vk::gpu::Sell upload_sell(DeviceMemory& m, const vk::HostCsr& A) {
-  const int tpr = sell_tpr(A.nrows);
+vk::gpu::Sell upload_sell(DeviceMemory& m, const vk::HostCsr& A, int warps_per_sm) {
+  const int tpr = sell_tpr(A.nrows, warps_per_sm);
   HostSell S = build_sell(A, tpr);
   vk::gpu::Sell d;
   d.tpr = tpr;
@@ -562,12 +564,12 @@ void allocate_device(vk_hierarchy* h) {
     D.ndof = H.ndof;
     D.n_u = H.n_u;
     D.n_p = H.n_p;
-    D.A = upload_sell(m, H.A);
+    D.A = upload_sell(m, H.A, h->opt.spmv_warps);
     D.Acsr = upload_csr(m, H.A);
     D.dir = m.upload(H.dir);
     if (l > 0) {
-      D.P = upload_sell(m, H.P);
-      D.R = upload_sell(m, H.R);
+      D.P = upload_sell(m, H.P, h->opt.spmv_warps);
+      D.R = upload_sell(m, H.R, h->opt.spmv_warps);
     }
     D.b = m.get_n<double>(H.ndof);
     D.x = m.get_n<double>(H.ndof);
@@ -1370,6 +1372,7 @@ void vk_default_options(vk_options* o) {
   o->autotune = 1;
   o->apply_schedule = -1;
   o->batch_engine = VK_ENGINE_TCGEN05;
+  o->spmv_warps = 48;
 }
 
 const char* vk_last_error(void) { return g_err.c_str(); }
