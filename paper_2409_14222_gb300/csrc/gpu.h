@@ -69,8 +69,6 @@ struct Patches {
 
 // ---- sparse / vector kernels (kernels_sparse.cu) -------------------------------------------------
 int sell_residual(const Sell& A, const double* b, const double* x, double* y, cudaStream_t s);
-int csr_restrict(const Csr& R, const uint8_t* dir_coarse, const double* r, double* rc, cudaStream_t s);
-int csr_prolong_add(const Csr& P, const double* ec, double* x, cudaStream_t s);
 // rc = R r with rc = 0 at coarse Dirichlet DoFs; x += P ec  (SELL forms of R and P)
 int sell_restrict(const Sell& R, const uint8_t* dir_coarse, const double* r, double* rc, cudaStream_t s);
 int sell_prolong_add(const Sell& P, const double* ec, double* x, cudaStream_t s);

@@ -317,7 +317,15 @@ __global__ void __launch_bounds__(kT) k_scatter_mm(int ndof, const int* __restri
     z = r[idx];
   } else {
     z = 0.f;
-    for (int e = dptr[i]; e < dptr[i + 1]; ++e) z += delta[int64_t(e) * kNR + rr];
+    const int e0 = dptr[i], e1 = dptr[i + 1];
+    // the first 8 corrections as one predicated batch (all loads in flight), the rest in order
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = e0 + u < e1 ? delta[int64_t(e0 + u) * kNR + rr] : 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (e0 + u < e1) z += v[u];
+    for (int e = e0 + 8; e < e1; ++e) z += delta[int64_t(e) * kNR + rr];
   }
   switch (mode) {
     case 0:

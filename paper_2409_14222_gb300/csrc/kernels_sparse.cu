@@ -85,27 +85,6 @@ int launch_sell(const Sell& A, const double* b, const uint8_t* mask, const doubl
   return 1;
 }
 
-__global__ void k_csr_restrict(int nrows, const int* __restrict__ ptr, const int* __restrict__ col,
-                               const double* __restrict__ val, const uint8_t* __restrict__ dir,
-                               const double* __restrict__ r, double* __restrict__ rc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nrows) return;
-  double s = 0.0;
-  if (!dir[i])
-    for (int e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], r[col[e]], s);
-  rc[i] = s;
-}
-
-__global__ void k_csr_prolong_add(int nrows, const int* __restrict__ ptr, const int* __restrict__ col,
-                                  const double* __restrict__ val, const double* __restrict__ ec,
-                                  double* __restrict__ x) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nrows) return;
-  double s = 0.0;
-  for (int e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], ec[col[e]], s);
-  x[i] += s;
-}
-
 template <int T>
 __device__ double block_sum(double v) {
   __shared__ double sh[T / 32];
@@ -213,17 +192,7 @@ int sell_prolong_add(const Sell& P, const double* ec, double* x, cudaStream_t s)
   return launch_sell<2>(P, x, nullptr, ec, x, s);
 }
 
-int csr_restrict(const Csr& R, const uint8_t* dir_coarse, const double* r, double* rc, cudaStream_t s) {
-  if (R.nrows == 0) return 0;
-  k_csr_restrict<<<blocks_for(R.nrows), kThreads, 0, s>>>(R.nrows, R.ptr, R.col, R.val, dir_coarse, r, rc);
-  return 1;
-}
 
-int csr_prolong_add(const Csr& P, const double* ec, double* x, cudaStream_t s) {
-  if (P.nrows == 0) return 0;
-  k_csr_prolong_add<<<blocks_for(P.nrows), kThreads, 0, s>>>(P.nrows, P.ptr, P.col, P.val, ec, x);
-  return 1;
-}
 
 int dot_partials(const double* x, const double* y, int n, double* partial, cudaStream_t s) {
   k_dot_partials<<<kReduceBlocks, kThreads, 0, s>>>(x, y, n, partial);
