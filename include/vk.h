@@ -268,6 +268,16 @@ int vk_export_csr(const vk_hierarchy* h, int level, int which, int32_t* ptr, int
  * Patches are ordered vertices, then edges (horizontal, vertical, diagonal), then cells. */
 int vk_export_patches(const vk_hierarchy* h, int level, int32_t* ptr, int32_t* dofs, int8_t* kind);
 
+/* Velocity and pressure DoF counts of a level (ndof = n_u + n_p; Case 1 of Sec. 3: continuous P_k
+ * velocity, continuous P_{k-1} pressure).  Either pointer may be NULL.  Works on host-only hierarchies. */
+int vk_ndof(const vk_hierarchy* h, int level, int64_t* n_u, int64_t* n_p);
+
+/* Coordinates of every DoF of a level in the canonical order: xy (host, 2*ndof doubles, may be NULL)
+ * receives (x, y) of the DoF's Lagrange node (equispaced nodes of the structured mesh of Sec. 4);
+ * kind (host, ndof bytes, may be NULL) receives 0 / 1 for the x / y velocity component and 2 for
+ * pressure.  Works on host-only hierarchies. */
+int vk_export_dof_coords(const vk_hierarchy* h, int level, double* xy, int8_t* kind);
+
 /* Copies the Dirichlet flags (1 = no-slip velocity DoF) of a level into a host array of ndof bytes. */
 int vk_export_dirichlet(const vk_hierarchy* h, int level, uint8_t* flags);
 

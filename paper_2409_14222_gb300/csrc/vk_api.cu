@@ -1629,6 +1629,46 @@ int vk_export_patches(const vk_hierarchy* h, int level, int32_t* ptr, int32_t* d
   });
 }
 
+int vk_ndof(const vk_hierarchy* h, int level, int64_t* n_u, int64_t* n_p) {
+  return guard([&] {
+    check_level(h, level);
+    const vk::HostLevel& L = h->host[level];
+    if (n_u) *n_u = L.n_u;
+    if (n_p) *n_p = L.n_p;
+    return VK_OK;
+  });
+}
+
+int vk_export_dof_coords(const vk_hierarchy* h, int level, double* xy, int8_t* kind) {
+  return guard([&] {
+    check_level(h, level);
+    if (!xy && !kind) raise(VK_ERR_ARG, "null outputs");
+    const vk::HostLevel& L = h->host[level];
+    const int nv = L.nv1, np = L.np1, kN = L.k * L.N, k1N = (L.k - 1) * L.N;
+    for (int d = 0; d < L.ndof; ++d) {
+      double x, y;
+      int8_t c;
+      if (d < L.n_u) {
+        const int node = d / 2;
+        x = double(node % nv) / kN;
+        y = double(node / nv) / kN;
+        c = int8_t(d & 1);
+      } else {
+        const int q = d - L.n_u;
+        x = double(q % np) / k1N;
+        y = double(q / np) / k1N;
+        c = 2;
+      }
+      if (xy) {
+        xy[2 * int64_t(d)] = x;
+        xy[2 * int64_t(d) + 1] = y;
+      }
+      if (kind) kind[d] = c;
+    }
+    return VK_OK;
+  });
+}
+
 int vk_export_dirichlet(const vk_hierarchy* h, int level, uint8_t* flags) {
   return guard([&] {
     check_level(h, level);

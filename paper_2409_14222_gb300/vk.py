@@ -40,7 +40,7 @@ SYMBOLS = [
     "vk_level_info", "vk_lambda", "vk_residual", "vk_vanka", "vk_smooth", "vk_restrict", "vk_prolong",
     "vk_coarse_solve", "vk_vcycle", "vk_solve", "vk_solve_host", "vk_csr_dims", "vk_export_csr",
     "vk_export_patches", "vk_export_dirichlet", "vk_hessenberg_eigenvalues", "vk_stats_reset", "vk_stats_read",
-    "vk_vanka_noalloc", "vk_solve_batch", "vk_apply_schedule", "vk_default_server_config", "vk_server_create", "vk_server_submit", "vk_server_wait",
+    "vk_vanka_noalloc", "vk_solve_batch", "vk_apply_schedule", "vk_ndof", "vk_export_dof_coords", "vk_default_server_config", "vk_server_create", "vk_server_submit", "vk_server_wait",
     "vk_server_get_stats", "vk_server_destroy",
 ]
 
@@ -147,6 +147,8 @@ def lib():
             "vk_export_csr": (I, [H, I, I, VP, VP, VP]),
             "vk_export_patches": (I, [H, I, VP, VP, VP]),
             "vk_export_dirichlet": (I, [H, I, VP]),
+            "vk_ndof": (I, [H, I, P(I64), P(I64)]),
+            "vk_export_dof_coords": (I, [H, I, VP, VP]),
             "vk_hessenberg_eigenvalues": (I, [I, VP, VP, VP]),
             "vk_stats_reset": (I, [H, I]),
             "vk_default_server_config": (None, [P(vk_server_config)]),
@@ -303,6 +305,22 @@ class Hierarchy:
         kind = np.zeros(info["npatch"], np.int8)
         check(lib().vk_export_patches(self.handle, level, _ptr(ptr), _ptr(dofs), _ptr(kind)))
         return ptr, dofs, kind
+
+    def dof_counts(self, level=None):
+        """(n_u, n_p) of a level (vk_ndof)."""
+        nu_, np_ = ctypes.c_int64(), ctypes.c_int64()
+        check(lib().vk_ndof(self.handle, self.nlevels - 1 if level is None else level, ctypes.byref(nu_),
+                            ctypes.byref(np_)))
+        return nu_.value, np_.value
+
+    def export_dof_coords(self, level):
+        """(xy[ndof, 2], kind[ndof]) of a level: node coordinates, 0/1 velocity component, 2 pressure."""
+        import numpy as np
+        n = self.ndof(level)
+        xy = np.zeros((n, 2), np.float64)
+        kind = np.zeros(n, np.int8)
+        check(lib().vk_export_dof_coords(self.handle, level, _ptr(xy), _ptr(kind)))
+        return xy, kind
 
     def export_dirichlet(self, level):
         import numpy as np

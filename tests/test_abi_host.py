@@ -107,3 +107,21 @@ def test_footprint_builds_every_device_layout_on_the_host(vk, key):
     # vk_footprint builds the SELL forms of A, P and R (with their column-range check) and the patch
     # plans without a device; P has more rows than columns, so its padding must point at column 0
     assert vk.footprint(*key) > 0
+
+
+@pytest.mark.parametrize("Nc,L,k", [(4, 2, 2), (2, 2, 3), (2, 2, 4)])
+def test_dof_counts_and_coordinates_equal_the_oracle_layout(vk, Nc, L, k):
+    h = vk.Hierarchy(Nc, L, k, host_only=True)
+    for l in range(L):
+        s = fem.Space(Nc * 2 ** l, k)
+        assert h.dof_counts(l) == (s.n_u, s.n_p)
+        xy, kind = h.export_dof_coords(l)
+        vx, vy = s.vnode_xy()
+        px, py = s.pnode_xy()
+        assert np.array_equal(xy[0:s.n_u:2, 0], vx) and np.array_equal(xy[1:s.n_u:2, 0], vx)
+        assert np.array_equal(xy[0:s.n_u:2, 1], vy) and np.array_equal(xy[1:s.n_u:2, 1], vy)
+        assert np.array_equal(xy[s.n_u:, 0], px) and np.array_equal(xy[s.n_u:, 1], py)
+        assert np.array_equal(kind[:s.n_u], np.tile([0, 1], s.n_u // 2)) and np.all(kind[s.n_u:] == 2)
+        # Dirichlet flags are exactly the velocity DoFs on the boundary of the unit square
+        on_bnd = (xy[:, 0] == 0) | (xy[:, 1] == 0) | (xy[:, 0] == 1) | (xy[:, 1] == 1)
+        assert np.array_equal(h.export_dirichlet(l), on_bnd & (kind < 2))
