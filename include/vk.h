@@ -106,6 +106,8 @@ typedef struct vk_options {
                                0 (default) in normal use                                           */
   int32_t spmv_warps;     /* SELL layout of the sparse products: threads per row = the smallest of
                              1, 2, 4, 8 that gives at least this many warps per SM (default 48)    */
+  int32_t batch_coarse_fp32; /* vk_solve_batch: 0 (default) keeps the coarsest-level dense solve in
+                             FP64 inside the FP32 V-cycle; 1 applies an FP32 copy of the inverse   */
 } vk_options;
 
 /* Device memory provider.  alloc returns device memory of at least `bytes` (256-byte aligned) or
@@ -243,7 +245,8 @@ int vk_solve(vk_hierarchy* h, const double* b_dev, double* x_dev, double rtol, i
  * V-cycle preconditioner runs on all columns together in FP32, with every patch solve of Algorithm 1
  * applied as a small dense product on the tensor cores (BF16 or FP16 inverses scaled per patch; with
  * FP16 each right-hand-side column is also scaled to its largest magnitude over the patch, which
- * BF16's FP32-sized exponent does not need; FP32 accumulation).  A column's result does not depend
+ * BF16's FP32-sized exponent does not need; FP32 accumulation); the coarsest-level solve stays FP64
+ * unless batch_coarse_fp32 is set.  A column's result does not depend
  * on the other columns.  Needs a hierarchy set up with batch_prec != VK_BATCH_NONE.  infos (host,
  * nrhs entries, may be NULL) receive the per-column results; histories are not recorded.
  * Returns VK_ERR_NOT_CONVERGED if a column reached maxit, VK_ERR_NONFINITE if a column diverged. */

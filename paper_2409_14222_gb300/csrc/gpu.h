@@ -186,6 +186,8 @@ int patch_apply_mma(const Patches& P, const int64_t* foff16, const void* frag, c
 int scatter_mm(const Patches& P, int ndof, const uint8_t* dir, const float* r, const float* delta, int mode,
                float theta, float c1, float c2, float* zout, float* d, float* x, cudaStream_t s);
 int coarse_mm(const float* Minv, int n, int ld, const float* B, float* X, cudaStream_t s);
+// FP64 coarse solve of 16 right-hand sides: X[n][16] = Minv[0:n, 0:n] B[n][16]
+int coarse_mm64(const double* Minv, int n, int ld, const double* B, double* X, cudaStream_t s);
 int to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
 int to_f64(const float* a, double* b, int64_t n, cudaStream_t s);
 int gather_cols(const double* B, int64_t ld, int nrhs, double* Y, int n, cudaStream_t s);

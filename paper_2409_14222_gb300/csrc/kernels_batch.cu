@@ -415,6 +415,59 @@ __global__ void __launch_bounds__(256) k_coarse_mm(const float* __restrict__ Min
   if (row < n) X[int64_t(row) * kNR + rr] = acc;
 }
 
+// ---- coarse solve, FP64: X[n][16] = Minv[0:n,0:n] B[n][16] --------------------------------------
+// Same blocking as k_coarse_mm (16 rows x 16 right-hand sides per block) with 64-wide K chunks of
+// doubles; the next chunk's loads are issued into registers before the current chunk's products.
+constexpr int kCoarseK64 = 64;
+__global__ void __launch_bounds__(256) k_coarse_mm64(const double* __restrict__ Minv, int n, int ld,
+                                                     const double* __restrict__ B, double* __restrict__ X) {
+  __shared__ double2 As[kCoarseRows][kCoarseK64 / 2 + 1];
+  __shared__ double Bs[kCoarseK64][kNR];
+  const int tid = threadIdx.x;
+  const int rl = tid >> 4, rr = tid & 15;
+  const int row0 = blockIdx.x * kCoarseRows;
+  double2 pa[2], pb[2];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + 256 * u;                  // 0..511: A tile as 16 rows x 32 double2
+      const int ar = e >> 5, ac = (e & 31) * 2;
+      const int row = row0 + ar, k = k0 + ac;
+      double2 v = make_double2(0.0, 0.0);
+      if (row < n) {
+        const double* src = Minv + int64_t(row) * ld + k;
+        v.x = k < n ? src[0] : 0.0;
+        v.y = k + 1 < n ? src[1] : 0.0;
+      }
+      pa[u] = v;
+      const int bk = e >> 3, bq = (e & 7) * 2;        // B tile as 64 rows x 8 double2
+      pb[u] = (k0 + bk < n) ? *reinterpret_cast<const double2*>(B + int64_t(k0 + bk) * kNR + bq)
+                            : make_double2(0.0, 0.0);
+    }
+  };
+  double acc = 0.0;
+  load(0);
+  for (int k0 = 0; k0 < n; k0 += kCoarseK64) {
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + 256 * u;
+      As[e >> 5][e & 31] = pa[u];
+      *reinterpret_cast<double2*>(&Bs[e >> 3][(e & 7) * 2]) = pb[u];
+    }
+    __syncthreads();
+    if (k0 + kCoarseK64 < n) load(k0 + kCoarseK64);
+#pragma unroll 8
+    for (int c = 0; c < kCoarseK64 / 2; ++c) {
+      const double2 a = As[rl][c];
+      acc = fma(a.x, Bs[2 * c][rr], acc);
+      acc = fma(a.y, Bs[2 * c + 1][rr], acc);
+    }
+  }
+  const int row = row0 + rl;
+  if (row < n) X[int64_t(row) * kNR + rr] = acc;
+}
+
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (i < n) b[i] = float(a[i]);
@@ -690,6 +743,11 @@ int scatter_mm(const Patches& P, int ndof, const uint8_t* dir, const float* r, c
 
 int coarse_mm(const float* Minv, int n, int ld, const float* B, float* X, cudaStream_t s) {
   k_coarse_mm<<<(n + kCoarseRows - 1) / kCoarseRows, 256, 0, s>>>(Minv, n, ld, B, X);
+  return 1;
+}
+
+int coarse_mm64(const double* Minv, int n, int ld, const double* B, double* X, cudaStream_t s) {
+  k_coarse_mm64<<<(n + kCoarseRows - 1) / kCoarseRows, 256, 0, s>>>(Minv, n, ld, B, X);
   return 1;
 }
 

@@ -332,7 +332,8 @@ struct vk_hierarchy {
   // vk_solve_batch workspace (finest level, FP64, 16 interleaved right-hand sides)
   int kb = 0;
   int64_t ldb = 0;
-  float* cinv_f = nullptr;
+  float* cinv_f = nullptr;                    // FP32 coarse inverse (batch_coarse_fp32)
+  double *cb64 = nullptr, *cx64 = nullptr;     // FP64 coarse right-hand sides / solutions (batch)
   double *Vb = nullptr, *Zb = nullptr, *wb = nullptr, *xob = nullptr, *Hb = nullptr, *csb = nullptr, *snb = nullptr;
   double *gb = nullptr, *histb = nullptr, *hcolb = nullptr, *t2b = nullptr, *partb = nullptr, *sqb = nullptr;
   double* yb = nullptr;
@@ -379,6 +380,7 @@ void validate(const vk_problem* p, const vk_options* o) {
   if (o->batch_engine != VK_ENGINE_TCGEN05 && o->batch_engine != VK_ENGINE_MMA_SYNC) raise(VK_ERR_ARG, "bad batch_engine");
   if (o->test_expire_wait != 0 && o->test_expire_wait != 1) raise(VK_ERR_ARG, "test_expire_wait must be 0 or 1");
   if (o->spmv_warps < 1 || o->spmv_warps > 4096) raise(VK_ERR_ARG, "spmv_warps must be in 1..4096");
+  if (o->batch_coarse_fp32 != 0 && o->batch_coarse_fp32 != 1) raise(VK_ERR_ARG, "batch_coarse_fp32 must be 0 or 1");
   if (o->apply_schedule < -1 || o->apply_schedule >= int(apply_candidates().size()))
     raise(VK_ERR_ARG, "apply_schedule must be -1 or a candidate index");
   if (o->batch_prec != VK_BATCH_NONE) {
@@ -526,7 +528,12 @@ void allocate_batch(vk_hierarchy* h) {
     D.db = m.get_n<float>(size_t(H.ndof) * NR);
   }
   const int mdim = h->nc + 1;
-  h->cinv_f = m.get_n<float>(size_t(mdim) * mdim);
+  if (h->opt.batch_coarse_fp32) {
+    h->cinv_f = m.get_n<float>(size_t(mdim) * mdim);
+  } else {
+    h->cb64 = m.get_n<double>(size_t(h->nc) * NR);
+    h->cx64 = m.get_n<double>(size_t(h->nc) * NR);
+  }
   const int nf = h->host[L - 1].ndof;
   h->kb = h->opt.batch_max_iterations;
   const int ldh = h->kb + 1;
@@ -839,7 +846,7 @@ void setup_device(vk_hierarchy* h, cudaStream_t s) {
       h->n_launch += vk::gpu::pack_tc(D.pat, D.tc, static_cast<const double*>(D.pat.factors), D.ascale, half, s);
     }
     const int64_t mm = int64_t(h->nc + 1) * (h->nc + 1);
-    h->n_launch += vk::gpu::to_f32(h->Cinv, h->cinv_f, mm, s);
+    if (h->opt.batch_coarse_fp32) h->n_launch += vk::gpu::to_f32(h->Cinv, h->cinv_f, mm, s);
     CK(cudaMemsetAsync(h->tc_err, 0, 4 * sizeof(int), s));
     CK(cudaGetLastError());
   }
@@ -1205,7 +1212,16 @@ void smooth_b(vk_hierarchy* h, int l, const float* b, float* x, bool zero_init, 
 
 void vcycle_b(vk_hierarchy* h, int l, const float* b, float* x, cudaStream_t s) {
   if (l == 0) {
-    h->n_launch += vk::gpu::coarse_mm(h->cinv_f, h->nc, h->nc + 1, b, x, s);
+    if (h->opt.batch_coarse_fp32) {
+      h->n_launch += vk::gpu::coarse_mm(h->cinv_f, h->nc, h->nc + 1, b, x, s);
+    } else {
+      // the coarsest-level solve stays FP64: widen the FP32 right-hand sides, apply the FP64
+      // bordered inverse, round the solution back for the FP32 V-cycle
+      const int64_t len = int64_t(h->nc) * 16;
+      h->n_launch += vk::gpu::to_f64(b, h->cb64, len, s);
+      h->n_launch += vk::gpu::coarse_mm64(h->Cinv, h->nc, h->nc + 1, h->cb64, h->cx64, s);
+      h->n_launch += vk::gpu::to_f32(h->cx64, x, len, s);
+    }
     return;
   }
   DevLevel& D = h->lv[l];

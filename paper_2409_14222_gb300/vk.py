@@ -64,7 +64,8 @@ class vk_options(ctypes.Structure):
                 ("max_iterations", ctypes.c_int32), ("batch_prec", ctypes.c_int32),
                 ("batch_max_iterations", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("apply_schedule", ctypes.c_int32), ("batch_engine", ctypes.c_int32),
-                ("test_expire_wait", ctypes.c_int32), ("spmv_warps", ctypes.c_int32)]
+                ("test_expire_wait", ctypes.c_int32), ("spmv_warps", ctypes.c_int32),
+                ("batch_coarse_fp32", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
