@@ -26,8 +26,10 @@
 // tile at (c/2) * 4096 + (c%2) * 2048 + 128 m, so the K-adjacent core matrix is 2048 bytes away
 // (leading byte offset) and the next row block 128 bytes (stride byte offset); B likewise with N/8
 // row blocks (the results of the GPU tests confirm this reading of the two offsets).  Every mbarrier
-// wait is bounded (about 2 s of %globaltimer); on expiry the CTA records
-// VK_ERR_TIMEOUT in *err, waits (bounded) for its MMAs in flight, frees its tensor memory and returns.
+// wait is bounded (about 2 s of %globaltimer); on expiry the CTA records VK_ERR_TIMEOUT in *err and
+// raises a shared abort flag that ends the other roles' waits, the producer waits (bounded) for its
+// copies and MMAs still in flight, and the tensor memory is freed before the CTA returns.  (A test
+// exercises this path by announcing one group's copy without issuing it: skip_group.)
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
