@@ -125,3 +125,41 @@ def test_dof_counts_and_coordinates_equal_the_oracle_layout(vk, Nc, L, k):
         # Dirichlet flags are exactly the velocity DoFs on the boundary of the unit square
         on_bnd = (xy[:, 0] == 0) | (xy[:, 1] == 0) | (xy[:, 0] == 1) | (xy[:, 1] == 1)
         assert np.array_equal(h.export_dirichlet(l), on_bnd & (kind < 2))
+
+
+def test_default_options_are_the_documented_ones(vk):
+    o = vk.default_options()
+    assert (o.sweeps, o.weights, o.cheb_lo, o.cheb_hi, o.eig_steps) == (1, vk.VK_WEIGHTS_PLAIN, 0.25, 1.1, 10)
+    assert o.factor_prec == vk.VK_PREC_F64 and o.use_graph == 1 and o.max_iterations == 100
+    assert o.batch_prec == vk.VK_BATCH_NONE and o.batch_max_iterations == 60
+    assert o.autotune == 1 and o.apply_schedule == -1 and o.batch_engine == vk.VK_ENGINE_TCGEN05
+    assert o.test_expire_wait == 0 and o.spmv_warps == 48 and o.batch_coarse_fp32 == 0
+
+
+def test_footprint_follows_the_options(vk):
+    key = (8, 3, 2)
+    f64 = vk.footprint(*key)
+    f32 = vk.footprint(*key, options=vk.default_options(factor_prec=vk.VK_PREC_F32))
+    f64e = vk.footprint(*key, options=vk.default_options(factor_prec=vk.VK_PREC_F64E))
+    assert f32 < f64 < f64e          # 4-byte inverses; FP32 pairs also keep a split residual
+    batch = vk.footprint(*key, options=vk.default_options(batch_prec=vk.VK_BATCH_BF16))
+    assert batch > f64
+    # FP32 coarse copy (n_c + 1)^2 floats instead of two FP64 16-column coarse blocks
+    nc = vk.ndof_of(8, 1, 2)
+    coarse32 = vk.footprint(*key, options=vk.default_options(batch_prec=vk.VK_BATCH_BF16, batch_coarse_fp32=1))
+    assert abs((coarse32 - batch) - (4 * (nc + 1) ** 2 - 2 * 16 * 8 * nc)) < 4096
+
+
+@pytest.mark.parametrize("field,value", [("apply_schedule", 12), ("apply_schedule", -2), ("batch_engine", 2),
+                                         ("spmv_warps", 0), ("test_expire_wait", 2), ("batch_coarse_fp32", 3),
+                                         ("sweeps", 0), ("eig_steps", 65), ("factor_prec", 3)])
+def test_invalid_options_are_refused(vk, field, value):
+    with pytest.raises(vk.VkError) as e:
+        vk.footprint(4, 2, 2, options=vk.default_options(**{field: value}))
+    assert e.value.code == vk.vk.VK_ERR_ARG
+
+
+def test_batch_basis_size_is_bounded(vk):
+    with pytest.raises(vk.VkError):
+        vk.footprint(4, 2, 2, options=vk.default_options(batch_prec=vk.VK_BATCH_BF16, batch_max_iterations=128))
+    assert vk.footprint(4, 2, 2, options=vk.default_options(batch_prec=vk.VK_BATCH_BF16, batch_max_iterations=127)) > 0
