@@ -92,7 +92,11 @@ class ClockSampler:
 
     def __init__(self, index=0):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # scratch file of the samples (only their summary goes into the JSON line); VK_CLOCKS_DIR
+        # keeps it somewhere else than the system temporary directory
+        import tempfile
+        self.path = os.path.join(os.environ.get("VK_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"vk_clocks_bench_{os.getpid()}.csv")
         self.index = index
 
     def __enter__(self):

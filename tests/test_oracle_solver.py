@@ -13,7 +13,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 # ------------------------------------------------------------------ patches (Sec. 3.1)
 
-SURVEY_SIZES = {
+HAND_DERIVED_SIZES = {
     # distinct patch sizes (Dirichlet DoFs excluded) on an 8x8 mesh, by kind; derived by hand from
     # the closure-of-star rule: interior, edge-adjacent, corner patches ...
     2: {"vertex": {3, 9, 11, 15, 27, 29, 33, 39}},
@@ -36,7 +36,7 @@ def test_patch_counts_sizes_and_pressure_partition(k):
         assert len(kinds["edge"]) == 3 * N * N + 2 * N
     if k >= 4:
         assert len(kinds["cell"]) == 2 * N * N
-    for kind, sizes in SURVEY_SIZES[k].items():
+    for kind, sizes in HAND_DERIVED_SIZES[k].items():
         assert set(kinds[kind]) == sizes
         assert max(kinds[kind]) == patches.interior_patch_size(k, kind)
     # every pressure DoF is in exactly one patch; no Dirichlet DoF is in any patch
