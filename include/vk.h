@@ -45,6 +45,7 @@ extern "C" {
 #define VK_ERR_TIMEOUT 6        /* a bounded device-side wait expired                           */
 #define VK_ERR_CUDA 7           /* CUDA runtime error                                           */
 #define VK_ERR_INTERNAL 8
+#define VK_ERR_CANCELLED 9      /* a queued solve request was cancelled, or the service stopped   */
 
 /* ---- options ----------------------------------------------------------------------------------- */
 #define VK_WEIGHTS_PLAIN 0         /* Algorithm 1 with w_i = gamma_i = identity (a plain sum)       */
@@ -67,15 +68,29 @@ extern "C" {
 #define VK_CSR_P 1  /* prolongation from level l-1 to level l (ndof_l x ndof_{l-1})                 */
 #define VK_CSR_R 2  /* restriction R = P^T (ndof_{l-1} x ndof_l)                                     */
 
+#define VK_BC_DIRICHLET_ALL 0  /* velocity Dirichlet condition on the whole boundary (Eq. StokesDirichletNoSlip) */
+
 /* Mesh hierarchy: the unit square cut into N_coarse x N_coarse squares, each split from its top-left
  * to its bottom-right corner (Sec. 4), refined uniformly nlevels-1 times (Sec. 3).  Velocity is
- * continuous P_k, pressure continuous P_{k-1} (Case 1 of Sec. 3), 2 <= k <= 4.  No-slip Dirichlet
- * rows on the whole boundary (Eq. StokesDirichletNoSlip); nu is the viscosity of Eq. (Stokes1). */
+ * continuous P_k, pressure continuous P_{k-1} (Case 1 of Sec. 3), 2 <= k <= 4; nu is the viscosity of
+ * Eq. (Stokes1).
+ *   bc:     VK_BC_DIRICHLET_ALL is the only boundary condition of the method (the paper's problem has
+ *           a velocity Dirichlet condition on all of the boundary, Eqs. StokesDirichletNoSlip and
+ *           model_problem); any other value is refused with VK_ERR_ARG.  The boundary VALUES are data
+ *           of the right-hand side, not of the hierarchy: Dirichlet rows of the matrix are identity rows
+ *           (their columns zeroed), so b's entries at the Dirichlet DoFs (vk_export_dirichlet) are the
+ *           prescribed velocities and the remaining entries must already carry the lifting
+ *           F - A_FB g of nonzero data (the manufactured problem of Sec. 4 is built that way).
+ *   domain: {x0, x1, y0, y1} of the rectangle; the method is stated on the unit square (Sec. 4), so
+ *           only {0, 1, 0, 1} is accepted (all four zero is read as that default); anything else is
+ *           refused with VK_ERR_ARG. */
 typedef struct vk_problem {
   int32_t N_coarse;
   int32_t nlevels;
   int32_t k;
   double nu;
+  int32_t bc;
+  double domain[4];
 } vk_problem;
 
 typedef struct vk_options {
@@ -108,6 +123,11 @@ typedef struct vk_options {
                              1, 2, 4, 8 that gives at least this many warps per SM (default 48)    */
   int32_t batch_coarse_fp32; /* vk_solve_batch: 0 (default) keeps the coarsest-level dense solve in
                              FP64 inside the FP32 V-cycle; 1 applies an FP32 copy of the inverse   */
+  int32_t test_singular_patch; /* test of the singular-patch path: >= 0 zeroes, in the copy of the
+                             finest-level matrix uploaded for the patch gather only, the row of the
+                             last DoF of that (canonical) finest-level patch, so its patch matrix is
+                             singular and vk_setup returns VK_ERR_SINGULAR naming that patch; -1
+                             (default) in normal use                                                */
 } vk_options;
 
 /* Device memory provider.  alloc returns device memory of at least `bytes` (256-byte aligned) or
@@ -145,6 +165,10 @@ void vk_default_options(vk_options* o);
  * `alloc` (NULL = cudaMalloc); work is queued on `stream` and synchronised before return. */
 int vk_setup(const vk_problem* p, const vk_options* o, const vk_allocator* alloc, void* stream,
              vk_hierarchy** out);
+
+/* Checks a problem and options as vk_setup does (ranges, bc, domain, option values) without building
+ * anything.  Returns VK_OK or VK_ERR_ARG with a message. */
+int vk_check_problem(const vk_problem* p, const vk_options* o);
 
 /* Frees the hierarchy and every device buffer it owns.  NULL is ignored. */
 void vk_destroy(vk_hierarchy* h);
@@ -369,6 +393,10 @@ int vk_server_submit(vk_server* s, const vk_request* r, uint64_t* ticket);
  * fills *res.  Returns VK_ERR_TIMEOUT if the result is not ready in time (the request stays queued). */
 int vk_server_wait(vk_server* s, uint64_t ticket, double* x_host, vk_result* res, int timeout_ms);
 int vk_server_get_stats(vk_server* s, vk_server_stats* out);
+/* Cancels a request that is still queued (not yet taken by a slot): its result becomes available to
+ * vk_server_wait at once with status VK_ERR_CANCELLED and no solution.  Returns VK_OK, or VK_ERR_ARG
+ * if the ticket is unknown, already running or already finished (a running solve is not interrupted). */
+int vk_server_cancel(vk_server* s, uint64_t ticket);
 /* Finishes the queued requests, stops the workers and frees every hierarchy. */
 void vk_server_destroy(vk_server* s);
 

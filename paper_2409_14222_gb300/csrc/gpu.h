@@ -89,6 +89,7 @@ int divide(double a, double* x, int n, cudaStream_t s);                  // x /=
 // ---- patch kernels (kernels_patch.cu) -------------------------------------------------------------
 // Gather every patch matrix from the CSR matrix, invert it by Gauss-Jordan with partial pivoting,
 // and store it in the warp-packed layout.  status[0] receives 1 + the first singular patch id.
+// Returns -1 (nothing launched) when the level has a patch larger than 128 DoFs.
 int patch_factor(const Csr& A, const Patches& P, int prec, void* factors, int* status, cudaStream_t s);
 // delta[slot] = (A_i^{-1} r[idx_i]) for every patch (one launch for all patches of a level).  With
 // FP32-pair inverses r is first split into r2 (ndof float2) and delta holds FP32 pairs.

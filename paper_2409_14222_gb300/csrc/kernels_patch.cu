@@ -414,7 +414,7 @@ int patch_factor(const Csr& A, const Patches& P, int prec, void* factors, int* s
   const int nmax = 4 * P.nb_max;
   const size_t smem = size_t(nmax) * nmax * 8 + size_t(nmax) * 12;
   const int smem_cap = 128 * 128 * 8 + 128 * 12;
-  if (nmax > 128) return 0;
+  if (nmax > 128) return -1;   // the caller reports VK_ERR_ARG: nothing is left unfactored silently
   if (prec == 0) {
     cudaFuncSetAttribute(k_patch_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);
     k_patch_factor<double><<<P.npatch, kFactorThreads, smem, s>>>(A, P.slot_ptr, P.slot_dofs, P.foff,

@@ -368,7 +368,14 @@ void validate(const vk_problem* p, const vk_options* o) {
   if (p->N_coarse < 1 || p->nlevels < 1 || p->nlevels > 12) raise(VK_ERR_ARG, "bad mesh hierarchy");
   const int64_t Nf = int64_t(p->N_coarse) << (p->nlevels - 1);
   if (Nf * p->k > 8192) raise(VK_ERR_ARG, "finest mesh too large for 32-bit indices");
-  if (!(p->nu > 0.0)) raise(VK_ERR_ARG, "viscosity must be positive");
+  if (!(p->nu > 0.0) || !std::isfinite(p->nu)) raise(VK_ERR_ARG, "viscosity must be positive and finite");
+  if (p->bc != VK_BC_DIRICHLET_ALL) raise(VK_ERR_ARG, "bc must be VK_BC_DIRICHLET_ALL");
+  {
+    const double* d = p->domain;
+    const bool unset = d[0] == 0.0 && d[1] == 0.0 && d[2] == 0.0 && d[3] == 0.0;
+    const bool unit = d[0] == 0.0 && d[1] == 1.0 && d[2] == 0.0 && d[3] == 1.0;
+    if (!unset && !unit) raise(VK_ERR_ARG, "domain must be the unit square {0, 1, 0, 1}");
+  }
   if (o->sweeps < 1) raise(VK_ERR_ARG, "sweeps must be >= 1");
   if (o->weights != VK_WEIGHTS_PLAIN && o->weights != VK_WEIGHTS_MULTIPLICITY) raise(VK_ERR_ARG, "bad weights");
   if (o->factor_prec != VK_PREC_F64 && o->factor_prec != VK_PREC_F32 && o->factor_prec != VK_PREC_F64E)
@@ -381,6 +388,7 @@ void validate(const vk_problem* p, const vk_options* o) {
   if (o->test_expire_wait != 0 && o->test_expire_wait != 1) raise(VK_ERR_ARG, "test_expire_wait must be 0 or 1");
   if (o->spmv_warps < 1 || o->spmv_warps > 4096) raise(VK_ERR_ARG, "spmv_warps must be in 1..4096");
   if (o->batch_coarse_fp32 != 0 && o->batch_coarse_fp32 != 1) raise(VK_ERR_ARG, "batch_coarse_fp32 must be 0 or 1");
+  if (o->test_singular_patch < -1) raise(VK_ERR_ARG, "test_singular_patch must be -1 or a patch id");
   if (o->apply_schedule < -1 || o->apply_schedule >= int(apply_candidates().size()))
     raise(VK_ERR_ARG, "apply_schedule must be -1 or a candidate index");
   if (o->batch_prec != VK_BATCH_NONE) {
@@ -416,12 +424,20 @@ vk::gpu::Sell upload_sell(DeviceMemory& m, const vk::HostCsr& A, int warps_per_s
   return d;
 }
 
-vk::gpu::Csr upload_csr(DeviceMemory& m, const vk::HostCsr& A) {
+// CSR copy on the device.  zero_row >= 0 uploads that row with zero values (test of the
+// singular-patch path only; the host matrix is unchanged).
+vk::gpu::Csr upload_csr(DeviceMemory& m, const vk::HostCsr& A, int zero_row = -1) {
   vk::gpu::Csr c;
   c.nrows = A.nrows;
   c.ptr = m.upload(A.ptr);
   c.col = m.upload(A.col);
-  c.val = m.upload(A.val);
+  if (zero_row >= 0 && zero_row < A.nrows) {
+    std::vector<double> v(A.val);
+    for (int e = A.ptr[zero_row]; e < A.ptr[zero_row + 1]; ++e) v[e] = 0.0;
+    c.val = m.upload(v);
+  } else {
+    c.val = m.upload(A.val);
+  }
   return c;
 }
 
@@ -572,7 +588,13 @@ void allocate_device(vk_hierarchy* h) {
     D.n_u = H.n_u;
     D.n_p = H.n_p;
     D.A = upload_sell(m, H.A, h->opt.spmv_warps);
-    D.Acsr = upload_csr(m, H.A);
+    int zero_row = -1;
+    if (l == L - 1 && h->opt.test_singular_patch >= 0) {
+      const int np = int(H.patch_ptr.size()) - 1;
+      if (h->opt.test_singular_patch >= np) raise(VK_ERR_ARG, "test_singular_patch out of range");
+      zero_row = H.patch_dofs[H.patch_ptr[h->opt.test_singular_patch + 1] - 1];
+    }
+    D.Acsr = upload_csr(m, H.A, zero_row);
     D.dir = m.upload(H.dir);
     if (l > 0) {
       D.P = upload_sell(m, H.P, h->opt.spmv_warps);
@@ -824,7 +846,9 @@ void setup_device(vk_hierarchy* h, cudaStream_t s) {
   const int L = h->prob.nlevels;
   for (int l = 1; l < L; ++l) {
     DevLevel& D = h->lv[l];
-    h->n_launch += vk::gpu::patch_factor(D.Acsr, D.pat, D.pat.prec, const_cast<void*>(D.pat.factors), h->iflag + l, s);
+    const int nl = vk::gpu::patch_factor(D.Acsr, D.pat, D.pat.prec, const_cast<void*>(D.pat.factors), h->iflag + l, s);
+    if (nl < 0) raise(VK_ERR_ARG, "level " + std::to_string(l) + " has a patch larger than the factor kernel supports");
+    h->n_launch += nl;
     CK(cudaGetLastError());
   }
   // coarsest level: bordered inverse
@@ -1389,6 +1413,14 @@ void vk_default_options(vk_options* o) {
   o->apply_schedule = -1;
   o->batch_engine = VK_ENGINE_TCGEN05;
   o->spmv_warps = 48;
+  o->test_singular_patch = -1;
+}
+
+int vk_check_problem(const vk_problem* p, const vk_options* o) {
+  return guard([&] {
+    validate(p, o);
+    return VK_OK;
+  });
 }
 
 const char* vk_last_error(void) { return g_err.c_str(); }

@@ -2,7 +2,8 @@
 // size and order, served by `slots` worker threads that each own a CUDA stream, so solves that are
 // admitted together run concurrently on the device (continuous batching: a request is admitted as
 // soon as a slot and enough device memory are free).  Hierarchies are kept resident between requests
-// in a pool keyed by (N_coarse, nlevels, k); a pool entry is used by one slot at a time.  Admission is
+// in a pool keyed by the whole problem (N_coarse, nlevels, k and the bits of the viscosity nu, which
+// enters the matrix); a pool entry is used by one slot at a time.  Admission is
 // by device footprint (vk_footprint): when the budget would be exceeded, idle hierarchies are evicted
 // least-recently-used first; a request waits while the memory it needs is held by busy solves.
 //
@@ -11,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -33,7 +35,16 @@ double ms_since(Clock::time_point t0, Clock::time_point t1) {
   return std::chrono::duration<double, std::milli>(t1 - t0).count();
 }
 
-using Key = std::tuple<int, int, int>;  // N_coarse, nlevels, k
+// N_coarse, nlevels, k, bit pattern of nu (two requests share a hierarchy only if their matrices are
+// the same; bc and domain have a single accepted value each, checked at submission)
+using Key = std::tuple<int, int, int, uint64_t>;
+
+Key key_of(const vk_problem& p) {
+  uint64_t bits = 0;
+  static_assert(sizeof(bits) == sizeof(p.nu), "nu is a double");
+  std::memcpy(&bits, &p.nu, sizeof(bits));
+  return Key{p.N_coarse, p.nlevels, p.k, bits};
+}
 
 struct Instance {
   vk_hierarchy* h = nullptr;
@@ -88,7 +99,7 @@ size_t footprint_of(vk_server* s, const vk_problem& p) {
 // allows (evicting idle LRU instances), or returns nullptr if the request must wait.
 Instance* acquire(vk_server* s, std::unique_lock<std::mutex>& lk, const vk_problem& p, int stream_id,
                   cudaStream_t stream, double* setup_ms, int* status) {
-  const Key key{p.N_coarse, p.nlevels, p.k};
+  const Key key = key_of(p);
   auto& list = s->pool[key];
   for (auto& inst : list)
     if (!inst->busy) {
@@ -153,6 +164,8 @@ Instance* acquire(vk_server* s, std::unique_lock<std::mutex>& lk, const vk_probl
       }
     s->used -= need;
     *status = rc;
+    // the released reservation may be what another worker is waiting for
+    s->cv_work.notify_all();
     return nullptr;
   }
   raw->h = h;
@@ -179,7 +192,11 @@ void worker(vk_server* s, int id) {
     if (!stream_ok) status = VK_ERR_CUDA;
     while (status == VK_OK) {
       inst = acquire(s, lk, job.problem, id, stream, &setup_ms, &status);
-      if (inst || status != VK_OK || s->stopping) break;
+      if (inst || status != VK_OK) break;
+      if (s->stopping) {
+        status = VK_ERR_CANCELLED;  // the service stopped while this request waited for memory
+        break;
+      }
       s->cv_work.wait(lk);  // memory held by busy solves: wait for a release
     }
     Done out;
@@ -260,16 +277,19 @@ int vk_server_create(const vk_server_config* cfg, vk_server** out) {
 
 int vk_server_submit(vk_server* s, const vk_request* r, uint64_t* ticket) {
   g_srv_err.clear();
-  if (!s || !r || !r->b || !ticket || r->maxit < 1) {
+  if (!s || !r || !r->b || !ticket || r->maxit < 1 || r->maxit > s->cfg.options.max_iterations ||
+      !(r->rtol >= 0.0)) {
     g_srv_err = "bad request";
     return VK_ERR_ARG;
   }
-  const int k = r->problem.k;
-  const int64_t Nf = int64_t(r->problem.N_coarse) << std::max(0, r->problem.nlevels - 1);
-  if (k < 2 || k > 4 || r->problem.nlevels < 1 || r->problem.N_coarse < 1) {
-    g_srv_err = "bad problem";
+  // the same checks as vk_setup (level count, index range of the finest mesh, viscosity, bc, domain)
+  // before the size of b is computed from the problem
+  if (vk_check_problem(&r->problem, &s->cfg.options) != VK_OK) {
+    g_srv_err = std::string("bad problem: ") + vk_last_error();
     return VK_ERR_ARG;
   }
+  const int k = r->problem.k;
+  const int64_t Nf = int64_t(r->problem.N_coarse) << (r->problem.nlevels - 1);
   const int64_t ndof = 2 * (k * Nf + 1) * (k * Nf + 1) + ((k - 1) * Nf + 1) * ((k - 1) * Nf + 1);
   Job job;
   job.problem = r->problem;
@@ -301,6 +321,26 @@ int vk_server_wait(vk_server* s, uint64_t ticket, double* x_host, vk_result* res
   if (x_host && !d.x.empty()) std::memcpy(x_host, d.x.data(), d.x.size() * sizeof(double));
   if (res) *res = d.res;
   return VK_OK;
+}
+
+int vk_server_cancel(vk_server* s, uint64_t ticket) {
+  g_srv_err.clear();
+  if (!s) return VK_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+    if (it->ticket == ticket) {
+      Done d;
+      d.res.status = VK_ERR_CANCELLED;
+      d.res.queue_ms = d.res.latency_ms = ms_since(it->submitted, Clock::now());
+      s->queue.erase(it);
+      s->st.completed++;
+      s->st.failed++;
+      s->done[ticket] = std::move(d);
+      s->cv_done.notify_all();
+      return VK_OK;
+    }
+  g_srv_err = "ticket is not queued (unknown, running or finished)";
+  return VK_ERR_ARG;
 }
 
 int vk_server_get_stats(vk_server* s, vk_server_stats* out) {

@@ -20,6 +20,8 @@ VK_ERR_NOT_CONVERGED = 5
 VK_ERR_TIMEOUT = 6
 VK_ERR_CUDA = 7
 VK_ERR_INTERNAL = 8
+VK_ERR_CANCELLED = 9
+VK_BC_DIRICHLET_ALL = 0
 
 VK_WEIGHTS_PLAIN = 0
 VK_WEIGHTS_MULTIPLICITY = 1
@@ -32,7 +34,7 @@ VK_ENGINE_TCGEN05, VK_ENGINE_MMA_SYNC = 0, 1
 
 STATUS_NAMES = {0: "VK_OK", 1: "VK_ERR_ARG", 2: "VK_ERR_NO_MEMORY", 3: "VK_ERR_SINGULAR",
                 4: "VK_ERR_NONFINITE", 5: "VK_ERR_NOT_CONVERGED", 6: "VK_ERR_TIMEOUT", 7: "VK_ERR_CUDA",
-                8: "VK_ERR_INTERNAL"}
+                8: "VK_ERR_INTERNAL", 9: "VK_ERR_CANCELLED"}
 
 # exported symbols declared in include/vk.h
 SYMBOLS = [
@@ -41,7 +43,7 @@ SYMBOLS = [
     "vk_coarse_solve", "vk_vcycle", "vk_solve", "vk_solve_host", "vk_csr_dims", "vk_export_csr",
     "vk_export_patches", "vk_export_dirichlet", "vk_hessenberg_eigenvalues", "vk_stats_reset", "vk_stats_read",
     "vk_vanka_noalloc", "vk_solve_batch", "vk_apply_schedule", "vk_ndof", "vk_export_dof_coords", "vk_default_server_config", "vk_server_create", "vk_server_submit", "vk_server_wait",
-    "vk_server_get_stats", "vk_server_destroy",
+    "vk_server_get_stats", "vk_server_destroy", "vk_check_problem", "vk_server_cancel",
 ]
 
 
@@ -53,7 +55,11 @@ class VkError(RuntimeError):
 
 class vk_problem(ctypes.Structure):
     _fields_ = [("N_coarse", ctypes.c_int32), ("nlevels", ctypes.c_int32), ("k", ctypes.c_int32),
-                ("nu", ctypes.c_double)]
+                ("nu", ctypes.c_double), ("bc", ctypes.c_int32), ("domain", ctypes.c_double * 4)]
+
+
+def make_problem(N_coarse, nlevels, k, nu=1.0, bc=VK_BC_DIRICHLET_ALL, domain=(0.0, 1.0, 0.0, 1.0)):
+    return vk_problem(N_coarse, nlevels, k, nu, bc, (ctypes.c_double * 4)(*domain))
 
 
 class vk_options(ctypes.Structure):
@@ -65,7 +71,7 @@ class vk_options(ctypes.Structure):
                 ("batch_max_iterations", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("apply_schedule", ctypes.c_int32), ("batch_engine", ctypes.c_int32),
                 ("test_expire_wait", ctypes.c_int32), ("spmv_warps", ctypes.c_int32),
-                ("batch_coarse_fp32", ctypes.c_int32)]
+                ("batch_coarse_fp32", ctypes.c_int32), ("test_singular_patch", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -158,6 +164,8 @@ def lib():
             "vk_server_wait": (I, [VP, ctypes.c_uint64, VP, P(vk_result), I]),
             "vk_server_get_stats": (I, [VP, P(vk_server_stats)]),
             "vk_server_destroy": (None, [VP]),
+            "vk_server_cancel": (I, [VP, ctypes.c_uint64]),
+            "vk_check_problem": (I, [P(vk_problem), P(vk_options)]),
             "vk_stats_read": (I, [H, P(vk_stats)]),
             "vk_apply_schedule": (I, [H, I, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32),
                                       P(ctypes.c_int32), VP, P(ctypes.c_int32)]),
@@ -234,7 +242,7 @@ class Hierarchy:
 
     def __init__(self, N_coarse, nlevels, k, nu=1.0, options=None, device="cuda", host_only=False,
                  lambdas=None, stream=None, allocator="torch"):
-        self.problem = vk_problem(N_coarse, nlevels, k, nu)
+        self.problem = make_problem(N_coarse, nlevels, k, nu)
         self.options = options if options is not None else default_options()
         if host_only:
             self.options.host_only = 1
@@ -420,7 +428,7 @@ class Hierarchy:
 
 
 def footprint(N_coarse, nlevels, k, nu=1.0, options=None):
-    p = vk_problem(N_coarse, nlevels, k, nu)
+    p = make_problem(N_coarse, nlevels, k, nu)
     o = options if options is not None else default_options()
     b = ctypes.c_size_t()
     check(lib().vk_footprint(ctypes.byref(p), ctypes.byref(o), ctypes.byref(b)))
@@ -463,7 +471,7 @@ class Server:
         import numpy as np
         b = np.ascontiguousarray(b, dtype=np.float64)
         assert b.size == ndof_of(N_coarse, nlevels, k)
-        r = vk_request(vk_problem(N_coarse, nlevels, k, nu), b.ctypes.data, float(rtol), int(maxit))
+        r = vk_request(make_problem(N_coarse, nlevels, k, nu), b.ctypes.data, float(rtol), int(maxit))
         t = ctypes.c_uint64()
         check(lib().vk_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
         self._keep[t.value] = ndof_of(N_coarse, nlevels, k)
@@ -479,6 +487,10 @@ class Server:
                                    ctypes.byref(res), int(timeout_ms)))
         del self._keep[ticket]
         return x, {name: getattr(res, name) for name, _ in vk_result._fields_}
+
+    def cancel(self, ticket):
+        """vk_server_cancel: drop a request that is still queued (its wait then reports VK_ERR_CANCELLED)."""
+        check(lib().vk_server_cancel(self.handle, ctypes.c_uint64(ticket)))
 
     def stats(self):
         st = vk_server_stats()

@@ -163,3 +163,25 @@ def test_batch_basis_size_is_bounded(vk):
     with pytest.raises(vk.VkError):
         vk.footprint(4, 2, 2, options=vk.default_options(batch_prec=vk.VK_BATCH_BF16, batch_max_iterations=128))
     assert vk.footprint(4, 2, 2, options=vk.default_options(batch_prec=vk.VK_BATCH_BF16, batch_max_iterations=127)) > 0
+
+
+def _check(vk, prob, opts=None):
+    import ctypes
+    o = opts if opts is not None else vk.default_options()
+    return vk.lib().vk_check_problem(ctypes.byref(prob), ctypes.byref(o))
+
+
+def test_problem_boundary_data_and_domain_are_checked(vk):
+    # the method's problem: velocity Dirichlet data on the whole boundary of the unit square
+    assert _check(vk, vk.vk.make_problem(4, 2, 2)) == vk.vk.VK_OK
+    assert _check(vk, vk.vk.make_problem(4, 2, 2, domain=(0.0, 0.0, 0.0, 0.0))) == vk.vk.VK_OK
+    bad = [vk.vk.make_problem(4, 2, 2, bc=1), vk.vk.make_problem(4, 2, 2, domain=(0.0, 2.0, 0.0, 2.0)),
+           vk.vk.make_problem(4, 2, 2, domain=(-1.0, 0.0, 0.0, 1.0)), vk.vk.make_problem(4, 2, 2, nu=0.0),
+           vk.vk.make_problem(4, 2, 2, nu=float("inf")), vk.vk.make_problem(4, 13, 2),
+           vk.vk.make_problem(4, 2, 5), vk.vk.make_problem(4096, 2, 2)]
+    for p in bad:
+        assert _check(vk, p) == vk.vk.VK_ERR_ARG
+    with pytest.raises(vk.VkError) as e:
+        vk.footprint(4, 2, 2, options=vk.default_options(test_singular_patch=10 ** 6))
+    assert e.value.code == vk.vk.VK_ERR_ARG
+    assert vk.default_options().test_singular_patch == -1
