@@ -143,8 +143,30 @@ def test_vanka_is_symmetric_and_sums_overlaps():
     # a DoF in no patch is only a Dirichlet DoF, where M acts as the identity
     mask = s.dirichlet_mask()
     assert np.array_equal(M[np.ix_(mask, mask)], np.eye(mask.sum()))
-    # overlap: with multiplicity weights a vector r = A e_i restricted to one patch reproduces e_i there
-    # at DoFs that belong to that single patch only (pressure DoFs belong to exactly one patch)
+
+
+@pytest.mark.parametrize("N,k", [(3, 2), (2, 3), (2, 4)])
+def test_vanka_weights_on_the_identity_operator(N, k):
+    # With A = I every local problem is A_i = I, so Algorithm 1 reduces to sum_i R_i^T W_i R_i r:
+    # multiplicity weights (1 / number of patches of the DoF) are a partition of unity, so M^{-1} r = r
+    # at every DoF; plain weights give count * r.  The counts come from a brute-force scan of the patch
+    # lists; Dirichlet DoFs (in no patch) keep the identity.
+    s = fem.Space(N, k)
+    mask = s.dirichlet_mask()
+    plist = patches.build_patches(s)
+    count = np.zeros(s.ndof)
+    for _, _, dofs in plist:
+        for d in dofs:
+            count[d] += 1
+    assert np.all((count == 0) == mask)
+    I = sp.identity(s.ndof, format="csr")
+    r = np.random.default_rng(41).standard_normal(s.ndof)
+    zm = solver.vanka_apply(solver.Level(s, I, mask, plist, "multiplicity"), r)
+    assert np.allclose(zm, r, rtol=4e-16 * count.max(), atol=0)
+    zp = solver.vanka_apply(solver.Level(s, I, mask, plist, "plain"), r)
+    want = np.where(mask, r, count * r)
+    assert np.allclose(zp, want, rtol=4e-16 * count.max(), atol=0)
+    assert count.max() > 1     # overlaps exist, so the two weightings differ
 
 
 def test_single_patch_vanka_makes_fgmres_converge_in_one_iteration():
@@ -290,6 +312,102 @@ def test_vcycle_coarse_level_is_exact_bordered_solve():
     x = H.vcycle(b)
     assert np.linalg.norm(c.A @ x - b) <= 1e-12 * np.linalg.norm(b)
     assert abs(x[c.space.n_u:].sum()) <= 1e-10 * np.linalg.norm(x)
+
+
+def _dense_vanka(lev):
+    """M^{-1} of Algorithm 1 as a dense matrix: sum_i R_i^T inv(A_i) R_i (+ W_i), identity on Dirichlet
+    rows, built from explicit inverses of the dense blocks (no LU solves, no scatter code)."""
+    A = lev.A.toarray()
+    n = A.shape[0]
+    M = np.zeros((n, n))
+    for _, _, d in lev.patches:
+        M[np.ix_(d, d)] += np.linalg.inv(A[np.ix_(d, d)])
+    M = lev.weight[:, None] * M
+    M[lev.mask, :] = 0.0
+    M[lev.mask, lev.mask] = 1.0
+    return M
+
+
+def _smoother_matrix(lev, Minv, nu):
+    """nu Chebyshev steps on [lam/4, 1.1 lam] from a zero guess as a matrix G (x = G b).  The error
+    after the steps is q(M^{-1} A) e_0 with q(t) = T_nu((theta - t)/delta) / T_nu(theta/delta) (the
+    closed form of the Chebyshev polynomial), so x = s(M^{-1} A) M^{-1} b with s(t) = (1 - q(t)) / t."""
+    from numpy.polynomial import Chebyshev, Polynomial
+    lam = lev.lam
+    lo, hi = 0.25 * lam, 1.1 * lam
+    theta, delta = (hi + lo) / 2, (hi - lo) / 2
+    T = Chebyshev.basis(nu).convert(kind=Polynomial)
+    q = T(Polynomial([theta / delta, -1.0 / delta])) / T(theta / delta)
+    one_minus_q = Polynomial([1.0]) - q
+    assert abs(one_minus_q.coef[0]) < 1e-14
+    s_coef = one_minus_q.coef[1:]
+    X = Minv @ lev.A.toarray()
+    S = np.zeros_like(X)
+    for c in s_coef[::-1]:                      # Horner in the matrix X
+        S = S @ X + c * np.eye(len(X))
+    return S @ Minv
+
+
+def _vcycle_matrix(H, l=None):
+    """The V(nu, nu) cycle of Sec. 3 as a matrix B (x = B b), composed from dense pieces: pre-smoothing
+    G, coarse correction K = P B_c D_c R (D_c zeroes the coarse Dirichlet entries), post-smoothing G;
+    the coarsest level is the top-left block of the inverse of the bordered matrix."""
+    if l is None:
+        l = len(H.levels) - 1
+    lev = H.levels[l]
+    if l == 0:
+        n = lev.A.shape[0]
+        z = lev.space.nullspace()
+        Bd = np.zeros((n + 1, n + 1))
+        Bd[:n, :n] = lev.A.toarray()
+        Bd[:n, n] = z
+        Bd[n, :n] = z
+        return np.linalg.inv(Bd)[:n, :n]
+    A = lev.A.toarray()
+    I = np.eye(A.shape[0])
+    G = _smoother_matrix(lev, _dense_vanka(lev), H.sweeps)
+    Dc = np.diag((~H.levels[l - 1].mask).astype(float))
+    K = lev.P.toarray() @ _vcycle_matrix(H, l - 1) @ Dc @ lev.R.toarray()
+    X1 = G                                      # x1 = G b
+    X2 = X1 + K @ (I - A @ X1)                  # x2 = x1 + K (b - A x1)
+    return X2 + G @ (I - A @ X2)                # x3 = x2 + G (b - A x2)
+
+
+@pytest.mark.parametrize("Nc,L,k,nu", [(2, 2, 2, 1), (2, 2, 2, 2), (2, 2, 3, 1), (2, 2, 3, 2), (2, 3, 2, 1)])
+def test_vcycle_equals_its_dense_composition(Nc, L, k, nu):
+    H = solver.Hierarchy(Nc, L, k, sweeps=nu)
+    fin = H.finest
+    B = _vcycle_matrix(H)
+    rng = np.random.default_rng(43)
+    for _ in range(2):
+        b = rng.standard_normal(fin.space.ndof)
+        want = B @ b
+        dev = np.linalg.norm(H.vcycle(b) - want) / np.linalg.norm(want)
+        assert dev <= 1e-13, dev
+    if L == 2:
+        # two levels: x = (I - E) A^+ b_hat with E = S_post C S_pre the error propagation operator
+        A = fin.A.toarray()
+        E = np.eye(len(A)) - B @ A
+        bh = solver.project(fin.space, rng.standard_normal(fin.space.ndof))
+        xs = np.linalg.lstsq(A, bh, rcond=None)[0]
+        assert np.linalg.norm(H.vcycle(bh) - (xs - E @ xs)) <= 1e-10 * np.linalg.norm(xs)
+
+
+def test_vcycle_pin_detects_planted_mistakes(monkeypatch):
+    # the dense-composition pin must fail for a cycle that skips post-smoothing or the zeroing of the
+    # coarse Dirichlet entries after restriction (mistakes planted in the oracle, on the CPU)
+    H = solver.Hierarchy(2, 2, 2, sweeps=1)
+    B = _vcycle_matrix(H)
+    b = np.random.default_rng(44).standard_normal(H.finest.space.ndof)
+    want = B @ b
+    assert np.linalg.norm(H.vcycle(b) - want) <= 1e-13 * np.linalg.norm(want)
+    orig_smooth = H.smooth
+    monkeypatch.setattr(H, "smooth", lambda l, bb, x: x if x is not None else orig_smooth(l, bb, x))
+    assert np.linalg.norm(H.vcycle(b) - want) > 1e-1 * np.linalg.norm(want)
+    monkeypatch.setattr(H, "smooth", orig_smooth)
+    coarse = H.levels[0]
+    monkeypatch.setattr(coarse, "mask", np.zeros_like(coarse.mask))
+    assert np.linalg.norm(H.vcycle(b) - want) > 1e-2 * np.linalg.norm(want)
 
 
 def test_vcycle_is_a_contraction_config1():
