@@ -1,11 +1,15 @@
-"""Benchmark: FGMRES solves of 2D Stokes (Taylor-Hood P2/P1, 16x16 -> 128x128, 4 levels) on one GB300.
+"""Benchmark: FGMRES solves of 2D Stokes (Taylor-Hood P2/P1, 32x32 -> 512x512, 5 levels, 2,364,419
+DoFs) on one GB300.
 
 One step = one FGMRES solve to 1e-8 relative residual (zero initial guess, V(1,1) cycles with
-Chebyshev-accelerated matrix-full Vanka smoothing) of a seeded N(0,1) right-hand side already resident
-in HBM.  The hierarchy (assembly, patch inverses, coarse inverse, eigenvalue estimates) is built once
-before timing and kept resident, as a solver service would.
+Chebyshev-accelerated matrix-full Vanka smoothing, FP64) of a seeded N(0,1) right-hand side already
+resident in HBM.  The hierarchy (assembly, patch inverses, coarse inverse, eigenvalue estimates) is
+built once before timing and kept resident, as a solver service would.  The default line also nests
+two sub-records measured in the same run: the 16x16 -> 128x128 P2/P1 workload (148,739 DoFs) and the
+16-right-hand-side mixed-precision solve of the 512x512 workload (BF16 patch inverses on the tensor
+cores, FP32 V-cycle, FP64 FGMRES per column) with its error against the FP64 solutions.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vk|reference] [--config cfg2]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vk|reference] [--config cfg4]
 
 N > 1 runs under torch.distributed.run as independent replicas (the path does not shard).
 --impl reference times the CPU oracle (the plain FP64 NumPy restatement of the method) on the host.
@@ -32,26 +36,41 @@ CONFIGS = {
     "cfg3p3": (16, 3, 3, 1, 1e-8, "2D Stokes TH P3/P2, 16x16 -> 64x64 (3 levels), FGMRES to 1e-8"),
     "cfg3p4": (16, 3, 4, 1, 1e-8, "2D Stokes TH P4/P3, 16x16 -> 64x64 (3 levels), FGMRES to 1e-8"),
     "cfg4": (32, 5, 2, 1, 1e-8, "2D Stokes TH P2/P1, 32x32 -> 512x512 (5 levels), FGMRES to 1e-8"),
+    "cfg4batch": (32, 5, 2, 1, 1e-8, "2D Stokes TH P2/P1, 32x32 -> 512x512 (5 levels), FGMRES to 1e-8"),
     "cfg5": (8, 0, 0, 1, 1e-8, "Serving: Poisson stream of solve requests, N in {16..256} (coarsest 8x8), "
                                "k in {2,3,4}, FGMRES to 1e-8"),
 }
+DEFAULT_CONFIG = "cfg4"
 
 HBM_FALLBACK = 6800.0
-FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 (vector and tensor) nominal rate
+# the oracle's stored whole-solve results (tests/golden/make_golden.py, oracle only): the iteration
+# count of a configuration whose oracle solve is too long to repeat here
+GOLDEN = {"cfg4": "oracle_p2_32to512.npz", "cfg3p4": "oracle_p4_16to64.npz"}
 
 
-def recorded_traffic(config, prec):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu record, or None when the
-    record is for another workload or the kernel source changed since the capture."""
+def golden_iterations(config):
+    name = GOLDEN.get(config)
+    if not name:
+        return None
+    p = os.path.join(ROOT, "tests", "golden", name)
+    if not os.path.exists(p):
+        return None
+    with np.load(p) as z:
+        return int(z["iterations"])
+
+
+def recorded_traffic(config, prec, kernel="k_patch_apply"):
+    """DRAM bytes per launch of a kernel from the committed ncu record, or None when the record is for
+    another workload or the kernel source changed since the capture."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            rec = json.load(f)["k_patch_apply"]
+            rec = json.load(f)[kernel]
         with open(os.path.join(ROOT, "paper_2409_14222_gb300", "csrc", rec["source"]), "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()[:16]
     except (OSError, KeyError, ValueError):
         return None
-    if sha != rec["source_sha256_16"] or config != "cfg2" or prec != "f64":
+    if sha != rec["source_sha256_16"] or config != rec.get("config") or prec != rec.get("prec"):
         return None
     return float(rec["dram_bytes_per_launch"])
 
@@ -170,77 +189,205 @@ def max_over_ranks(v, world):
     return float(t.item())
 
 
-def oracle_cpu_baseline(cfg, seed=0):
-    """The oracle timed as it stands on the host cores: one full FGMRES solve of the workload
-    (hierarchy built before timing, like the GPU arm)."""
+
+
+# ---- the oracle on the host cores (cpu_baseline and --impl reference) ---------------------------
+SAMPLE_ITERS = 3
+
+
+def oracle_sample_hierarchy(cfg):
+    """The oracle hierarchy a bounded sample runs on: the workload's own when its oracle setup and
+    iterations take seconds (up to 16x16 -> 128x128 P2), else the 16x16 -> 128x128 P2/P1 hierarchy of
+    the same method (same element, patches, smoother, cycle and Krylov method, 148,739 DoFs) whose
+    per-DoF cost stands in for the larger mesh."""
+    from oracle import solver
+    Nc, L, k, sweeps, rtol, _ = cfg
+    ndof_target = 2 * (k * (Nc << (L - 1)) + 1) ** 2 + ((k - 1) * (Nc << (L - 1)) + 1) ** 2
+    if ndof_target <= 148739:
+        key = (Nc, L, k, sweeps)
+    else:
+        key = (16, 4, k, sweeps)
+    t0 = time.perf_counter()
+    H = solver.Hierarchy(key[0], key[1], key[2], sweeps=key[3])
+    return H, key, ndof_target, time.perf_counter() - t0
+
+
+def oracle_steps(H, rtol, count, seed0):
+    """`count` samples; each is one oracle FGMRES solve stopped after SAMPLE_ITERS iterations (V-cycles,
+    products, orthogonalisation, Givens, the final combination and true residual).  Seconds each."""
     from oracle import solver
     import synthetic_inputs as si
-    Nc, L, k, sweeps, rtol, _ = cfg
-    t0 = time.perf_counter()
-    H = solver.Hierarchy(Nc, L, k, sweeps=sweeps)
-    t_setup = time.perf_counter() - t0
-    b = si.rhs_normal(H.finest.space.ndof, seed)
-    t0 = time.perf_counter()
-    res = solver.solve(H, b, rtol, 100)
-    t = time.perf_counter() - t0
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": 1.0 / t, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": f"1 full FGMRES solve (seed {seed}, {res.iters} iterations, {t:.1f} s; hierarchy setup "
-                      f"{t_setup:.1f} s excluded); NumPy/SciPy FP64, BLAS threads "
-                      f"{os.environ.get('OPENBLAS_NUM_THREADS', 'default')}",
-            "iterations": res.iters, "seconds": t}
+    ndof = H.finest.space.ndof
+    out = []
+    for s in range(count):
+        b = si.rhs_normal(ndof, seed0 + s)
+        t0 = time.perf_counter()
+        solver.solve(H, b, rtol, SAMPLE_ITERS)
+        out.append(time.perf_counter() - t0)
+    return out
 
 
-def run_reference(args, cfg):
-    """--impl reference: the oracle on the host cores, same metric and config."""
+def oracle_target_iterations(config, cfg, H, key):
+    """FGMRES iterations of one solve of the target workload by the oracle: the stored oracle result
+    when the workload is too large to solve here, else one untimed full oracle solve."""
+    from oracle import solver
+    import synthetic_inputs as si
+    it = golden_iterations(config)
+    if it is not None:
+        return it, "stored oracle result (tests/golden)"
+    if key[:3] == cfg[:3]:
+        res = solver.solve(H, si.rhs_normal(H.finest.space.ndof, 0), cfg[4], 100)
+        return res.iters, "one untimed full oracle solve (seed 0)"
+    return None, "unknown"
+
+
+def cpu_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def oracle_cpu_baseline(config, cfg, budget_s=15.0):
+    """The oracle timed as it stands on the host cores, on a bounded sample (about budget_s of CPU
+    work), scaled to solves/s of the workload."""
+    H, key, ndof_target, setup_s = oracle_sample_hierarchy(cfg)
+    iters, src = oracle_target_iterations(config, cfg, H, key)
+    times = oracle_steps(H, cfg[4], 1, 500)
+    n = max(1, int(budget_s / max(times[0], 1e-3)))
+    times = oracle_steps(H, cfg[4], n, 600)
+    mean = float(np.mean(times))
+    ndof_s = H.finest.space.ndof
+    scale = (ndof_target / ndof_s) * ((iters or SAMPLE_ITERS) / SAMPLE_ITERS)
+    return {"value": 1.0 / (mean * scale), "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": (f"{n} oracle FGMRES solves of seeded N(0,1) right-hand sides on the {key[0]}x{key[0]} -> "
+                       f"{key[0] << (key[1] - 1)}x{key[0] << (key[1] - 1)} P{key[2]} hierarchy ({ndof_s} DoFs), "
+                       f"each stopped after {SAMPLE_ITERS} iterations, {mean:.2f} s each; scaled to one solve of "
+                       f"the workload by DoFs ({ndof_target}/{ndof_s}) and iterations ({iters}/{SAMPLE_ITERS}, "
+                       f"{src}); oracle setup {setup_s:.1f} s excluded; NumPy/SciPy FP64, BLAS threads "
+                       f"{os.environ.get('OPENBLAS_NUM_THREADS', 'default')}"),
+            "sample_seconds": mean, "scale_to_one_solve": scale}
+
+
+def run_reference(args, config, cfg):
+    """--impl reference: the oracle on the host cores, same metric, unit and config as the GPU arm.
+    Each step is a bounded sample (one oracle solve stopped after SAMPLE_ITERS iterations); ms_per_step
+    is that measured sample time, and `value` scales it to solves/s of the workload (the scale factor
+    is printed under "extrapolation")."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return
-    from oracle import solver
-    import synthetic_inputs as si
-    Nc, L, k, sweeps, rtol, desc = cfg
-    H = solver.Hierarchy(Nc, L, k, sweeps=sweeps)
-    ndof = H.finest.space.ndof
-    # one full solve (untimed warm-up) fixes the iteration count of the workload; each timed step is
-    # a bounded sample: the first `sample_iters` FGMRES iterations of a solve, scaled to a full solve
-    full = solver.solve(H, si.rhs_normal(ndof, 0), rtol, 100)
-    sample_iters = min(3, full.iters)
-    for w in range(max(0, args.warmup - 1)):
-        solver.solve(H, si.rhs_normal(ndof, 100 + w), rtol, sample_iters)
-    times = []
-    for s in range(args.steps):
-        b = si.rhs_normal(ndof, 1000 + s)
-        t0 = time.perf_counter()
-        solver.solve(H, b, rtol, sample_iters)
-        times.append((time.perf_counter() - t0) * full.iters / sample_iters)
+    H, key, ndof_target, setup_s = oracle_sample_hierarchy(cfg)
+    iters, src = oracle_target_iterations(config, cfg, H, key)
+    iters = iters or SAMPLE_ITERS
+    oracle_steps(H, cfg[4], args.warmup, 100)
+    times = oracle_steps(H, cfg[4], args.steps, 1000)
     total = sum(times)
-    value = args.steps / total
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    sample = (f"each step: first {sample_iters} FGMRES iterations of a solve, scaled by "
-              f"{full.iters}/{sample_iters} (full solve iteration count); hierarchy built before timing")
+    ndof_s = H.finest.space.ndof
+    scale = (ndof_target / ndof_s) * (iters / SAMPLE_ITERS)
+    value = args.steps / (total * scale)
+    sample = (f"each step: one oracle FGMRES solve of a seeded N(0,1) right-hand side on the {key[0]}x{key[0]} -> "
+              f"{key[0] << (key[1] - 1)}x{key[0] << (key[1] - 1)} P{key[2]} hierarchy ({ndof_s} DoFs) stopped "
+              f"after {SAMPLE_ITERS} iterations; value = steps / (timed seconds x {scale:.3g}), the scale to one "
+              f"solve of the workload by DoFs ({ndof_target}/{ndof_s}) and iterations ({iters}/{SAMPLE_ITERS}, "
+              f"{src}); oracle setup {setup_s:.1f} s before timing")
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "impl": "reference",
-        "config": {"workload": desc, "ndof": ndof, "iterations": full.iters},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": cfg[5], "ndof": ndof_target, "iterations": iters},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "vcycle_dof_per_s": ndof * full.iters * args.steps / total,
-        "latency_ms": {"p50": 1e3 * float(np.percentile(times, 50)), "p99": 1e3 * float(np.percentile(times, 99))},
+        "extrapolation": {"timed_seconds": total, "sample_ndof": ndof_s, "target_ndof": ndof_target,
+                          "sample_iterations": SAMPLE_ITERS, "target_iterations": iters, "scale": scale,
+                          "ms_per_step_is": "the measured sample", "value_is": "solves/s of the workload"},
+        "vcycle_dof_per_s": ndof_s * SAMPLE_ITERS * args.steps / total,
+        "latency_ms": {"p50": 1e3 * float(np.percentile(times, 50)) * scale,
+                       "p99": 1e3 * float(np.percentile(times, 99)) * scale},
     }
     print(json.dumps(out), flush=True)
 
 
-def run_vk(args, cfg):
-    import torch
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    from __graft_entry__ import build
-    build()
-    import paper_2409_14222_gb300 as vk
-    import synthetic_inputs as si
-    Nc, L, k, sweeps, rtol, desc = cfg
+# ---- GPU arm ---------------------------------------------------------------------------------------
+def timed_solves(torch, G, B, x, rtol, steps, warmup, flush, world, clk=None):
+    """W untimed solves, then K solves each bracketed by CUDA events on the launching stream, with the
+    L2 overwritten (256 MiB > 129 MB) before each (outside the events).  Max over ranks."""
+    stream = torch.cuda.current_stream()
+    for w in range(warmup):
+        G.solve(B[w], x, rtol=rtol, history=False)
+    torch.cuda.synchronize()
+    G.stats_reset(time_kernels=False)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    iters = []
+    barrier(world)
+    torch.cuda.synchronize()
+    if clk is not None:
+        clk.__enter__()
+    try:
+        torch.cuda.profiler.start()          # a profiler started with --profile-from-start off sees only this
+        for s in range(steps):
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+            out = G.solve(B[warmup + s], x, rtol=rtol, history=False)
+            ev[s][1].record(stream)
+            iters.append(out["iterations"])
+            if not out["converged"]:
+                raise RuntimeError(f"solve {s} did not converge: {out}")
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    finally:
+        if clk is not None:
+            clk.__exit__(None, None, None)
+    barrier(world)
+    st = G.stats()
+    times_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = max_over_ranks(sum(times_ms) / 1e3, world)
+    return {"total_s": total_s, "times_ms": times_ms, "iters": iters, "vcycles": st["vcycles"],
+            "launches": int(st["launches"])}
+
+
+def kernel_times(torch, G, B, x, rtol, count, warmup, flush):
+    """CUDA events around every finest-level patch-apply and V-cycle residual launch of `count` solves
+    (host-driven FGMRES loop: events cannot bracket the iterations of the graph's device-side loop; the
+    kernels and their launch configurations are the same)."""
+    G.stats_reset(time_kernels=True)
+    for s in range(count):
+        flush.fill_(float(s))
+        G.solve(B[warmup + s], x, rtol=rtol, history=False)
+    torch.cuda.synchronize()
+    kt = G.stats()
+    G.stats_reset(time_kernels=False)
+    return kt
+
+
+def apply_roofline(kt, prec, hbm, peak_kind, fp64_tflops, config):
+    """Roofline of the dominant kernel, the finest-level patch application: FP64 inverses are bound by
+    the FP64 pipe (2 flops per 8-byte entry needs 1.7 TFLOP/s at full HBM bandwidth, above the part's
+    FP64 rate), so they are measured against the FMA rate probed in this run; FP32 and FP32-pair
+    inverses against the measured HBM bandwidth."""
+    n = max(int(kt["apply_launches"]), 1)
+    avg_s = kt["apply_ms"] / n / 1e3
+    gbs = kt["apply_bytes"] / avg_s / 1e9
+    tflops = kt["apply_flops"] / avg_s / 1e12
+    hbm_view = {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+    if prec == "f64":
+        roof = {"bound": "alu", "achieved": tflops, "peak": fp64_tflops, "unit": "TFLOP/s",
+                "frac": tflops / fp64_tflops, "kernel": "k_patch_apply (finest level, FP64 inverses)",
+                "peak_source": "FP64 FMA rate measured in this run (vk_measure_fma_rate, of measured)",
+                "hbm_view": hbm_view}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "kernel": f"k_patch_apply (finest level, {prec.upper()} inverses)",
+                "peak_source": hbm_view["peak_source"] + ", of measured" if peak_kind == "measured" else
+                "fallback 6.8 TB/s, of fallback", "tflops": tflops}
+    roof["traffic"] = recorded_traffic(config, prec)
+    roof["launch_avg_us"] = avg_s * 1e6
+    roof["bytes_per_launch"] = kt["apply_bytes"]
+    roof["flops_per_launch"] = kt["apply_flops"]
+    roof["launches_timed"] = int(kt["apply_launches"])
+    return roof
+
+
+def make_options(vk, args, sweeps):
     opts = vk.default_options(sweeps=sweeps)
     if args.prec == "f32":
         opts.factor_prec = vk.VK_PREC_F32
@@ -250,116 +397,200 @@ def run_vk(args, cfg):
         opts.use_graph = 0
     if args.spmv_warps:
         opts.spmv_warps = args.spmv_warps
-    stream = torch.cuda.current_stream()
+    return opts
+
+
+def single_rhs_record(vk, torch, si, cfg, args, opts, steps, warmup, flush, world, rank, peaks, clk=None,
+                      e2e=True):
+    """One single-right-hand-side workload: setup, timed solves, kernel times, end-to-end solves."""
+    Nc, L, k, sweeps, rtol, desc = cfg
+    t0 = time.perf_counter()
     G = vk.Hierarchy(Nc, L, k, options=opts)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
     ndof = G.ndof()
-    # inputs resident in HBM before timing: one RHS per step
-    seeds = [rank * 100000 + s for s in range(args.warmup + args.steps)]
+    seeds = [rank * 100000 + s for s in range(warmup + steps)]
     B = [torch.from_numpy(si.rhs_normal(ndof, s)).cuda() for s in seeds]
     x = torch.zeros(ndof, dtype=torch.float64, device="cuda")
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for w in range(args.warmup):
-        G.solve(B[w], x, rtol=rtol, history=False)
-    torch.cuda.synchronize()
-    G.stats_reset(time_kernels=False)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    iters = []
-    barrier(world)
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        torch.cuda.profiler.start()          # a profiler started with --profile-from-start off sees only this
-        for s in range(args.steps):
-            flush.fill_(float(s))            # overwrite L2 (256 MiB > 129 MB) between timed solves
-            ev[s][0].record(stream)
-            out = G.solve(B[args.warmup + s], x, rtol=rtol, history=False)
-            ev[s][1].record(stream)
-            iters.append(out["iterations"])
-            if not out["converged"]:
-                raise RuntimeError(f"solve {s} did not converge: {out}")
+    t = timed_solves(torch, G, B, x, rtol, steps, warmup, flush, world, clk)
+    kt = kernel_times(torch, G, B, x, rtol, min(steps, 10), warmup, flush)
+    rec = {"G": G, "ndof": ndof, "setup_s": setup_s, "timed": t, "kt": kt,
+           "value": world * steps / t["total_s"],
+           "vcycle_dof_per_s": world * ndof * t["vcycles"] / t["total_s"]}
+    if e2e:
+        # end to end through the C ABI with host buffers (pinned): H2D copy + solve + D2H copy per step
+        bh = [torch.from_numpy(si.rhs_normal(ndof, 7777 + s)).pin_memory() for s in range(steps)]
+        xh = torch.zeros(ndof, dtype=torch.float64).pin_memory()
+        G.solve_host(bh[0].numpy(), xh.numpy(), rtol=rtol)
         torch.cuda.synchronize()
-        torch.cuda.profiler.stop()
-    barrier(world)
-    st = G.stats()
-    times_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = max_over_ranks(sum(times_ms) / 1e3, world)
-    value = world * args.steps / total_s
-    vcycles = st["vcycles"]
-    # dominant kernel: every finest-level patch-apply launch of the same K solves, bracketed by CUDA
-    # events on its stream (the solves run through the host-driven FGMRES loop here, because events
-    # cannot bracket each iteration of the graph's device-side loop; the kernels and launch
-    # configurations are the same)
-    G.stats_reset(time_kernels=True)
-    for s in range(args.steps):
-        flush.fill_(float(s))
-        G.solve(B[args.warmup + s], x, rtol=rtol, history=False)
-    torch.cuda.synchronize()
-    kt = G.stats()
-    G.stats_reset(time_kernels=False)       # back to the graph path for the end-to-end pass
-    # end to end through the C ABI with host buffers (pinned): H2D copy + solve + D2H copy per step
-    bh = [torch.from_numpy(si.rhs_normal(ndof, 7777 + s)).pin_memory() for s in range(args.steps)]
-    xh = torch.zeros(ndof, dtype=torch.float64).pin_memory()
-    G.solve_host(bh[0].numpy(), xh.numpy(), rtol=rtol)
-    torch.cuda.synchronize()
-    barrier(world)
+        barrier(world)
+        t1 = time.perf_counter()
+        for s in range(steps):
+            G.solve_host(bh[s].numpy(), xh.numpy(), rtol=rtol)
+        rec["e2e_s"] = max_over_ranks(time.perf_counter() - t1, world)
+    return rec
+
+
+def summary_of(rec, cfg, args, hbm, peak_kind, fp64_tflops, config):
+    t, kt = rec["timed"], rec["kt"]
+    Nc, L, k, sweeps, rtol, desc = cfg
+    return {
+        "workload": desc, "ndof": rec["ndof"], "value": rec["value"], "unit": "solves/s",
+        "ms_per_step": 1e3 * t["total_s"] / len(t["iters"]), "steps": len(t["iters"]),
+        "vcycle_dof_per_s": rec["vcycle_dof_per_s"],
+        "iterations": {"mean": float(np.mean(t["iters"])), "min": int(min(t["iters"])), "max": int(max(t["iters"]))},
+        "latency_ms": {"p50": float(np.percentile(t["times_ms"], 50)), "p99": float(np.percentile(t["times_ms"], 99))},
+        "setup_s": rec["setup_s"], "gpu_launches": t["launches"],
+        "roofline": apply_roofline(kt, args.prec, hbm, peak_kind, fp64_tflops, config),
+        "spmv": spmv_roofline(kt, "spmv_bytes", hbm, peak_kind, "k_sell residual r = b - A x (finest level, FP64)"),
+        "apply_schedule": schedules(rec["G"], L),
+    }
+
+
+def batch_record(vk, torch, si, cfg, args, flush, hbm, peaks, peak_kind, G64=None, fp64_value=None,
+                 engine=None, coarse_fp32=0, steps=None):
+    """16 right-hand sides per step through vk_solve_batch: FP32 V-cycle with BF16 (or FP16) scaled
+    patch inverses on the tensor cores, FP64 coarsest solve, FP64 FGMRES per column.  With G64 (the
+    FP64 single-right-hand-side hierarchy of the same workload) the first four columns are compared
+    with FP64 solves of the same right-hand sides."""
+    Nc, L, k, sweeps, rtol, desc = cfg
+    bp = vk.VK_BATCH_FP16 if args.batch_prec == "fp16" else vk.VK_BATCH_BF16
+    engine = engine or args.engine
+    eng = {"tcgen05": vk.VK_ENGINE_TCGEN05, "mma_sync": vk.VK_ENGINE_MMA_SYNC}[engine]
     t0 = time.perf_counter()
-    for s in range(args.steps):
-        G.solve_host(bh[s].numpy(), xh.numpy(), rtol=rtol)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    if rank != 0:
-        return
+    Gb = vk.Hierarchy(Nc, L, k, options=vk.default_options(sweeps=sweeps, batch_prec=bp, batch_engine=eng,
+                                                              batch_max_iterations=args.batch_maxit,
+                                                              batch_coarse_fp32=coarse_fp32))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    n = Gb.ndof()
+    stream = torch.cuda.current_stream()
+    Bs = [torch.from_numpy(si.rhs_batch(n, range(16 * i, 16 * i + 16)).T.copy()).cuda() for i in range(2)]
+    X = torch.zeros(16, n, dtype=torch.float64, device="cuda")
+    nsteps = steps or min(args.steps, 5)
+    for w in range(3):
+        Gb.solve_batch(Bs[w % 2], X, rtol=rtol, maxit=args.batch_maxit)
+    torch.cuda.synchronize()
+    Gb.stats_reset(time_kernels=False)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+    iters = []
+    for st in range(nsteps):
+        flush.fill_(float(st))
+        ev[st][0].record(stream)
+        out = Gb.solve_batch(Bs[st % 2], X, rtol=rtol, maxit=args.batch_maxit)
+        ev[st][1].record(stream)
+        iters += [o["iterations"] for o in out]
+        if not all(o["converged"] for o in out):
+            raise RuntimeError("a column did not converge")
+    torch.cuda.synchronize()
+    stt = Gb.stats()
+    times_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(times_ms) / 1e3
+    value = 16 * nsteps / total_s
+    # tensor-core patch apply and block residual, finest level: CUDA events around every launch
+    Gb.stats_reset(time_kernels=True)
+    out = Gb.solve_batch(Bs[0], X, rtol=rtol, maxit=args.batch_maxit)
+    torch.cuda.synchronize()
+    kt = Gb.stats()
+    Gb.stats_reset(time_kernels=False)
+    avg_s = kt["apply_ms"] / max(kt["apply_launches"], 1) / 1e3
+    gbs = kt["batch_apply_bytes"] / avg_s / 1e9
+    tflops = kt["batch_apply_flops"] / avg_s / 1e12
+    rec = {
+        "workload": desc + ", 16 right-hand sides per step", "engine": engine, "batch_prec": args.batch_prec,
+        "coarse_solve": "fp32" if coarse_fp32 else "fp64",
+        "value": value, "unit": "solves/s", "steps": nsteps, "ms_per_step": 1e3 * total_s / nsteps,
+        "setup_s": setup_s, "vcycle_dof_per_s": 16 * n * stt["vcycles"] / total_s,
+        "iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)), "max": int(max(iters))},
+        "latency_ms": {"p50": float(np.percentile(times_ms, 50)), "p99": float(np.percentile(times_ms, 99))},
+        "gpu_launches": int(stt["launches"]),
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                     "kernel": (f"{'k_patch_tc (tcgen05' if engine == 'tcgen05' else 'k_patch_mma (mma.sync'}; "
+                                f"{args.batch_prec.upper()} inverses x 16 right-hand sides, finest level)"),
+                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})", "launch_avg_us": avg_s * 1e6,
+                     "bytes_per_launch": kt["batch_apply_bytes"], "tensor_tflops": tflops,
+                     "tensor_frac_of_bf16_peak": tflops / float(peaks.get("bf16_tflops", 1907.0))},
+        "spmv": spmv_roofline(kt, "batch_spmv_bytes", hbm, peak_kind,
+                              "k_mm block residual R = B - A X (finest level, FP32, 16 right-hand sides)"),
+    }
+    if G64 is not None:
+        errs = []
+        x1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        for r in range(4):
+            G64.solve(Bs[0][r].contiguous(), x1, rtol=rtol, history=False)
+            errs.append(float(torch.linalg.vector_norm(X[r] - x1) / torch.linalg.vector_norm(x1)))
+        rec["rel_error_vs_fp64_solution"] = {"max": max(errs), "mean": float(np.mean(errs)), "columns": 4}
+    if fp64_value:
+        rec["speedup_vs_plain_fp64_one_at_a_time"] = value / fp64_value
+    del Gb, X
+    torch.cuda.empty_cache()
+    return rec
+
+
+def run_vk(args, config, cfg):
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    from __graft_entry__ import build
+    build()
+    import paper_2409_14222_gb300 as vk
+    import synthetic_inputs as si
+    Nc, L, k, sweeps, rtol, desc = cfg
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK))
-    apply_avg_s = kt["apply_ms"] / max(kt["apply_launches"], 1) / 1e3
-    gbs = kt["apply_bytes"] / apply_avg_s / 1e9
-    gflops = kt["apply_flops"] / apply_avg_s / 1e9
-    frac_hbm, frac_alu = gbs / hbm, gflops / FP64_NOMINAL_GFLOPS
-    if args.prec == "f64" and frac_alu > frac_hbm:
-        roof = {"bound": "alu", "achieved": gflops / 1e3, "peak": FP64_NOMINAL_GFLOPS / 1e3, "unit": "TFLOP/s",
-                "frac": frac_alu, "traffic": None, "kernel": "k_patch_apply (finest level, FP64 inverses)",
-                "peak_source": "GB300 nominal FP64 rate 1.25 TFLOP/s (fp64 FMA pipe)",
-                "hbm_view": {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": frac_hbm, "peak_source": peak_kind}}
-    else:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": frac_hbm, "traffic": None,
-                "kernel": f"k_patch_apply (finest level, {args.prec.upper()} inverses)",
-                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
-    roof["traffic"] = recorded_traffic(args.config, args.prec)
-    roof["launch_avg_us"] = apply_avg_s * 1e6
-    roof["bytes_per_launch"] = kt["apply_bytes"]
-    roof["launches_timed"] = int(kt["apply_launches"])
-    roof["spmv"] = spmv_roofline(kt, "spmv_bytes", hbm, peak_kind, "k_sell residual r = b - A x (finest level, FP64)")
-    cpu = None
-    if not args.no_cpu_baseline:
-        cpu = oracle_cpu_baseline(cfg)
-    clocks = clk.summary()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    fp64_tflops = vk.measure_fma_rate(True)
+    fp32_tflops = vk.measure_fma_rate(False)
+    opts = make_options(vk, args, sweeps)
+    clk = ClockSampler(local)
+    main = single_rhs_record(vk, torch, si, cfg, args, opts, args.steps, args.warmup, flush, world, rank, peaks, clk)
+    s = summary_of(main, cfg, args, hbm, peak_kind, fp64_tflops, config)
+    nested = {}
+    if config == "cfg4" and world == 1 and not args.no_nested:
+        c2 = CONFIGS["cfg2"]
+        r2 = single_rhs_record(vk, torch, si, c2, args, make_options(vk, args, c2[3]), args.steps, args.warmup,
+                               flush, world, rank, peaks, e2e=False)
+        nested["cfg2"] = summary_of(r2, c2, args, hbm, peak_kind, fp64_tflops, "cfg2")
+        del r2
+        torch.cuda.empty_cache()
+        nested["batch16"] = batch_record(vk, torch, si, cfg, args, flush, hbm, peaks, peak_kind, G64=main["G"],
+                                         fp64_value=main["value"])
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu_baseline else oracle_cpu_baseline(config, cfg)
+    roof = dict(s["roofline"])
+    roof["spmv"] = s["spmv"]
     out = {
-        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": main["value"], "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": s["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"f64": "f64", "f64e": "f64 vectors; patch inverses as FP32 pairs (48-bit), FP32-pair products",
                   "f32": "f64 vectors, f32 patch inverses"}[args.prec],
         "data": "synthetic",
-        "config": {"workload": desc, "ndof": ndof, "levels": L, "k": k, "sweeps": sweeps, "rtol": rtol,
+        "config": {"workload": desc, "ndof": main["ndof"], "levels": L, "k": k, "sweeps": sweeps, "rtol": rtol,
                    "factor_prec": args.prec, "fgmres_loop": "host" if args.no_graph else "CUDA graph (WHILE node)",
                    "rhs": "N(0,1), numpy default_rng(seed)",
                    "l2": "256 MiB buffer overwritten between timed solves (outside the per-solve events)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "apply_schedule": schedules(G, L)},
-        "vcycle_dof_per_s": world * ndof * vcycles / total_s,
-        "iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)), "max": int(max(iters))},
-        "latency_ms": {"p50": float(np.percentile(times_ms, 50)), "p99": float(np.percentile(times_ms, 99))},
-        "e2e": {"value": world * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * ndof,
-                "d2h_bytes_per_step": 8 * ndof},
-        "gpu_launches": int(st["launches"]),
+                   "apply_schedule": s["apply_schedule"]},
+        "vcycle_dof_per_s": main["vcycle_dof_per_s"], "iterations": s["iterations"], "latency_ms": s["latency_ms"],
+        "setup_s": main["setup_s"],
+        "e2e": {"value": world * args.steps / main["e2e_s"], "unit": "solves/s", "h2d_bytes_per_step": 8 * main["ndof"],
+                "d2h_bytes_per_step": 8 * main["ndof"]},
+        "gpu_launches": s["gpu_launches"],
         "roofline": roof,
+        "fma_rate_measured_here": {"fp64_tflops": fp64_tflops, "fp32_tflops": fp32_tflops,
+                                   "how": "vk_measure_fma_rate: independent FMA chains on every SM, best of 5"},
+        "nested": nested,
         "cpu_baseline": cpu,
-        "clocks": clocks,
+        "clocks": clk.summary(),
     }
     print(json.dumps(out), flush=True)
 
 
-def run_batch(args, cfg):
-    """cfg4: 16 right-hand sides per step through vk_solve_batch (FP32 V-cycle, BF16/FP16 patch
-    inverses on the tensor cores, FP64 FGMRES per column), against plain FP64 single solves."""
+def run_batch(args, config, cfg):
+    """--config cfg4batch: the 16-right-hand-side solve as its own line, with the other tensor-core
+    engine, the FP32 coarsest-solve variant and plain FP64 one-at-a-time solves for comparison."""
     import torch
     from __graft_entry__ import build
     build()
@@ -367,157 +598,52 @@ def run_batch(args, cfg):
     import synthetic_inputs as si
     torch.cuda.set_device(0)
     Nc, L, k, sweeps, rtol, desc = cfg
-    bp = vk.VK_BATCH_FP16 if args.batch_prec == "fp16" else vk.VK_BATCH_BF16
-    t0 = time.perf_counter()
-    engines = {"tcgen05": vk.VK_ENGINE_TCGEN05, "mma_sync": vk.VK_ENGINE_MMA_SYNC}
-    other = "mma_sync" if args.engine == "tcgen05" else "tcgen05"
-    G = vk.Hierarchy(Nc, L, k, options=vk.default_options(sweeps=sweeps, batch_prec=bp,
-                                                             batch_engine=engines[args.engine],
-                                                             batch_max_iterations=args.batch_maxit))
-    setup_s = time.perf_counter() - t0
-    n = G.ndof()
-    stream = torch.cuda.current_stream()
-    nb = args.warmup + args.steps
-    Bs = [torch.from_numpy(si.rhs_batch(n, range(16 * i, 16 * i + 16)).T.copy()).cuda() for i in range(min(nb, 4))]
-    X = torch.zeros(16, n, dtype=torch.float64, device="cuda")
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for w in range(args.warmup):
-        G.solve_batch(Bs[w % len(Bs)], X, rtol=rtol, maxit=args.batch_maxit)
-    torch.cuda.synchronize()
-    G.stats_reset(time_kernels=False)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    iters = []
-    with ClockSampler(0) as clk:
-        torch.cuda.profiler.start()
-        for st in range(args.steps):
-            flush.fill_(float(st))
-            ev[st][0].record(stream)
-            out = G.solve_batch(Bs[st % len(Bs)], X, rtol=rtol, maxit=args.batch_maxit)
-            ev[st][1].record(stream)
-            iters += [o["iterations"] for o in out]
-            if not all(o["converged"] for o in out):
-                raise RuntimeError("a column did not converge")
-        torch.cuda.synchronize()
-        torch.cuda.profiler.stop()
-    stt = G.stats()
-    times_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(times_ms) / 1e3
-    value = 16 * args.steps / total_s
-    # tensor-core patch apply, finest level: CUDA events around every launch of the same solves
-    G.stats_reset(time_kernels=True)
-    for st in range(min(args.steps, 3)):
-        G.solve_batch(Bs[st % len(Bs)], X, rtol=rtol, maxit=args.batch_maxit)
-    torch.cuda.synchronize()
-    kt = G.stats()
-    G.stats_reset(time_kernels=False)
-    avg_s = kt["apply_ms"] / max(kt["apply_launches"], 1) / 1e3
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK))
-    gbs = kt["batch_apply_bytes"] / avg_s / 1e9
-    tflops = kt["batch_apply_flops"] / avg_s / 1e12
-    roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
-            "kernel": (f"{'k_patch_tc (tcgen05' if args.engine == 'tcgen05' else 'k_patch_mma (mma.sync'}; "
-                       f"{args.batch_prec.upper()} inverses x 16 right-hand sides, finest level)"),
-            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})", "launch_avg_us": avg_s * 1e6,
-            "bytes_per_launch": kt["batch_apply_bytes"], "tensor_tflops": tflops,
-            "tensor_frac_of_bf16_peak": tflops / float(peaks.get("bf16_tflops", 1888.3)),
-            "spmv": spmv_roofline(kt, "batch_spmv_bytes", hbm, peak_kind,
-                                  "k_mm block residual R = B - A X (finest level, FP32, 16 right-hand sides)")}
-    # the same solves with the other tensor-core engine (tcgen05 with TMEM and TMA, or warp-level mma.sync)
-    Gm = vk.Hierarchy(Nc, L, k, options=vk.default_options(sweeps=sweeps, batch_prec=bp,
-                                                              batch_engine=engines[other],
-                                                              batch_max_iterations=args.batch_maxit))
-    Xm = torch.zeros_like(X)
-    Gm.solve_batch(Bs[0], Xm, rtol=rtol, maxit=args.batch_maxit)
-    torch.cuda.synchronize()
-    nm = min(args.steps, 3)
-    tm = 0.0
-    for st in range(nm):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.fill_(float(st))
-        e0.record(stream)
-        Gm.solve_batch(Bs[st % len(Bs)], Xm, rtol=rtol, maxit=args.batch_maxit)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tm += e0.elapsed_time(e1) / 1e3
-    Gm.stats_reset(time_kernels=True)
-    Gm.solve_batch(Bs[0], Xm, rtol=rtol, maxit=args.batch_maxit)
-    torch.cuda.synchronize()
-    km = Gm.stats()
-    am = km["apply_ms"] / max(km["apply_launches"], 1) / 1e3
-    other_engine = {"engine": other, "solves_per_s": 16 * nm / tm, "patch_apply_us": am * 1e6,
-                "patch_apply_gbs": km["batch_apply_bytes"] / am / 1e9,
-                "bytes_per_launch": km["batch_apply_bytes"]}
-    del Gm, Xm
-    # the same solves with the coarsest-level solve in FP32 instead of FP64 (batch_coarse_fp32)
-    Gc = vk.Hierarchy(Nc, L, k, options=vk.default_options(sweeps=sweeps, batch_prec=bp,
-                                                              batch_engine=engines[args.engine],
-                                                              batch_max_iterations=args.batch_maxit,
-                                                              batch_coarse_fp32=1))
-    Xc = torch.zeros_like(X)
-    Gc.solve_batch(Bs[0], Xc, rtol=rtol, maxit=args.batch_maxit)
-    torch.cuda.synchronize()
-    tc_ = 0.0
-    for st in range(nm):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.fill_(float(st))
-        e0.record(stream)
-        oc = Gc.solve_batch(Bs[st % len(Bs)], Xc, rtol=rtol, maxit=args.batch_maxit)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tc_ += e0.elapsed_time(e1) / 1e3
-    fp32_coarse = {"solves_per_s": 16 * nm / tc_, "iterations_mean": float(np.mean([o["iterations"] for o in oc]))}
-    del Gc, Xc
-    # plain FP64, one right-hand side at a time, same GPU and tolerance
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     G64 = vk.Hierarchy(Nc, L, k, options=vk.default_options(sweeps=sweeps))
+    n = G64.ndof()
     x1 = torch.zeros(n, dtype=torch.float64, device="cuda")
-    B0 = Bs[0]
-    G64.solve(B0[0].contiguous(), x1, rtol=rtol)
+    B = [torch.from_numpy(si.rhs_normal(n, 5000 + s)).cuda() for s in range(8)]
+    for w in range(3):
+        G64.solve(B[w], x1, rtol=rtol, history=False)
     torch.cuda.synchronize()
-    nf = min(args.steps, 8)
-    errs, t64 = [], 0.0
-    G.solve_batch(B0, X, rtol=rtol, maxit=args.batch_maxit)
-    for r in range(nf):
+    stream = torch.cuda.current_stream()
+    t64 = 0.0
+    for r in range(3, 8):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         flush.fill_(float(r))
         e0.record(stream)
-        G64.solve(B0[r].contiguous(), x1, rtol=rtol, history=False)
+        G64.solve(B[r], x1, rtol=rtol, history=False)
         e1.record(stream)
         torch.cuda.synchronize()
         t64 += e0.elapsed_time(e1) / 1e3
-        errs.append(float(torch.linalg.vector_norm(X[r] - x1) / torch.linalg.vector_norm(x1)))
-    fp64 = {"solves_per_s": nf / t64, "ms_per_solve": 1e3 * t64 / nf}
-    # FP64 single-right-hand-side kernels at this size: CUDA events around the finest patch apply and
-    # the finest residual SpMV (host-driven FGMRES loop, same kernels and launch shapes)
-    G64.stats_reset(time_kernels=True)
-    G64.solve(B0[0].contiguous(), x1, rtol=rtol, history=False)
-    torch.cuda.synchronize()
-    k64 = G64.stats()
-    G64.stats_reset(time_kernels=False)
-    a64 = k64["apply_ms"] / max(k64["apply_launches"], 1) / 1e3
-    fp64["patch_apply"] = {"kernel": "k_patch_apply (finest level, FP64 inverses)", "launch_avg_us": a64 * 1e6,
-                           "tflops": k64["apply_flops"] / a64 / 1e12,
-                           "frac_of_fp64_nominal": k64["apply_flops"] / a64 / 1e9 / FP64_NOMINAL_GFLOPS,
-                           "hbm_gbs": k64["apply_bytes"] / a64 / 1e9}
-    fp64["spmv"] = spmv_roofline(k64, "spmv_bytes", hbm, peak_kind, "k_sell residual r = b - A x (finest level, FP64)")
+    fp64_value = 5 / t64
+    clk = ClockSampler(0)
+    with clk:
+        rec = batch_record(vk, torch, si, cfg, args, flush, hbm, peaks, peak_kind, G64=G64, fp64_value=fp64_value,
+                           steps=args.steps)
+    other = "mma_sync" if args.engine == "tcgen05" else "tcgen05"
+    rec_other = batch_record(vk, torch, si, cfg, args, flush, hbm, peaks, peak_kind, engine=other, steps=3)
+    rec_c32 = batch_record(vk, torch, si, cfg, args, flush, hbm, peaks, peak_kind, coarse_fp32=1, steps=3)
     print(json.dumps({
-        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": rec["value"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": 3, "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
         "dtype": f"f64 FGMRES per column; f32 V-cycle with f64 coarsest solve; {args.batch_prec} patch inverses "
                  f"(tensor cores, f32 accumulate)",
-        "engine": args.engine,
         "data": "synthetic",
-        "config": {"workload": desc + ", 16 right-hand sides per step", "ndof": n, "levels": L, "k": k,
-                   "rhs_per_step": 16, "rtol": rtol, "setup_s": setup_s,
+        "config": {"workload": rec["workload"], "ndof": n, "levels": L, "k": k, "rhs_per_step": 16, "rtol": rtol,
+                   "engine": args.engine,
                    "l2": "256 MiB buffer overwritten between timed steps (outside the events)"},
-        "iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)), "max": int(max(iters))},
-        "vcycle_dof_per_s": 16 * n * stt["vcycles"] / total_s,
-        "latency_ms": {"p50": float(np.percentile(times_ms, 50)), "p99": float(np.percentile(times_ms, 99))},
-        "plain_fp64_single_rhs": fp64, "speedup_vs_plain_fp64": value / fp64["solves_per_s"],
-        "other_engine": other_engine, "fp32_coarse_solve_variant": fp32_coarse,
-        "rel_error_vs_fp64_solution": {"max": max(errs), "mean": float(np.mean(errs)), "columns": nf},
-        "gpu_launches": int(stt["launches"]), "roofline": roof, "clocks": clk.summary(),
+        "iterations": rec["iterations"], "vcycle_dof_per_s": rec["vcycle_dof_per_s"], "latency_ms": rec["latency_ms"],
+        "plain_fp64_single_rhs": {"solves_per_s": fp64_value},
+        "speedup_vs_plain_fp64": rec["speedup_vs_plain_fp64_one_at_a_time"],
+        "rel_error_vs_fp64_solution": rec["rel_error_vs_fp64_solution"],
+        "other_engine": {k_: rec_other[k_] for k_ in ("engine", "value", "roofline")},
+        "fp32_coarse_solve_variant": {k_: rec_c32[k_] for k_ in ("value", "iterations")},
+        "gpu_launches": rec["gpu_launches"], "roofline": dict(rec["roofline"], spmv=rec["spmv"]),
+        "clocks": clk.summary(),
     }), flush=True)
 
 
@@ -624,32 +750,36 @@ def run_serving(args):
     }), flush=True)
 
 
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vk", choices=["vk", "reference"])
-    ap.add_argument("--config", default="cfg2", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default=DEFAULT_CONFIG, choices=sorted(CONFIGS))
     ap.add_argument("--prec", default="f64", choices=["f64", "f64e", "f32"],
                     help="patch inverses: FP64, FP32-pair emulated FP64, or FP32")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven FGMRES loop instead of the whole-solve CUDA graph (for kernel profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-nested", action="store_true", help="cfg4: skip the nested cfg2 and 16-RHS records")
     ap.add_argument("--requests", type=int, default=1000, help="cfg5: requests in the 1x stream")
     ap.add_argument("--slots", type=int, default=4, help="cfg5: concurrent solves")
     ap.add_argument("--no-baseline", action="store_true", help="cfg5: skip the one-at-a-time FP64 pass")
-    ap.add_argument("--batch-prec", default="bf16", choices=["bf16", "fp16"], help="cfg4: 16-bit inverse format")
+    ap.add_argument("--batch-prec", default="bf16", choices=["bf16", "fp16"], help="16-bit inverse format")
     ap.add_argument("--spmv-warps", type=int, default=0, help="SELL threads-per-row rule (warps per SM); 0 = default")
     ap.add_argument("--levels", type=int, default=0, help="override the level count (profiling variants only)")
     ap.add_argument("--rtol", type=float, default=0.0, help="override the tolerance (profiling variants only)")
-    ap.add_argument("--batch-maxit", type=int, default=60, help="cfg4: FGMRES basis size per right-hand side")
+    ap.add_argument("--batch-maxit", type=int, default=60, help="FGMRES basis size per right-hand side (batch)")
     ap.add_argument("--engine", default="tcgen05", choices=["tcgen05", "mma_sync"],
-                    help="cfg4: tensor-core instruction family of the patch solves")
+                    help="tensor-core instruction family of the batched patch solves")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "vk":
         ap.error("--warmup must be >= 3")
-    cfg = CONFIGS[args.config]
+    config = args.config
+    cfg = CONFIGS[config]
     if args.levels or args.rtol:
         # a smaller or looser variant of a workload, for profiler captures (never a bench line)
         Nc, L, k, sweeps, rtol, desc = cfg
@@ -657,14 +787,15 @@ def main():
         rtol = args.rtol or rtol
         cfg = (Nc, L, k, sweeps, rtol, f"{desc.split(',')[0]}, {Nc}x{Nc} -> {Nc << (L - 1)}x{Nc << (L - 1)} "
                                          f"({L} levels), rtol {rtol:g} [profiling variant]")
+        config = config + "-variant"
     if args.impl == "reference":
-        run_reference(args, cfg)
+        run_reference(args, config, cfg)
     elif args.config == "cfg5":
         run_serving(args)
-    elif args.config == "cfg4":
-        run_batch(args, cfg)
+    elif args.config == "cfg4batch":
+        run_batch(args, config, cfg)
     else:
-        run_vk(args, cfg)
+        run_vk(args, config, cfg)
 
 
 if __name__ == "__main__":

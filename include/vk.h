@@ -314,9 +314,9 @@ typedef struct vk_stats {
   int64_t vcycles;         /* V-cycles started on the finest level                                   */
   int64_t apply_launches;  /* finest-level patch-apply launches bracketed by CUDA events            */
   double apply_ms;         /* their summed event durations (ms), measured on the launching stream   */
-  double apply_bytes;      /* algorithmic bytes of one finest-level patch-apply launch:
-                              s*sum(n_i^2) inverse entries (s = 8 FP64, 4 FP32) + 20*sum(n_i)
-                              (DoF index, gathered residual, written correction) + 16 per patch     */
+  double apply_bytes;      /* algorithmic bytes of one finest-level patch sweep:
+                              s*sum(n_i^2) inverse entries (s = 8 FP64 and FP32 pairs, 4 FP32)
+                              + 4*sum(n_i) DoF indices + 24*ndof (residual, correction in and out) */
   double apply_flops;      /* 2*sum(n_i^2) flops of one finest-level patch-apply launch             */
   double batch_apply_bytes;/* compulsory bytes of one finest-level tensor-core patch apply of
                               vk_solve_batch: 16-bit inverses as stored + index tables as read +
@@ -399,6 +399,12 @@ int vk_server_get_stats(vk_server* s, vk_server_stats* out);
 int vk_server_cancel(vk_server* s, uint64_t ticket);
 /* Finishes the queued requests, stops the workers and frees every hierarchy. */
 void vk_server_destroy(vk_server* s);
+
+/* Measurement helper (no counterpart in the paper: it measures the roofline denominator of the FP64
+ * kernels).  FMA throughput of the current device in TFLOP/s (2 flops per FMA): precision 0 = FP64,
+ * 1 = FP32.  Runs independent FMA chains on every SM, best of 5 launches timed with CUDA events on
+ * `stream` (synchronises it); allocates and frees a small device buffer.  VK_ERR_CUDA on failure. */
+int vk_measure_fma_rate(int precision, void* stream, double* tflops);
 
 /* Host-only helper: eigenvalues of the m x m row-major real upper-Hessenberg matrix H (the Arnoldi
  * matrix of the eigenvalue estimate).  Returns VK_ERR_INTERNAL if the QR iteration does not converge. */

@@ -54,6 +54,7 @@ struct Patches {
   const int64_t* foff = nullptr;    // npatch: offset (elements) of patch p's packed inverse
   const void* factors = nullptr;    // packed inverses: double (FP64), float (FP32) or float2 (FP32 pair)
   int prec = 0;                     // 0 = FP64, 1 = FP32, 2 = FP32 pair (emulated FP64)
+  int sym = 0;                      // 1: symmetric tile layout (sym_packed_size), else warp-packed
   int nb_max = 0;                   // largest packed column-group count ceil(n/4) of the level
   // DoF -> slots (ascending canonical patch order), for the atomic-free sum.  The patch solves write
   // the correction of canonical slot s to delta[slot_pos[s]], so the corrections of DoF i are the
@@ -91,6 +92,7 @@ int divide(double a, double* x, int n, cudaStream_t s);                  // x /=
 // and store it in the warp-packed layout.  status[0] receives 1 + the first singular patch id.
 // Returns -1 (nothing launched) when the level has a patch larger than 128 DoFs.
 int patch_factor(const Csr& A, const Patches& P, int prec, void* factors, int* status, cudaStream_t s);
+// (the layout written is P.sym's)
 // delta[slot] = (A_i^{-1} r[idx_i]) for every patch (one launch for all patches of a level).  With
 // FP32-pair inverses r is first split into r2 (ndof float2) and delta holds FP32 pairs.
 int patch_apply(const Patches& P, const double* r, float2* r2, double* delta, cudaStream_t s);
@@ -109,6 +111,17 @@ int vanka_scatter(const Patches& P, int ndof, const uint8_t* dir, const double* 
                    cudaStream_t s);
 // Size of the packed inverse of an n x n patch (elements): 32 * ceil(n/8) * ceil(n/4).
 inline int64_t packed_size(int n) { return 32LL * ((n + 7) / 8) * ((n + 3) / 4); }
+// Symmetric tile layout (FP32 and FP32-pair inverses of levels whose patches have at most kSymMaxN
+// DoFs).  A_i is a principal submatrix of the symmetric saddle-point matrix, so A_i^{-1} is symmetric:
+// with NT = ceil(n/8) blocks of 8 rows / columns, only the 8 x 8 tiles (I, J) with I <= J are stored,
+// row-major over I then J, 64 entries each; lane l = i + 8 j of a warp holds the entries (i, j) and
+// (i, j + 4) of a tile at positions 2 l and 2 l + 1 (one 16-byte load per lane for FP32 pairs).  An
+// off-diagonal entry stores the mean of the two mirrored entries of the computed inverse.
+constexpr int kSymMaxN = 80;
+inline int64_t sym_packed_size(int n) {
+  const int64_t t = (n + 7) / 8;
+  return 32LL * t * (t + 1);
+}
 
 // ---- dense coarse solve (kernels_dense.cu) --------------------------------------------------------
 // Dense bordered matrix [[A, z], [z^T, 0]] (row-major, (n+1)^2) from the CSR coarsest matrix.
@@ -240,6 +253,11 @@ int patch_apply_tc(const TcPatches& T, bool half, const float* rhs, float* delta
 
 // 16-bit fragment count (uint4 units) of an n x n patch: (ceil(n/16))^2 tiles of 32 lanes
 inline int64_t frag_size(int n) { return 32LL * ((n + 15) / 16) * ((n + 15) / 16); }
+
+// FMA throughput of this device (kernels_probe.cu): best of 5 timed launches of independent FMA
+// chains over every SM; FP64 or FP32; TFLOP/s (2 flops per FMA), or < 0 on a CUDA error.  scratch:
+// device buffer of at least 8 * 256 * 8 * (SM count) bytes (never written in practice).
+double fma_rate_tflops(bool fp64, void* scratch, cudaStream_t s);
 
 // x = sum_i Z[i] y[i]
 int combine(const double* Z, int64_t ldz, int m, const double* y, double* x, int n, cudaStream_t s);

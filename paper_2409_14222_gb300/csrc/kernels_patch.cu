@@ -41,7 +41,7 @@ template <typename FT>
 __global__ void __launch_bounds__(kFactorThreads) k_patch_factor(Csr A, const int* __restrict__ slot_ptr,
                                                                  const int* __restrict__ slot_dofs,
                                                                  const int64_t* __restrict__ foff,
-                                                                 FT* __restrict__ F, int* status) {
+                                                                 FT* __restrict__ F, int* status, int sym) {
   extern __shared__ double sm[];
   __shared__ double red_v[kFactorThreads / 32];
   __shared__ int red_i[kFactorThreads / 32];
@@ -128,8 +128,24 @@ __global__ void __launch_bounds__(kFactorThreads) k_patch_factor(Csr A, const in
       }
     }
   __syncthreads();
-  const int NB = (n + 3) / 4, NA = (n + 7) / 8;
   FT* out = F + foff[p];
+  if (sym) {
+    // symmetric tile layout: tiles (I, J), I <= J, row-major; entry (i, j + 4 w) of a tile at 2 l + w
+    // with l = i + 8 j; the stored value is the mean of the two mirrored entries
+    const int NT = (n + 7) / 8;
+    for (int e = tid; e < 32 * NT * (NT + 1); e += kFactorThreads) {
+      int rem = e >> 6, I = 0;
+      while (rem >= NT - I) {
+        rem -= NT - I;
+        ++I;
+      }
+      const int J = I + rem, l = (e & 63) >> 1, w = e & 1;
+      const int row = 8 * I + (l & 7), col = 8 * J + (l >> 3) + 4 * w;
+      out[e] = store_entry<FT>((row < n && col < n) ? 0.5 * (M[row * n + col] + M[col * n + row]) : 0.0);
+    }
+    return;
+  }
+  const int NB = (n + 3) / 4, NA = (n + 7) / 8;
   for (int e = tid; e < 32 * NA * NB; e += kFactorThreads) {
     const int lane = e & 31, ab = e >> 5;
     const int a = ab / NB, b = ab - a * NB;
@@ -298,6 +314,164 @@ __global__ void __launch_bounds__(256) k_patch_apply(int w0, int w1, const int* 
   }
 }
 
+// ---- symmetric tile layout (FP32 and FP32-pair inverses, patches of at most kSymMaxN DoFs) ----------
+// One warp per patch.  Lane l = i + 8 j holds entries (i, j) and (i, j + 4) of every stored tile
+// (I, J), I <= J.  With x the local residual:
+//   row part:    y_I += T_IJ x_J                 (lane: row i of block I, columns j, j + 4 of block J)
+//   column part: y_J += T_IJ^T x_I   (I < J)     (lane: columns j, j + 4 of block J, row i of block I)
+// so every stored off-diagonal entry is used twice and the lower triangle is never read.  The row
+// partial sums are combined over the four lanes of a row (xor 8, 16), the column partial sums over
+// the eight lanes of a column (xor 1, 2, 4); row m of block I is then row part + column part, written
+// by the lanes with j == I mod 4.  Fixed order everywhere, so every launch shape gives the same bits.
+template <typename FT>
+struct SymOps;
+
+template <>
+struct SymOps<float> {   // FP32 inverses: FP32 local residual, FP32 products and sums
+  using X = float;
+  using Vec = float2;    // a lane's two entries of a tile
+  struct Acc {
+    float v;
+  };
+  static __device__ __forceinline__ X load_x(const double* r, const float2*, int d) {
+    return __double2float_rn(__ldg(r + d));
+  }
+  static __device__ __forceinline__ X zero_x() { return 0.f; }
+  static __device__ __forceinline__ Acc zero() { return Acc{0.f}; }
+  static __device__ __forceinline__ void fma_(Acc& a, float e, X x) { a.v = __fmaf_rn(e, x, a.v); }
+  static __device__ __forceinline__ void entries(const Vec& v, float& e0, float& e1) {
+    e0 = v.x;
+    e1 = v.y;
+  }
+  static __device__ __forceinline__ Acc add(Acc a, Acc b) { return Acc{__fadd_rn(a.v, b.v)}; }
+  static __device__ __forceinline__ Acc shfl_xor(Acc a, int o) { return Acc{__shfl_xor_sync(0xffffffffu, a.v, o)}; }
+  static __device__ __forceinline__ Acc shfl(Acc a, int src) { return Acc{__shfl_sync(0xffffffffu, a.v, src)}; }
+  static __device__ __forceinline__ void store(double* delta, int idx, Acc a) { delta[idx] = double(a.v); }
+};
+
+template <>
+struct SymOps<float2> {  // FP32-pair inverses: pair products (exact split) with TwoSum accumulation
+  using X = float2;
+  using Vec = float4;
+  struct Acc {
+    float hi, lo;
+  };
+  static __device__ __forceinline__ X load_x(const double*, const float2* r2, int d) { return __ldg(r2 + d); }
+  static __device__ __forceinline__ X zero_x() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ Acc zero() { return Acc{0.f, 0.f}; }
+  static __device__ __forceinline__ void fma_(Acc& a, float2 e, X x) {
+    const float p = __fmul_rn(e.x, x.x);
+    float er = __fmaf_rn(e.x, x.x, -p);
+    er = __fmaf_rn(e.x, x.y, er);
+    er = __fmaf_rn(e.y, x.x, er);
+    two_sum_acc(a.hi, a.lo, p);
+    a.lo = __fadd_rn(a.lo, er);
+  }
+  static __device__ __forceinline__ void entries(const Vec& v, float2& e0, float2& e1) {
+    e0 = make_float2(v.x, v.y);
+    e1 = make_float2(v.z, v.w);
+  }
+  static __device__ __forceinline__ Acc add(Acc a, Acc b) {
+    two_sum_acc(a.hi, a.lo, b.hi);
+    a.lo = __fadd_rn(a.lo, b.lo);
+    return a;
+  }
+  static __device__ __forceinline__ Acc shfl_xor(Acc a, int o) {
+    return Acc{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+  }
+  static __device__ __forceinline__ Acc shfl(Acc a, int src) {
+    return Acc{__shfl_sync(0xffffffffu, a.hi, src), __shfl_sync(0xffffffffu, a.lo, src)};
+  }
+  static __device__ __forceinline__ void store(double* delta, int idx, Acc a) {
+    reinterpret_cast<float2*>(delta)[idx] = make_float2(a.hi, a.lo);
+  }
+};
+
+template <int NT, typename FT>
+__device__ __forceinline__ void apply_sym(int n, int s0, const int* __restrict__ dofs, const FT* __restrict__ Fp,
+                                          const double* __restrict__ r, const float2* __restrict__ r2,
+                                          const int* __restrict__ pos, double* __restrict__ delta, int lane) {
+  using O = SymOps<FT>;
+  using X = typename O::X;
+  using Vec = typename O::Vec;
+  using Acc = typename O::Acc;
+  using E = FT;
+  const int i = lane & 7, j = lane >> 3;
+  X xr[NT], xc0[NT], xc1[NT];
+#pragma unroll
+  for (int I = 0; I < NT; ++I) {
+    const int a = 8 * I + i, b0 = 8 * I + j, b1 = b0 + 4;
+    xr[I] = a < n ? O::load_x(r, r2, __ldg(dofs + a)) : O::zero_x();
+    xc0[I] = b0 < n ? O::load_x(r, r2, __ldg(dofs + b0)) : O::zero_x();
+    xc1[I] = b1 < n ? O::load_x(r, r2, __ldg(dofs + b1)) : O::zero_x();
+  }
+  Acc row[NT], col0[NT], col1[NT];
+#pragma unroll
+  for (int I = 0; I < NT; ++I) row[I] = col0[I] = col1[I] = O::zero();
+  const Vec* T = reinterpret_cast<const Vec*>(Fp) + lane;
+#pragma unroll
+  for (int I = 0; I < NT; ++I)
+#pragma unroll
+    for (int J = I; J < NT; ++J) {
+      const int t = I * NT - (I * (I - 1)) / 2 + (J - I);   // tiles before row I, then J - I
+      E e0, e1;
+      O::entries(__ldg(T + 32 * t), e0, e1);
+      O::fma_(row[I], e0, xc0[J]);
+      O::fma_(row[I], e1, xc1[J]);
+      if (I != J) {
+        O::fma_(col0[J], e0, xr[I]);
+        O::fma_(col1[J], e1, xr[I]);
+      }
+    }
+#pragma unroll
+  for (int I = 0; I < NT; ++I) {
+    row[I] = O::add(row[I], O::shfl_xor(row[I], 8));
+    row[I] = O::add(row[I], O::shfl_xor(row[I], 16));
+#pragma unroll
+    for (int o = 1; o <= 4; o <<= 1) {
+      col0[I] = O::add(col0[I], O::shfl_xor(col0[I], o));
+      col1[I] = O::add(col1[I], O::shfl_xor(col1[I], o));
+    }
+  }
+#pragma unroll
+  for (int I = 0; I < NT; ++I) {
+    const int src = (i & 3) << 3;              // a lane whose column index is i mod 4
+    const Acc c0 = O::shfl(col0[I], src), c1 = O::shfl(col1[I], src);
+    const Acc y = O::add(row[I], i < 4 ? c0 : c1);
+    const int m = 8 * I + i;
+    if (j == (I & 3) && m < n) O::store(delta, __ldg(pos + s0 + m), y);
+  }
+}
+
+template <int NT, int NTMAX, typename FT>
+__device__ __forceinline__ void sym_dispatch(int nt, int n, int s0, const int* dofs, const FT* Fp, const double* r,
+                                             const float2* r2, const int* pos, double* delta, int lane) {
+  if constexpr (NT <= NTMAX) {
+    if (nt == NT)
+      apply_sym<NT, FT>(n, s0, dofs, Fp, r, r2, pos, delta, lane);
+    else
+      sym_dispatch<NT + 1, NTMAX, FT>(nt, n, s0, dofs, Fp, r, r2, pos, delta, lane);
+  }
+}
+
+// Work items w0 <= w < w1 with NTLO <= ceil(n/8) <= NTHI, one warp per patch (or a persistent grid).
+template <int NTLO, int NTHI, typename FT>
+__global__ void __launch_bounds__(256) k_patch_apply_sym(int w0, int w1, const int* __restrict__ work,
+                                                         const int* __restrict__ slot_ptr,
+                                                         const int* __restrict__ slot_dofs,
+                                                         const int64_t* __restrict__ foff,
+                                                         const FT* __restrict__ F, const double* __restrict__ r,
+                                                         const float2* __restrict__ r2, const int* __restrict__ pos,
+                                                         double* __restrict__ delta) {
+  const int nwarps = int((int64_t(gridDim.x) * blockDim.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  for (int w = w0 + int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); w < w1; w += nwarps) {
+    const int p = work[w];
+    const int s0 = slot_ptr[p], n = slot_ptr[p + 1] - s0;
+    sym_dispatch<NTLO, NTHI, FT>((n + 7) >> 3, n, s0, slot_dofs + s0, F + foff[p], r, r2, pos, delta, lane);
+  }
+}
+
 // r = rh + rl with rh = fl32(r), rl = fl32(r - rh): the FP32-pair form of a residual, once per DoF.
 __global__ void k_split_pairs(const double* __restrict__ r, float2* __restrict__ r2, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -385,6 +559,32 @@ int launch_range(const Patches& P, const ApplySched& sc, int w0, int w1, const d
   return 1;
 }
 
+template <int NTLO, int NTHI, typename FT>
+int launch_range_sym(const Patches& P, const ApplySched& sc, int w0, int w1, const double* r, const float2* r2,
+                     double* delta, cudaStream_t s) {
+  if (w1 <= w0) return 0;
+  k_patch_apply_sym<NTLO, NTHI, FT><<<apply_blocks(w1 - w0, sc, P.nsm), sc.threads, 0, s>>>(
+      w0, w1, P.work, P.slot_ptr, P.slot_dofs, P.foff, static_cast<const FT*>(P.factors), r, r2, P.slot_pos, delta);
+  return 1;
+}
+
+// Symmetric layout: the same launch shapes; the size classes of ceil(n/4) map to ceil(n/8) ranges
+// 1-2, 3-5, 6-10 and 10 (n <= kSymMaxN = 80).
+template <typename FT>
+int apply_sym_prec(const Patches& P, const ApplySched& sc, const double* r, const float2* r2, double* delta,
+                   cudaStream_t s) {
+  if (!sc.split) {
+    if (P.nb_max <= 10) return launch_range_sym<1, 5, FT>(P, sc, 0, P.npatch, r, r2, delta, s);
+    return launch_range_sym<1, 10, FT>(P, sc, 0, P.npatch, r, r2, delta, s);
+  }
+  int k = 0;
+  k += launch_range_sym<10, 10, FT>(P, sc, P.cls_lo[3], P.cls_hi[3], r, r2, delta, s);
+  k += launch_range_sym<6, 10, FT>(P, sc, P.cls_lo[2], P.cls_hi[2], r, r2, delta, s);
+  k += launch_range_sym<3, 5, FT>(P, sc, P.cls_lo[1], P.cls_hi[1], r, r2, delta, s);
+  k += launch_range_sym<1, 2, FT>(P, sc, P.cls_lo[0], P.cls_hi[0], r, r2, delta, s);
+  return k;
+}
+
 template <typename FT>
 int apply_prec(const Patches& P, const ApplySched& sc, const double* r, const float2* r2, double* delta,
                cudaStream_t s) {
@@ -418,15 +618,15 @@ int patch_factor(const Csr& A, const Patches& P, int prec, void* factors, int* s
   if (prec == 0) {
     cudaFuncSetAttribute(k_patch_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);
     k_patch_factor<double><<<P.npatch, kFactorThreads, smem, s>>>(A, P.slot_ptr, P.slot_dofs, P.foff,
-                                                                   static_cast<double*>(factors), status);
+                                                                   static_cast<double*>(factors), status, P.sym);
   } else if (prec == 1) {
     cudaFuncSetAttribute(k_patch_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);
     k_patch_factor<float><<<P.npatch, kFactorThreads, smem, s>>>(A, P.slot_ptr, P.slot_dofs, P.foff,
-                                                                  static_cast<float*>(factors), status);
+                                                                  static_cast<float*>(factors), status, P.sym);
   } else {
     cudaFuncSetAttribute(k_patch_factor<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);
     k_patch_factor<float2><<<P.npatch, kFactorThreads, smem, s>>>(A, P.slot_ptr, P.slot_dofs, P.foff,
-                                                                   static_cast<float2*>(factors), status);
+                                                                   static_cast<float2*>(factors), status, P.sym);
   }
   return 1;
 }
@@ -435,11 +635,12 @@ int patch_apply_sched(const Patches& P, const ApplySched& sc, const double* r, f
                       cudaStream_t s) {
   if (P.npatch == 0) return 0;
   if (P.prec == 0) return apply_prec<double>(P, sc, r, nullptr, delta, s);
-  if (P.prec == 1) return apply_prec<float>(P, sc, r, nullptr, delta, s);
+  if (P.prec == 1)
+    return P.sym ? apply_sym_prec<float>(P, sc, r, nullptr, delta, s) : apply_prec<float>(P, sc, r, nullptr, delta, s);
   // FP32-pair inverses: split the residual once per DoF first
   const int n = P.ndof;
   k_split_pairs<<<(n + 255) / 256, 256, 0, s>>>(r, r2, n);
-  return 1 + apply_prec<float2>(P, sc, r, r2, delta, s);
+  return 1 + (P.sym ? apply_sym_prec<float2>(P, sc, r, r2, delta, s) : apply_prec<float2>(P, sc, r, r2, delta, s));
 }
 
 int patch_apply(const Patches& P, const double* r, float2* r2, double* delta, cudaStream_t s) {

@@ -177,23 +177,30 @@ struct HostPatchPlan {
   std::vector<int64_t> foff;    // canonical id -> packed offset
   int64_t ftotal = 0;
   int nb_max = 0;
+  bool sym = false;             // symmetric tile layout of the inverses
   int cls_lo[4] = {0, 0, 0, 0}, cls_hi[4] = {0, 0, 0, 0};  // work-list range of each size class
   std::vector<int> dof_ptr, slot_pos;
   std::vector<double> weight;
 };
 
-HostPatchPlan plan_patches(const vk::HostLevel& L, int weights) {
+// Work order, storage offsets and DoF -> slot transpose of one level's patches.  FP32 and FP32-pair
+// inverses use the symmetric tile layout when every patch of the level has at most kSymMaxN DoFs.
+HostPatchPlan plan_patches(const vk::HostLevel& L, int weights, int prec) {
   HostPatchPlan P;
   const int np = int(L.patch_ptr.size()) - 1;
   P.work.resize(np);
   std::iota(P.work.begin(), P.work.end(), 0);
   auto nb = [&](int p) { return (L.patch_ptr[p + 1] - L.patch_ptr[p] + 3) / 4; };
   std::stable_sort(P.work.begin(), P.work.end(), [&](int a, int b) { return nb(a) > nb(b); });
+  int nmax = 0;
+  for (int p = 0; p < np; ++p) nmax = std::max(nmax, L.patch_ptr[p + 1] - L.patch_ptr[p]);
+  P.sym = prec != VK_PREC_F64 && nmax <= vk::gpu::kSymMaxN;
   P.foff.assign(np, 0);
   for (int w = 0; w < np; ++w) {
     const int p = P.work[w];
+    const int n = L.patch_ptr[p + 1] - L.patch_ptr[p];
     P.foff[p] = P.ftotal;
-    P.ftotal += vk::gpu::packed_size(L.patch_ptr[p + 1] - L.patch_ptr[p]);
+    P.ftotal += P.sym ? vk::gpu::sym_packed_size(n) : vk::gpu::packed_size(n);
     P.nb_max = std::max(P.nb_max, nb(p));
   }
   // size classes of ceil(n/4) (the work list is sorted by it, largest first, so each class is a range)
@@ -491,7 +498,7 @@ void allocate_batch(vk_hierarchy* h) {
       // largest first), cut into groups of kTcG[c] patches; each group's A image holds ceil(nmax/8)
       // K chunks of 2048 bytes
       {
-        const HostPatchPlan plan = plan_patches(H, h->opt.weights);
+        const HostPatchPlan plan = plan_patches(H, h->opt.weights, h->opt.factor_prec);
         int64_t btot = 0;
         vk::gpu::TcPatches& T = D.tc;
         for (int c = 0; c < 3; ++c) {
@@ -606,7 +613,7 @@ void allocate_device(vk_hierarchy* h) {
     D.d = m.get_n<double>(H.ndof);
     D.t = m.get_n<double>(H.ndof);
     if (l > 0) {
-      HostPatchPlan P = plan_patches(H, h->opt.weights);
+      HostPatchPlan P = plan_patches(H, h->opt.weights, h->opt.factor_prec);
       vk::gpu::Patches& G = D.pat;
       G.npatch = int(H.patch_ptr.size()) - 1;
       G.ndof = H.ndof;
@@ -618,6 +625,7 @@ void allocate_device(vk_hierarchy* h) {
       G.factors = m.get(size_t(P.ftotal) * fsz);
       G.prec = h->opt.factor_prec;
       G.nb_max = P.nb_max;
+      G.sym = P.sym ? 1 : 0;
       for (int c = 0; c < 4; ++c) {
         G.cls_lo[c] = P.cls_lo[c];
         G.cls_hi[c] = P.cls_hi[c];
@@ -891,8 +899,9 @@ void setup_device(vk_hierarchy* h, cudaStream_t s) {
       sn2 += n * n;
     }
     const double fsz = h->opt.factor_prec == VK_PREC_F32 ? 4.0 : 8.0;
-    // inverse entries + slot DoF indices + gathered r + written delta + per-patch work/offset/pointers
-    h->apply_bytes = fsz * sn2 + 20.0 * sn + 16.0 * np;
+    // algorithmic bytes of one sweep: the stored inverse entries, one 4-byte DoF index per slot, and
+    // the residual read plus the correction read and written once per DoF
+    h->apply_bytes = fsz * sn2 + 4.0 * sn + 24.0 * double(F.ndof);
     h->apply_flops = 2.0 * sn2;
     // residual SpMV r = b - A x: value + column index per stored nonzero; row index, b, x, r per row
     const double nnz = double(F.A.nnz()), nrow = double(F.ndof);
@@ -1755,6 +1764,23 @@ int vk_stats_read(vk_hierarchy* h, vk_stats* out) {
     out->spmv_ms = h->tm_spmv.total_ms();
     out->spmv_bytes = h->spmv_bytes;
     out->batch_spmv_bytes = h->bspmv_bytes;
+    return VK_OK;
+  });
+}
+
+int vk_measure_fma_rate(int precision, void* stream, double* tflops) {
+  return guard([&] {
+    if (!tflops || (precision != 0 && precision != 1)) raise(VK_ERR_ARG, "bad arguments");
+    std::lock_guard<std::mutex> lock(g_device_mu);
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    void* scratch = nullptr;
+    CK(cudaMalloc(&scratch, size_t(nsm) * 8 * 256 * 8));
+    const double t = vk::gpu::fma_rate_tflops(precision == 0, scratch, static_cast<cudaStream_t>(stream));
+    cudaFree(scratch);
+    if (!(t > 0.0)) raise(VK_ERR_CUDA, "FMA-rate probe failed");
+    *tflops = t;
     return VK_OK;
   });
 }

@@ -43,7 +43,7 @@ SYMBOLS = [
     "vk_coarse_solve", "vk_vcycle", "vk_solve", "vk_solve_host", "vk_csr_dims", "vk_export_csr",
     "vk_export_patches", "vk_export_dirichlet", "vk_hessenberg_eigenvalues", "vk_stats_reset", "vk_stats_read",
     "vk_vanka_noalloc", "vk_solve_batch", "vk_apply_schedule", "vk_ndof", "vk_export_dof_coords", "vk_default_server_config", "vk_server_create", "vk_server_submit", "vk_server_wait",
-    "vk_server_get_stats", "vk_server_destroy", "vk_check_problem", "vk_server_cancel",
+    "vk_server_get_stats", "vk_server_destroy", "vk_check_problem", "vk_server_cancel", "vk_measure_fma_rate",
 ]
 
 
@@ -166,6 +166,7 @@ def lib():
             "vk_server_destroy": (None, [VP]),
             "vk_server_cancel": (I, [VP, ctypes.c_uint64]),
             "vk_check_problem": (I, [P(vk_problem), P(vk_options)]),
+            "vk_measure_fma_rate": (I, [I, VP, P(D)]),
             "vk_stats_read": (I, [H, P(vk_stats)]),
             "vk_apply_schedule": (I, [H, I, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32),
                                       P(ctypes.c_int32), VP, P(ctypes.c_int32)]),
@@ -442,6 +443,13 @@ def hessenberg_eigenvalues(H):
     re, im = np.zeros(m), np.zeros(m)
     check(lib().vk_hessenberg_eigenvalues(m, _ptr(H), _ptr(re), _ptr(im)))
     return re + 1j * im
+
+
+def measure_fma_rate(fp64=True, stream=None):
+    """FMA throughput of the current device in TFLOP/s (vk_measure_fma_rate), FP64 or FP32."""
+    v = ctypes.c_double()
+    check(lib().vk_measure_fma_rate(0 if fp64 else 1, _stream_handle(stream), ctypes.byref(v)))
+    return v.value
 
 
 def ndof_of(N_coarse, nlevels, k):

@@ -141,7 +141,13 @@ def test_footprint_follows_the_options(vk):
     f64 = vk.footprint(*key)
     f32 = vk.footprint(*key, options=vk.default_options(factor_prec=vk.VK_PREC_F32))
     f64e = vk.footprint(*key, options=vk.default_options(factor_prec=vk.VK_PREC_F64E))
-    assert f32 < f64 < f64e          # 4-byte inverses; FP32 pairs also keep a split residual
+    # P2 patches (<= 39 DoFs): FP32 and FP32-pair inverses keep only the upper 8x8 tiles of the
+    # symmetric inverse; FP64 keeps the full warp-packed inverse
+    assert f32 < f64e < f64
+    # P4 patches (up to 123 DoFs) exceed the symmetric layout's bound: FP32 pairs are stored in full
+    # and keep a split residual as well
+    f64_p4 = vk.footprint(4, 2, 4)
+    assert f64_p4 < vk.footprint(4, 2, 4, options=vk.default_options(factor_prec=vk.VK_PREC_F64E))
     batch = vk.footprint(*key, options=vk.default_options(batch_prec=vk.VK_BATCH_BF16))
     assert batch > f64
     # FP32 coarse copy (n_c + 1)^2 floats instead of two FP64 16-column coarse blocks

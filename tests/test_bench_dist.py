@@ -57,3 +57,17 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
     assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["unit"] == "solves/s"
     assert rec["value"] > 0 and rec["e2e"]["h2d_bytes_per_step"] == 0
     assert rec["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_reference_arm_prints_the_time_it_measured():
+    # the printed ms_per_step x steps is the measured time of the samples; the extrapolation to one solve
+    # of the 512 x 512 workload is a separate, stated factor
+    cmd = [sys.executable, "bench.py", "--impl", "reference", "--config", "cfg4", "--steps", "2", "--warmup", "1"]
+    res = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert res.returncode == 0, res.stderr[-2000:]
+    rec = json.loads([ln for ln in res.stdout.splitlines() if ln.startswith("{")][-1])
+    ex = rec["extrapolation"]
+    assert abs(rec["ms_per_step"] * rec["steps"] - 1e3 * ex["timed_seconds"]) <= 1e-6 * 1e3 * ex["timed_seconds"]
+    assert abs(rec["value"] - rec["steps"] / (ex["timed_seconds"] * ex["scale"])) <= 1e-9 * rec["value"]
+    assert ex["target_ndof"] == 2364419 and rec["config"]["ndof"] == 2364419
+    assert "512x512" in rec["config"]["workload"]

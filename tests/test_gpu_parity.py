@@ -327,6 +327,40 @@ def test_fp32_factors_reach_tolerance(vk):
     assert err <= 1e-3
 
 
+@pytest.fixture(scope="module")
+def weighted(vk):
+    # Algorithm 1 with the multiplicity weights (each DoF's summed correction divided by the number of
+    # patches containing it), lambda estimated independently on both sides
+    out = {}
+    for case in [(4, 2, 2), (2, 3, 3), (2, 2, 4)]:
+        Nc, L, k = case
+        H = solver.Hierarchy(Nc, L, k, weights="multiplicity")
+        G = vk.Hierarchy(Nc, L, k, options=vk.default_options(weights=vk.VK_WEIGHTS_MULTIPLICITY))
+        out[case] = (H, G)
+    return out
+
+
+@pytest.mark.parametrize("case", [(4, 2, 2), (2, 3, 3), (2, 2, 4)])
+def test_multiplicity_weights_parity(vk, weighted, case):
+    H, G = weighted[case]
+    for l in range(1, case[1]):
+        assert abs(G.lam(l) - H.levels[l].lam) <= 1e-10 * H.levels[l].lam
+    rng = np.random.default_rng(51)
+    for l in range(1, case[1]):
+        lev = H.levels[l]
+        r = rng.standard_normal(lev.space.ndof)
+        z = torch.empty_like(dev(r))
+        G.vanka(l, dev(r), z)
+        got = host(z)
+        assert rel(got, solver.vanka_apply(lev, r)) <= 1e-10
+        assert np.array_equal(got[lev.mask], r[lev.mask])
+    b = rng.standard_normal(H.finest.space.ndof)
+    x = torch.empty_like(dev(b))
+    G.vcycle(dev(b), x)
+    assert rel(host(x), H.vcycle(b)) <= 1e-9
+    _solve_parity(vk, H, G, si.rhs_normal(H.finest.space.ndof, 0), 1e-10)
+
+
 def test_device_footprint_matches_prediction(vk):
     H, G = pair(vk, (2, 3, 3), inject=False)
     assert G.device_bytes() == vk.footprint(2, 3, 3)
