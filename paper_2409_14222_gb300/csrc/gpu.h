@@ -259,6 +259,123 @@ inline int64_t frag_size(int n) { return 32LL * ((n + 15) / 16) * ((n + 15) / 16
 // device buffer of at least 8 * 256 * 8 * (SM count) bytes (never written in practice).
 double fma_rate_tflops(bool fp64, void* scratch, cudaStream_t s);
 
+// ---- group kernels: one launch over the members of a group solve (vk_group_*) -------------------
+// Each member is an independent solve on its own hierarchy (its own mesh size, order and matrices).
+// A group launch processes the work of every member listed in its by-value argument block; item
+// ranges of the members are concatenated (prefix[m] .. prefix[m+1]) and a warp, thread or block finds
+// its member by a search over the prefix.  Per element, every group kernel does exactly the
+// arithmetic of its single-member counterpart, so a member's results do not depend on the others.
+constexpr int kGroupMax = 24;
+
+#ifdef __CUDACC__
+// Member of a concatenated range: the largest m with prefix[m] <= i (prefix[0] = 0, count members).
+__device__ __forceinline__ int group_member(const int* prefix, int count, int i) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+#endif
+
+struct GroupSpmvArgs {         // y = op(A) x per member (SELL modes of sell_residual etc.)
+  int count = 0;
+  int prefix[kGroupMax + 1] = {};   // slices
+  Sell A[kGroupMax];
+  const double* b[kGroupMax] = {};
+  const uint8_t* mask[kGroupMax] = {};
+  const double* x[kGroupMax] = {};
+  double* y[kGroupMax] = {};
+};
+// mode 0: y = b - A x, 1: y = A x, 2: y = b + A x, 3: y = mask ? 0 : A x
+int group_spmv(int mode, const GroupSpmvArgs& a, cudaStream_t s);
+
+struct GroupPatch {            // one level's patches of one member (the fields patch_apply reads)
+  const int* work = nullptr;
+  const int* slot_ptr = nullptr;
+  const int* slot_dofs = nullptr;
+  const int64_t* foff = nullptr;
+  const void* factors = nullptr;
+  const int* slot_pos = nullptr;
+  const int* dof_ptr = nullptr;
+  const double* weight = nullptr;
+  const uint8_t* dir = nullptr;
+  int sym = 0, ndof = 0;
+};
+struct GroupApplyArgs {        // delta = A_i^{-1} r[idx_i] for every patch of every member
+  int count = 0, prec = 0;          // prec: VK_PREC_* shared by the members
+  int nb_max = 0;                   // largest ceil(n/4) over the members' patches
+  int prefix[kGroupMax + 1] = {};   // patches (work items)
+  int dprefix[kGroupMax + 1] = {};  // DoFs (FP32-pair split of the residuals)
+  GroupPatch P[kGroupMax];
+  const double* r[kGroupMax] = {};
+  float2* r2[kGroupMax] = {};       // FP32-pair residual (prec 2)
+  double* delta[kGroupMax] = {};
+};
+int group_patch_apply(const GroupApplyArgs& a, cudaStream_t s);
+
+struct GroupScatterArgs {      // sum of the corrections + Dirichlet identity + Chebyshev update
+  int count = 0, prec = 0, mode = 0;
+  int prefix[kGroupMax + 1] = {};   // DoFs
+  GroupPatch P[kGroupMax];
+  const double* r[kGroupMax] = {};
+  const double* delta[kGroupMax] = {};
+  double theta[kGroupMax] = {}, c1[kGroupMax] = {}, c2[kGroupMax] = {};
+  double* z[kGroupMax] = {};
+  double* d[kGroupMax] = {};
+  double* x[kGroupMax] = {};
+};
+int group_vanka_scatter(const GroupScatterArgs& a, cudaStream_t s);
+
+struct GroupGemvArgs {         // x = Minv[0:n, 0:n] b per member (coarsest bordered inverse)
+  int count = 0;
+  int prefix[kGroupMax + 1] = {};   // rows
+  const double* Minv[kGroupMax] = {};
+  int n[kGroupMax] = {}, ld[kGroupMax] = {};
+  const double* b[kGroupMax] = {};
+  double* x[kGroupMax] = {};
+};
+int group_dense_gemv(const GroupGemvArgs& a, cudaStream_t s);
+
+struct GroupVecArgs {          // per-member vectors for the FGMRES kernels below
+  int count = 0;
+  int n[kGroupMax] = {};
+  const double* V[kGroupMax] = {};  // basis (leading dimension ld)
+  int64_t ld[kGroupMax] = {};
+  int nvec[kGroupMax] = {};         // vectors of V used (j + 1)
+  double* w[kGroupMax] = {};
+  double* partial[kGroupMax] = {};  // member scratch: kReduceBlocks * (kmax + 1) doubles
+  double* out[kGroupMax] = {};      // member results (H column, t2, scalar, ...)
+  double* acc[kGroupMax] = {};
+  int off[kGroupMax] = {}, len[kGroupMax] = {};   // pressure block (projection)
+};
+// partial sums of V[i] . w, i < nvec (grid kReduceBlocks x sum of nvec), then out[i] (+ acc[i])
+int group_multi_dot(const GroupVecArgs& a, cudaStream_t s);
+// w -= sum_i V[i] out[i]
+int group_multi_axpy(const GroupVecArgs& a, cudaStream_t s);
+// w[off .. off+len) -= its mean (out = scratch scalar)
+int group_pressure_project(const GroupVecArgs& a, cudaStream_t s);
+// out[0] = w . w (through partial)
+int group_norm2(const GroupVecArgs& a, cudaStream_t s);
+struct GroupGivensArgs {
+  int count = 0;
+  double* H[kGroupMax] = {};
+  int ldh[kGroupMax] = {};
+  double *cs[kGroupMax] = {}, *sn[kGroupMax] = {}, *g[kGroupMax] = {}, *hist[kGroupMax] = {};
+  int j[kGroupMax] = {};
+  double rtol[kGroupMax] = {};
+  int* flag[kGroupMax] = {};
+  const double* wsq[kGroupMax] = {};   // ||w||^2 of the new basis vector
+  const double* w[kGroupMax] = {};
+  double* vnext[kGroupMax] = {};       // V[j + 1] = w / ||w||
+  int n[kGroupMax] = {};
+  int kmax = 0;
+};
+// H[j+1][j] = ||w||, V[j+1] = w / ||w|| (all members, one launch), then the rotations of column j
+// (one block per member); flag[0] converged, flag[1] non-finite
+int group_normalize_givens(const GroupGivensArgs& a, cudaStream_t s);
+
 // x = sum_i Z[i] y[i]
 int combine(const double* Z, int64_t ldz, int m, const double* y, double* x, int n, cudaStream_t s);
 // y = scale * x

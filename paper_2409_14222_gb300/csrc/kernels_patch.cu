@@ -482,16 +482,11 @@ __global__ void k_split_pairs(const double* __restrict__ r, float2* __restrict__
 }
 
 template <bool kPairs>
-__global__ void __launch_bounds__(256) k_vanka_scatter(int ndof, const int* __restrict__ dptr,
-                                                       const double* __restrict__ weight,
-                                                       const uint8_t* __restrict__ dir,
-                                                       const double* __restrict__ r,
-                                                       const double* __restrict__ delta, int mode,
-                                                       double theta, double c1, double c2,
-                                                       double* __restrict__ zout, double* __restrict__ d,
-                                                       double* __restrict__ x) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ndof) return;
+__device__ __forceinline__ void scatter_dof(int i, const int* __restrict__ dptr, const double* __restrict__ weight,
+                                            const uint8_t* __restrict__ dir, const double* __restrict__ r,
+                                            const double* __restrict__ delta, int mode, double theta, double c1,
+                                            double c2, double* __restrict__ zout, double* __restrict__ d,
+                                            double* __restrict__ x) {
   double z;
   if (dir[i]) {
     z = r[i];
@@ -539,6 +534,61 @@ __global__ void __launch_bounds__(256) k_vanka_scatter(int ndof, const int* __re
       break;
     }
   }
+}
+
+template <bool kPairs>
+__global__ void __launch_bounds__(256) k_vanka_scatter(int ndof, const int* __restrict__ dptr,
+                                                       const double* __restrict__ weight,
+                                                       const uint8_t* __restrict__ dir,
+                                                       const double* __restrict__ r,
+                                                       const double* __restrict__ delta, int mode,
+                                                       double theta, double c1, double c2,
+                                                       double* __restrict__ zout, double* __restrict__ d,
+                                                       double* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ndof) return;
+  scatter_dof<kPairs>(i, dptr, weight, dir, r, delta, mode, theta, c1, c2, zout, d, x);
+}
+
+// ---- group forms (one launch over the members of a group solve) ---------------------------------
+template <bool kPairs>
+__global__ void __launch_bounds__(256) k_group_scatter(const __grid_constant__ GroupScatterArgs a) {
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= a.prefix[a.count]) return;
+  const int m = group_member(a.prefix, a.count, gi);
+  const GroupPatch& P = a.P[m];
+  scatter_dof<kPairs>(gi - a.prefix[m], P.dof_ptr, P.weight, P.dir, a.r[m], a.delta[m], a.mode, a.theta[m], a.c1[m],
+                      a.c2[m], a.z[m], a.d[m], a.x[m]);
+}
+
+__global__ void k_group_split_pairs(const __grid_constant__ GroupApplyArgs a) {
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= a.dprefix[a.count]) return;
+  const int m = group_member(a.dprefix, a.count, gi), i = gi - a.dprefix[m];
+  const double v = a.r[m][i];
+  const float h = __double2float_rn(v);
+  a.r2[m][i] = make_float2(h, __double2float_rn(v - double(h)));
+}
+
+// One warp per patch of any member, in each member's own work order and storage layout.
+template <int NBMAX, typename FT>
+__global__ void __launch_bounds__(256) k_group_apply(const __grid_constant__ GroupApplyArgs a) {
+  const int gw = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+  if (gw >= a.prefix[a.count]) return;
+  const int m = group_member(a.prefix, a.count, gw);
+  const GroupPatch& P = a.P[m];
+  const int lane = threadIdx.x & 31;
+  const int p = P.work[gw - a.prefix[m]];
+  const int s0 = P.slot_ptr[p], n = P.slot_ptr[p + 1] - s0;
+  const FT* F = static_cast<const FT*>(P.factors) + P.foff[p];
+  if constexpr (!std::is_same<FT, double>::value) {
+    if (P.sym) {
+      sym_dispatch<1, 10, FT>((n + 7) >> 3, n, s0, P.slot_dofs + s0, F, a.r[m], a.r2[m], P.slot_pos, a.delta[m], lane);
+      return;
+    }
+  }
+  apply_dispatch<1, NBMAX, FT>((n + 3) >> 2, n, s0, P.slot_dofs + s0, F, a.r[m], a.r2[m], P.slot_pos, a.delta[m],
+                               lane);
 }
 
 // Blocks of one launch over `items` work items: one warp per item, or (per_sm > 0) at most per_sm
@@ -645,6 +695,36 @@ int patch_apply_sched(const Patches& P, const ApplySched& sc, const double* r, f
 
 int patch_apply(const Patches& P, const double* r, float2* r2, double* delta, cudaStream_t s) {
   return patch_apply_sched(P, P.sched, r, r2, delta, s);
+}
+
+template <typename FT>
+int group_apply_prec(const GroupApplyArgs& a, cudaStream_t s) {
+  const int blocks = (a.prefix[a.count] + 7) / 8;   // 8 warps of 256 threads
+  if (a.nb_max <= 10)
+    k_group_apply<10, FT><<<blocks, 256, 0, s>>>(a);
+  else if (a.nb_max <= 19)
+    k_group_apply<19, FT><<<blocks, 256, 0, s>>>(a);
+  else
+    k_group_apply<32, FT><<<blocks, 256, 0, s>>>(a);
+  return 1;
+}
+
+int group_patch_apply(const GroupApplyArgs& a, cudaStream_t s) {
+  if (a.count == 0 || a.prefix[a.count] == 0) return 0;
+  if (a.prec == 0) return group_apply_prec<double>(a, s);
+  if (a.prec == 1) return group_apply_prec<float>(a, s);
+  k_group_split_pairs<<<(a.dprefix[a.count] + 255) / 256, 256, 0, s>>>(a);
+  return 1 + group_apply_prec<float2>(a, s);
+}
+
+int group_vanka_scatter(const GroupScatterArgs& a, cudaStream_t s) {
+  if (a.count == 0 || a.prefix[a.count] == 0) return 0;
+  const int blocks = (a.prefix[a.count] + 255) / 256;
+  if (a.prec == 2)
+    k_group_scatter<true><<<blocks, 256, 0, s>>>(a);
+  else
+    k_group_scatter<false><<<blocks, 256, 0, s>>>(a);
+  return 1;
 }
 
 int vanka_scatter(const Patches& P, int ndof, const uint8_t* dir, const double* r, const double* delta,

@@ -23,15 +23,12 @@ inline int blocks_for(int64_t n, int t = kThreads) { return int((n + t - 1) / t)
 //   kMode 2: y = b + A x          3: y = mask ? 0 : A x   (mask = Dirichlet flags of the output)
 // (b and y may be the same vector: each row reads b[row] before writing y[row].)
 template <int kMode, int T>
-__global__ void __launch_bounds__(kThreads) k_sell(int nslices, const int64_t* __restrict__ sptr,
-                                                   const int* __restrict__ sw, const int* __restrict__ col,
-                                                   const double* __restrict__ val, const int* __restrict__ rowof,
-                                                   const double* b, const uint8_t* __restrict__ mask,
-                                                   const double* __restrict__ x, double* y) {
+__device__ __forceinline__ void sell_slice(int warp, int lane, const int64_t* __restrict__ sptr,
+                                           const int* __restrict__ sw, const int* __restrict__ col,
+                                           const double* __restrict__ val, const int* __restrict__ rowof,
+                                           const double* b, const uint8_t* __restrict__ mask,
+                                           const double* __restrict__ x, double* y) {
   constexpr int C = 32 / T;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= nslices) return;
   const int t = lane % C;
   const int row = rowof[warp * C + t];
   const int steps = sw[warp] / T;
@@ -62,6 +59,33 @@ __global__ void __launch_bounds__(kThreads) k_sell(int nslices, const int64_t* _
   if (kMode == 1) y[row] = sum;
   if (kMode == 2) y[row] = b[row] + sum;
   if (kMode == 3) y[row] = mask[row] ? 0.0 : sum;
+}
+
+template <int kMode, int T>
+__global__ void __launch_bounds__(kThreads) k_sell(int nslices, const int64_t* __restrict__ sptr,
+                                                   const int* __restrict__ sw, const int* __restrict__ col,
+                                                   const double* __restrict__ val, const int* __restrict__ rowof,
+                                                   const double* b, const uint8_t* __restrict__ mask,
+                                                   const double* __restrict__ x, double* y) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (warp >= nslices) return;
+  sell_slice<kMode, T>(warp, threadIdx.x & 31, sptr, sw, col, val, rowof, b, mask, x, y);
+}
+
+// One warp per slice of any member's matrix; the member's own threads-per-row layout.
+template <int kMode>
+__global__ void __launch_bounds__(kThreads) k_group_sell(const __grid_constant__ GroupSpmvArgs a) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= a.prefix[a.count]) return;
+  const int m = group_member(a.prefix, a.count, gw);
+  const Sell& A = a.A[m];
+  const int w = gw - a.prefix[m], lane = threadIdx.x & 31;
+  switch (A.tpr) {
+    case 1: sell_slice<kMode, 1>(w, lane, A.sptr, A.swidth, A.col, A.val, A.rowof, a.b[m], a.mask[m], a.x[m], a.y[m]); break;
+    case 2: sell_slice<kMode, 2>(w, lane, A.sptr, A.swidth, A.col, A.val, A.rowof, a.b[m], a.mask[m], a.x[m], a.y[m]); break;
+    case 4: sell_slice<kMode, 4>(w, lane, A.sptr, A.swidth, A.col, A.val, A.rowof, a.b[m], a.mask[m], a.x[m], a.y[m]); break;
+    default: sell_slice<kMode, 8>(w, lane, A.sptr, A.swidth, A.col, A.val, A.rowof, a.b[m], a.mask[m], a.x[m], a.y[m]); break;
+  }
 }
 
 template <int kMode>
@@ -177,6 +201,18 @@ int axpy(double a, const double* x, double* y, int n, cudaStream_t s) {
 int scale(double a, double* x, int n, cudaStream_t s) {
   if (n <= 0) return 0;
   k_scale<<<blocks_for(n), kThreads, 0, s>>>(a, x, n);
+  return 1;
+}
+
+int group_spmv(int mode, const GroupSpmvArgs& a, cudaStream_t s) {
+  if (a.count == 0 || a.prefix[a.count] == 0) return 0;
+  const int g = blocks_for(int64_t(a.prefix[a.count]) * 32);
+  switch (mode) {
+    case 0: k_group_sell<0><<<g, kThreads, 0, s>>>(a); break;
+    case 1: k_group_sell<1><<<g, kThreads, 0, s>>>(a); break;
+    case 2: k_group_sell<2><<<g, kThreads, 0, s>>>(a); break;
+    default: k_group_sell<3><<<g, kThreads, 0, s>>>(a); break;
+  }
   return 1;
 }
 
