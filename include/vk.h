@@ -339,15 +339,64 @@ int vk_stats_reset(vk_hierarchy* h, int time_kernels);
 /* Reads the counters (waits for the recorded events). */
 int vk_stats_read(vk_hierarchy* h, vk_stats* out);
 
+/* ---- group solve: several independent solves advanced together ------------------------------- *
+ * A group holds up to `max_members` FGMRES solves (vk_solve semantics), each on its own hierarchy,
+ * which may differ in mesh size, number of levels and order k.  vk_group_step advances every active
+ * member by one FGMRES iteration, and every stage of it is ONE launch over all active members: the
+ * V-cycle's residuals, restrictions and prolongations (SELL products of every member's matrices), the
+ * patch solves of Algorithm 1 (uneven patches of every member and order in one launch, each member's
+ * own storage layout), the weighted sums with the Chebyshev update (Sec. 3), the coarsest-level solves,
+ * and the FGMRES projection, Gram-Schmidt, normalisation and Givens kernels.  Levels are matched from
+ * the finest down, so members with fewer levels reach their coarsest solve earlier in the cycle.
+ * Members join (vk_group_add) and leave (when they converge, hit maxit or fail) between steps, so a
+ * serving loop can batch requests continuously.  Each member's arithmetic is exactly that of
+ * vk_solve's host-driven loop (use_graph = 0), in the same order, so its iterations, history and x
+ * do not depend on the other members.  A hierarchy can be in at most one group member at a time and
+ * must not be used by other calls while it is.  All work is queued on the `stream` of each call. */
+typedef struct vk_group vk_group;
+
+int vk_group_create(int max_members, vk_group** out);  /* 1 <= max_members <= 24 */
+/* Adds a solve of A x = b on h's finest level (b_dev, x_dev: device, ndof doubles, caller-owned until
+ * the member finishes); runs its prologue (projection of b, ||b||, first basis vector) and returns
+ * its member id in *member.  A zero right-hand side finishes at once with x = 0. */
+int vk_group_add(vk_group* g, vk_hierarchy* h, const double* b_dev, double* x_dev, double rtol, int maxit,
+                 void* stream, int* member);
+/* One FGMRES iteration of every active member (synchronises the stream once to read the convergence
+ * flags); members that finish get x written.  *active (may be NULL) receives the members still active. */
+int vk_group_step(vk_group* g, void* stream, int* active);
+/* vk_group_add with a host right-hand side (ndof doubles, copied on `stream` into the hierarchy's own
+ * device staging buffer before the call returns); the solution stays in the hierarchy's staging
+ * buffer until vk_group_result copies it out. */
+int vk_group_add_host(vk_group* g, vk_hierarchy* h, const double* b_host, double rtol, int maxit, void* stream,
+                      int* member);
+/* *active = 1 while the member is being solved, 0 once it has finished (result pending). */
+int vk_group_active(const vk_group* g, int member, int* active);
+/* Result of a finished member: fills *info (history only if info->history is not NULL, maxit + 1
+ * doubles), copies its solution to x_host (ndof doubles; may be NULL) and returns the member's status
+ * (VK_OK, VK_ERR_NOT_CONVERGED, VK_ERR_NONFINITE, ...); the member id is free again afterwards.
+ * VK_ERR_ARG if the member is unknown or still active. */
+int vk_group_result(vk_group* g, int member, double* x_host, vk_solve_info* info);
+/* Kernels launched by the group since creation (all members together). */
+int vk_group_launches(const vk_group* g, int64_t* launches);
+void vk_group_destroy(vk_group* g);
+
 /* ---- solve service (continuous batching on one GPU) ------------------------------------------- *
  * A request is one FGMRES solve (vk_solve semantics) of a problem of its own mesh size and order.
- * `slots` worker threads, each with its own CUDA stream, take requests in arrival order as soon as
- * they are free, so the solves of admitted requests overlap on the device.  Hierarchies stay resident
- * between requests (one pool entry serves one slot at a time).  Admission is by device footprint
- * (vk_footprint): when memory_budget would be exceeded, idle hierarchies are destroyed least recently
- * used first, and a request waits while the memory it needs is held by running solves; a request
- * larger than the whole budget fails with VK_ERR_NO_MEMORY.  Results do not depend on the mix: each
- * solve runs the same deterministic kernels on its own hierarchy. */
+ * Requests are taken in arrival order by `slots` threads that find (or build) a resident hierarchy for
+ * each.  Hierarchies stay resident between requests (one pool entry serves one request at a time).
+ * Admission is by device footprint (vk_footprint): when memory_budget would be exceeded, idle
+ * hierarchies are destroyed least recently used first, and a request waits while the memory it needs
+ * is held by running solves; a request larger than the whole budget fails with VK_ERR_NO_MEMORY.
+ *   VK_SERVE_GROUP (default): one engine thread advances every admitted request together as members
+ *     of one group solve (vk_group_*): each FGMRES iteration of all of them is one launch per stage,
+ *     whatever their sizes and orders, and requests join and leave between iterations (continuous
+ *     batching).  At most slots <= 24 requests are in flight.
+ *   VK_SERVE_STREAMS: each slot solves its request alone (vk_solve_host) on its own CUDA stream, so
+ *     the solves overlap on the device but share no launch.
+ * Results do not depend on the mix: in both modes each request runs the same deterministic arithmetic
+ * on its own hierarchy (group members equal vk_solve's host-driven loop bit for bit). */
+#define VK_SERVE_GROUP 0
+#define VK_SERVE_STREAMS 1
 typedef struct vk_server vk_server;
 
 typedef struct vk_server_config {
@@ -357,6 +406,7 @@ typedef struct vk_server_config {
   int32_t device;        /* CUDA device ordinal                                                   */
   size_t memory_budget;  /* device bytes for resident hierarchies; 0 = 60% of free memory         */
   vk_options options;    /* options of every hierarchy the server builds                          */
+  int32_t mode;          /* VK_SERVE_GROUP (default) or VK_SERVE_STREAMS                           */
 } vk_server_config;
 
 typedef struct vk_request {
@@ -383,9 +433,14 @@ typedef struct vk_server_stats {
   int32_t queued;        /* requests waiting for a slot                                           */
   size_t bytes_used;     /* device bytes of resident hierarchies                                  */
   size_t memory_budget;
+  int64_t group_steps;   /* VK_SERVE_GROUP: FGMRES iterations of the group solve (each one launch per
+                            stage over its members)                                              */
+  int64_t member_steps;  /* VK_SERVE_GROUP: member iterations in them (member_steps / group_steps is
+                            the mean number of requests sharing each launch)                      */
 } vk_server_stats;
 
-void vk_default_server_config(vk_server_config* c);   /* 4 slots, 2 per key, device 0, budget 0 */
+void vk_default_server_config(vk_server_config* c);   /* 4 slots, 2 per key, device 0, budget 0,
+                                                         VK_SERVE_GROUP */
 int vk_server_create(const vk_server_config* c, vk_server** out);
 /* Queues a request; *ticket identifies it for vk_server_wait. */
 int vk_server_submit(vk_server* s, const vk_request* r, uint64_t* ticket);

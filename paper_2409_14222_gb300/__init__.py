@@ -4,7 +4,7 @@ Implements the hot path of arXiv 2409.14222 (composite Vanka patches, Chebyshev-
 additive relaxation, V-cycle preconditioned FGMRES) as a C-ABI CUDA library (``libvk.so``, declared in
 ``include/vk.h``) with this thin binding.  Build the library with ``build.build()``.
 """
-from .vk import (Hierarchy, Server, VkError, ndof_of, measure_fma_rate, default_options, footprint, hessenberg_eigenvalues, lib,  # noqa: F401
+from .vk import (Hierarchy, Server, Group, VkError, ndof_of, measure_fma_rate, default_options, footprint, hessenberg_eigenvalues, lib,  # noqa: F401
                  VK_PREC_F32, VK_PREC_F64, VK_PREC_F64E, VK_WEIGHTS_MULTIPLICITY, VK_WEIGHTS_PLAIN, VK_CSR_A, VK_CSR_P, VK_BATCH_NONE, VK_BATCH_BF16, VK_BATCH_FP16,
                  VK_ENGINE_TCGEN05, VK_ENGINE_MMA_SYNC,
                  VK_CSR_R, SYMBOLS)

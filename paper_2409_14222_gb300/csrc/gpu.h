@@ -349,6 +349,7 @@ struct GroupVecArgs {          // per-member vectors for the FGMRES kernels belo
   double* out[kGroupMax] = {};      // member results (H column, t2, scalar, ...)
   double* acc[kGroupMax] = {};
   int off[kGroupMax] = {}, len[kGroupMax] = {};   // pressure block (projection)
+  int prefix[kGroupMax + 1] = {};   // filled by the launchers: elements or vectors of the members
 };
 // partial sums of V[i] . w, i < nvec (grid kReduceBlocks x sum of nvec), then out[i] (+ acc[i])
 int group_multi_dot(const GroupVecArgs& a, cudaStream_t s);

@@ -103,13 +103,12 @@ __global__ void k_gj_unscramble(double* __restrict__ M, int m, const int* __rest
   }
 }
 
-// x[i] = sum_j Minv[i][j] b[j]: one warp per row, lane-strided partial sums, fixed-order tree.
 // x[row] = Minv[row][0:n] . b: one block of 128 threads per row (enough warps per SM for the FP64
 // pipe and the loads), two partial sums per thread, fixed combination order.
-__global__ void __launch_bounds__(128) k_dense_gemv(const double* __restrict__ Minv, int n, int ld,
-                                                    const double* __restrict__ b, double* __restrict__ x) {
+__device__ __forceinline__ void gemv_row(int row, const double* __restrict__ Minv, int n, int ld,
+                                         const double* __restrict__ b, double* __restrict__ x) {
   __shared__ double sh[4];
-  const int row = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31;
   const double* a = Minv + int64_t(row) * ld;
   double s0 = 0.0, s1 = 0.0;
   int j = tid;
@@ -123,6 +122,17 @@ __global__ void __launch_bounds__(128) k_dense_gemv(const double* __restrict__ M
   if (lane == 0) sh[tid >> 5] = s;
   __syncthreads();
   if (tid == 0) x[row] = (sh[0] + sh[1]) + (sh[2] + sh[3]);
+}
+
+__global__ void __launch_bounds__(128) k_dense_gemv(const double* __restrict__ Minv, int n, int ld,
+                                                    const double* __restrict__ b, double* __restrict__ x) {
+  gemv_row(blockIdx.x, Minv, n, ld, b, x);
+}
+
+__global__ void __launch_bounds__(128) k_group_gemv(const __grid_constant__ GroupGemvArgs a) {
+  const int gr = blockIdx.x;
+  const int m = group_member(a.prefix, a.count, gr);
+  gemv_row(gr - a.prefix[m], a.Minv[m], a.n[m], a.ld[m], a.b[m], a.x[m]);
 }
 
 }  // namespace
@@ -146,6 +156,12 @@ int gauss_jordan_inverse(double* M, int m, int* perm, double* fcol, int* piv, in
   }
   k_gj_unscramble<<<(m + 127) / 128, 128, 0, s>>>(M, m, perm);
   return 3 * m + 1;
+}
+
+int group_dense_gemv(const GroupGemvArgs& a, cudaStream_t s) {
+  if (a.count == 0 || a.prefix[a.count] == 0) return 0;
+  k_group_gemv<<<a.prefix[a.count], 128, 0, s>>>(a);
+  return 1;
 }
 
 int dense_gemv(const double* Minv, int n, int ld, const double* b, double* x, cudaStream_t s) {

@@ -291,7 +291,147 @@ __global__ void k_fg_combine(const double* __restrict__ Z, int64_t ldz, const Fg
 
 __global__ void k_fg_finish(FgState* st, const double* __restrict__ sq) { st->true_res = sqrt(*sq); }
 
+// ---- group forms: the same partitions, orders and trees as the single-solve kernels ------------
+// block (b, v) of the grid: member m and basis vector i of the concatenated vector list
+__global__ void __launch_bounds__(kT) k_group_multi_dot(const __grid_constant__ GroupVecArgs a) {
+  const int gv = blockIdx.y;
+  const int m = group_member(a.prefix, a.count, gv), i = gv - a.prefix[m];
+  const double* v = a.V[m] + a.ld[m] * i;
+  const double* w = a.w[m];
+  const int n = a.n[m];
+  double s = 0.0;
+  for (int r = blockIdx.x * kT + threadIdx.x; r < n; r += kReduceBlocks * kT) s = fma(v[r], w[r], s);
+  s = block_sum<kT>(s);
+  if (threadIdx.x == 0) a.partial[m][int64_t(i) * kReduceBlocks + blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kT) k_group_multi_finalize(const __grid_constant__ GroupVecArgs a) {
+  const int gv = blockIdx.x;
+  const int m = group_member(a.prefix, a.count, gv), i = gv - a.prefix[m];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < kReduceBlocks; b += kT) s += a.partial[m][int64_t(i) * kReduceBlocks + b];
+  s = block_sum<kT>(s);
+  if (threadIdx.x == 0) {
+    a.out[m][i] = s;
+    if (a.acc[m]) a.acc[m][i] += s;
+  }
+}
+
+__global__ void k_group_multi_axpy(const __grid_constant__ GroupVecArgs a) {
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= a.prefix[a.count]) return;
+  const int m = group_member(a.prefix, a.count, gi), r = gi - a.prefix[m];
+  const double* V = a.V[m];
+  const double* h = a.out[m];
+  const int64_t ld = a.ld[m];
+  double s = 0.0;
+  for (int i = 0; i < a.nvec[m]; ++i) s = fma(V[ld * i + r], h[i], s);
+  a.w[m][r] -= s;
+}
+
+// mode 0: partial sums of w[off .. off+len) (k_sum_partials); mode 1: of w . w over n (k_dot_partials)
+template <int kMode>
+__global__ void __launch_bounds__(kT) k_group_sum(const __grid_constant__ GroupVecArgs a) {
+  const int m = blockIdx.y;
+  double s = 0.0;
+  if (kMode == 0) {
+    const double* x = a.w[m] + a.off[m];
+    for (int i = blockIdx.x * kT + threadIdx.x; i < a.len[m]; i += kReduceBlocks * kT) s += x[i];
+  } else {
+    const double* x = a.w[m];
+    for (int i = blockIdx.x * kT + threadIdx.x; i < a.n[m]; i += kReduceBlocks * kT) s = fma(x[i], x[i], s);
+  }
+  s = block_sum<kT>(s);
+  if (threadIdx.x == 0) a.partial[a.count > 0 ? m : 0][blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kT) k_group_finalize(const __grid_constant__ GroupVecArgs a) {
+  const int m = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < kReduceBlocks; i += kT) s += a.partial[m][i];
+  s = block_sum<kT>(s);
+  if (threadIdx.x == 0) a.out[m][0] = s;
+}
+
+__global__ void k_group_subtract_mean(const __grid_constant__ GroupVecArgs a) {
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= a.prefix[a.count]) return;
+  const int m = group_member(a.prefix, a.count, gi), i = gi - a.prefix[m];
+  double* x = a.w[m] + a.off[m];
+  x[i] -= *a.out[m] / double(a.len[m]);
+}
+
+__global__ void k_group_normalize(const __grid_constant__ GroupGivensArgs a, const __grid_constant__ GroupVecArgs pre) {
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= pre.prefix[pre.count]) return;
+  const int m = group_member(pre.prefix, pre.count, gi), r = gi - pre.prefix[m];
+  const double nrm = sqrt(*a.wsq[m]);
+  if (r == 0) a.H[m][int64_t(a.j[m]) * a.ldh[m] + a.j[m] + 1] = nrm;
+  a.vnext[m][r] = nrm > 0.0 ? a.w[m][r] / nrm : a.w[m][r];
+}
+
+// one block per member: the rotations of column j (givens_column) and the convergence flags
+__global__ void k_group_givens(const __grid_constant__ GroupGivensArgs a) {
+  const int m = blockIdx.x;
+  const int j = a.j[m];
+  const double est = givens_column(a.H[m], a.ldh[m], a.cs[m], a.sn[m], a.g[m], a.hist[m], j);
+  if (threadIdx.x == 0) {
+    a.flag[m][0] = est <= a.rtol[m] * a.hist[m][0] ? 1 : 0;
+    a.flag[m][1] = isfinite(est) ? 0 : 1;
+  }
+}
+
 }  // namespace
+
+int group_multi_dot(const GroupVecArgs& a0, cudaStream_t s) {
+  if (a0.count == 0) return 0;
+  GroupVecArgs a = a0;
+  a.prefix[0] = 0;
+  for (int m = 0; m < a.count; ++m) a.prefix[m + 1] = a.prefix[m] + a.nvec[m];
+  if (a.prefix[a.count] == 0) return 0;
+  k_group_multi_dot<<<dim3(kReduceBlocks, a.prefix[a.count]), kT, 0, s>>>(a);
+  k_group_multi_finalize<<<a.prefix[a.count], kT, 0, s>>>(a);
+  return 2;
+}
+
+int group_multi_axpy(const GroupVecArgs& a0, cudaStream_t s) {
+  if (a0.count == 0) return 0;
+  GroupVecArgs a = a0;
+  a.prefix[0] = 0;
+  for (int m = 0; m < a.count; ++m) a.prefix[m + 1] = a.prefix[m] + a.n[m];
+  k_group_multi_axpy<<<(a.prefix[a.count] + kT - 1) / kT, kT, 0, s>>>(a);
+  return 1;
+}
+
+int group_pressure_project(const GroupVecArgs& a0, cudaStream_t s) {
+  if (a0.count == 0) return 0;
+  GroupVecArgs a = a0;
+  a.prefix[0] = 0;
+  for (int m = 0; m < a.count; ++m) a.prefix[m + 1] = a.prefix[m] + a.len[m];
+  k_group_sum<0><<<dim3(kReduceBlocks, a.count), kT, 0, s>>>(a);
+  k_group_finalize<<<a.count, kT, 0, s>>>(a);
+  k_group_subtract_mean<<<(a.prefix[a.count] + kT - 1) / kT, kT, 0, s>>>(a);
+  return 3;
+}
+
+int group_norm2(const GroupVecArgs& a, cudaStream_t s) {
+  if (a.count == 0) return 0;
+  k_group_sum<1><<<dim3(kReduceBlocks, a.count), kT, 0, s>>>(a);
+  k_group_finalize<<<a.count, kT, 0, s>>>(a);
+  return 2;
+}
+
+int group_normalize_givens(const GroupGivensArgs& a, cudaStream_t s) {
+  if (a.count == 0) return 0;
+  GroupVecArgs pre;
+  pre.count = a.count;
+  pre.prefix[0] = 0;
+  for (int m = 0; m < a.count; ++m) pre.prefix[m + 1] = pre.prefix[m] + a.n[m];
+  k_group_normalize<<<(pre.prefix[a.count] + kT - 1) / kT, kT, 0, s>>>(a, pre);
+  // shared memory of the largest column: 3 * kmax + 2 doubles
+  k_group_givens<<<a.count, 128, (3 * (a.kmax + 1) + 2) * sizeof(double), s>>>(a);
+  return 2;
+}
 
 int fg_init(const double* sq, FgState* st, double* g, double* hist, int kmax, cudaGraphConditionalHandle cond,
             cudaStream_t s) {

@@ -346,6 +346,7 @@ struct vk_hierarchy {
   double* yb = nullptr;
   int *activeb = nullptr, *itersb = nullptr, *nonfb = nullptr;
   int* tc_err = nullptr;   // set by the tcgen05 patch solves when a bounded wait expires
+  bool in_group = false;   // the FGMRES workspace is used by a vk_group member
   bool expire_once = false;  // vk_options.test_expire_wait, consumed by the first finest sweep
   ~vk_hierarchy() {
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -1847,3 +1848,473 @@ extern "C" int vk_vanka_noalloc(vk_hierarchy* h, int level, const double* r, dou
     return VK_OK;
   });
 }
+
+// ------------------------------------------------------------------------------------------------
+// Group solve (vk_group_*): several independent FGMRES solves advanced together, one launch per stage
+// over every active member.  Each member keeps its FGMRES state in its own hierarchy's workspace and
+// runs exactly the host-driven loop of solve_impl, with every single-member launch replaced by the
+// group launch of the same kernel body.
+namespace {
+
+struct GroupMember {
+  vk_hierarchy* h = nullptr;
+  const double* b = nullptr;
+  double* x = nullptr;
+  double rtol = 0.0, beta = 0.0, true_res = 0.0;
+  int maxit = 0, j = 0, status = VK_OK;
+  bool used = false, active = false, converged = false;
+  std::vector<double> hist;
+  std::chrono::steady_clock::time_point t0;
+};
+
+// one member's level in a group V-cycle, matched from the finest level down
+struct GLevel {
+  vk_hierarchy* h;
+  int l;
+  const double* b;
+  double* x;
+};
+
+vk::gpu::GroupPatch group_patch(const DevLevel& D) {
+  vk::gpu::GroupPatch g;
+  g.work = D.pat.work;
+  g.slot_ptr = D.pat.slot_ptr;
+  g.slot_dofs = D.pat.slot_dofs;
+  g.foff = D.pat.foff;
+  g.factors = D.pat.factors;
+  g.slot_pos = D.pat.slot_pos;
+  g.dof_ptr = D.pat.dof_ptr;
+  g.weight = D.pat.weight;
+  g.dir = D.dir;
+  g.sym = D.pat.sym;
+  g.ndof = D.ndof;
+  return g;
+}
+
+// group SpMV over the members' level matrices: which = 0 (A), 1 (P), 2 (R)
+int64_t group_sell(const std::vector<GLevel>& ms, int which, int mode, const std::vector<const double*>& b,
+                   const std::vector<const uint8_t*>& mask, const std::vector<const double*>& x,
+                   const std::vector<double*>& y, cudaStream_t s) {
+  vk::gpu::GroupSpmvArgs a;
+  a.count = int(ms.size());
+  for (int m = 0; m < a.count; ++m) {
+    const DevLevel& D = ms[m].h->lv[ms[m].l];
+    a.A[m] = which == 0 ? D.A : which == 1 ? D.P : D.R;
+    a.prefix[m + 1] = a.prefix[m] + a.A[m].nslices;
+    a.b[m] = b[m];
+    a.mask[m] = mask[m];
+    a.x[m] = x[m];
+    a.y[m] = y[m];
+  }
+  return vk::gpu::group_spmv(mode, a, s);
+}
+
+// nu Chebyshev steps of every member's level (the arithmetic of smooth())
+int64_t group_smooth(const std::vector<GLevel>& ms, bool zero_init, cudaStream_t s) {
+  int64_t launches = 0;
+  const int cnt = int(ms.size());
+  const vk_options& o = ms[0].h->opt;
+  std::vector<double> theta(cnt), delta(cnt), sigma(cnt), rho(cnt);
+  for (int m = 0; m < cnt; ++m) {
+    const double lam = ms[m].h->lv[ms[m].l].lam;
+    const double emax = o.cheb_hi * lam, emin = o.cheb_lo * lam;
+    theta[m] = 0.5 * (emax + emin);
+    delta[m] = 0.5 * (emax - emin);
+    sigma[m] = theta[m] / delta[m];
+    rho[m] = 1.0 / sigma[m];
+  }
+  for (int step = 0; step < o.sweeps; ++step) {
+    std::vector<const double*> rr(cnt);
+    if (!(step == 0 && zero_init)) {
+      std::vector<const double*> b(cnt), x(cnt), none(cnt, nullptr);
+      std::vector<const uint8_t*> nomask(cnt, nullptr);
+      std::vector<double*> r(cnt);
+      for (int m = 0; m < cnt; ++m) {
+        DevLevel& D = ms[m].h->lv[ms[m].l];
+        b[m] = ms[m].b;
+        x[m] = ms[m].x;
+        r[m] = D.r;
+        rr[m] = D.r;
+      }
+      launches += group_sell(ms, 0, 0, b, nomask, x, r, s);
+    } else {
+      for (int m = 0; m < cnt; ++m) rr[m] = ms[m].b;
+    }
+    vk::gpu::GroupApplyArgs ap;
+    vk::gpu::GroupScatterArgs sc;
+    ap.count = sc.count = cnt;
+    ap.prec = sc.prec = ms[0].h->opt.factor_prec;
+    int mode = 0;
+    for (int m = 0; m < cnt; ++m) {
+      DevLevel& D = ms[m].h->lv[ms[m].l];
+      ap.P[m] = sc.P[m] = group_patch(D);
+      ap.prefix[m + 1] = ap.prefix[m] + D.pat.npatch;
+      ap.dprefix[m + 1] = ap.dprefix[m] + D.ndof;
+      ap.nb_max = std::max(ap.nb_max, D.pat.nb_max);
+      ap.r[m] = rr[m];
+      ap.r2[m] = D.r2;
+      ap.delta[m] = D.delta;
+      sc.prefix[m + 1] = sc.prefix[m] + D.ndof;
+      sc.r[m] = rr[m];
+      sc.delta[m] = D.delta;
+      sc.theta[m] = theta[m];
+      sc.d[m] = D.d;
+      sc.x[m] = ms[m].x;
+      if (step == 0) {
+        mode = zero_init ? 1 : 2;
+      } else {
+        const double rho_new = 1.0 / (2.0 * sigma[m] - rho[m]);
+        sc.c1[m] = rho_new * rho[m];
+        sc.c2[m] = 2.0 * rho_new / delta[m];
+        rho[m] = rho_new;
+        mode = 3;
+      }
+    }
+    sc.mode = mode;
+    launches += vk::gpu::group_patch_apply(ap, s);
+    launches += vk::gpu::group_vanka_scatter(sc, s);
+  }
+  return launches;
+}
+
+// V(nu, nu) cycle of every member from its level ms[m].l down (the arithmetic of vcycle()).
+int64_t group_vcycle(const std::vector<GLevel>& ms, cudaStream_t s) {
+  int64_t launches = 0;
+  std::vector<GLevel> coarse, rest;
+  for (const GLevel& g : ms) (g.l == 0 ? coarse : rest).push_back(g);
+  if (!coarse.empty()) {
+    vk::gpu::GroupGemvArgs a;
+    a.count = int(coarse.size());
+    for (int m = 0; m < a.count; ++m) {
+      vk_hierarchy* h = coarse[m].h;
+      a.Minv[m] = h->Cinv;
+      a.n[m] = h->nc;
+      a.ld[m] = h->nc + 1;
+      a.b[m] = coarse[m].b;
+      a.x[m] = coarse[m].x;
+      a.prefix[m + 1] = a.prefix[m] + h->nc;
+    }
+    launches += vk::gpu::group_dense_gemv(a, s);
+  }
+  if (rest.empty()) return launches;
+  const int cnt = int(rest.size());
+  launches += group_smooth(rest, true, s);
+  std::vector<const double*> b(cnt), x(cnt), r(cnt), cx(cnt);
+  std::vector<double*> rw(cnt), cb(cnt), xw(cnt);
+  std::vector<const uint8_t*> nomask(cnt, nullptr), cdir(cnt);
+  std::vector<GLevel> down(cnt);
+  for (int m = 0; m < cnt; ++m) {
+    DevLevel& D = rest[m].h->lv[rest[m].l];
+    DevLevel& C = rest[m].h->lv[rest[m].l - 1];
+    b[m] = rest[m].b;
+    x[m] = rest[m].x;
+    xw[m] = rest[m].x;
+    rw[m] = D.r;
+    r[m] = D.r;
+    cb[m] = C.b;
+    cx[m] = C.x;
+    cdir[m] = C.dir;
+    down[m] = GLevel{rest[m].h, rest[m].l - 1, C.b, C.x};
+  }
+  launches += group_sell(rest, 0, 0, b, nomask, x, rw, s);         // r = b - A x
+  launches += group_sell(rest, 2, 3, b, cdir, r, cb, s);           // r_c = R r, coarse Dirichlet zeroed
+  launches += group_vcycle(down, s);
+  launches += group_sell(rest, 1, 2, x, nomask, cx, xw, s);        // x += P e_c
+  launches += group_smooth(rest, false, s);
+  return launches;
+}
+
+}  // namespace
+
+struct vk_group {
+  int max_members = 0;
+  std::vector<GroupMember> m;
+  int* dflags = nullptr;      // device: 2 flags per member
+  int* hflags = nullptr;      // pinned host mirror
+  int64_t launches = 0;
+  ~vk_group() {
+    if (dflags) cudaFree(dflags);
+    if (hflags) cudaFreeHost(hflags);
+  }
+};
+
+namespace {
+
+// The tail of solve_impl for one member: x = Z y from the rotated Hessenberg system, true residual.
+void group_finish(vk_group* g, GroupMember& M, cudaStream_t s) {
+  vk_hierarchy* h = M.h;
+  DevLevel& F = h->lv.back();
+  const int n = F.ndof, ldh = h->kmax + 1, m = M.j;
+  std::vector<double> Hh(size_t(ldh) * std::max(m, 1)), gh(m + 1), y(std::max(m, 1));
+  M.hist.assign(m + 1, 0.0);
+  CK(cudaMemcpyAsync(Hh.data(), h->H, size_t(ldh) * m * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(gh.data(), h->g, (m + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(M.hist.data(), h->hist, (m + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int i = m - 1; i >= 0; --i) {
+    double acc = gh[i];
+    for (int k = i + 1; k < m; ++k) acc -= Hh[size_t(k) * ldh + i] * y[k];
+    y[i] = acc / Hh[size_t(i) * ldh + i];
+  }
+  CK(cudaMemcpyAsync(h->yv, y.data(), m * sizeof(double), cudaMemcpyHostToDevice, s));
+  g->launches += vk::gpu::combine(h->Z, h->ldv, m, h->yv, M.x, n, s);
+  g->launches += vk::gpu::copy(F.t, M.b, n, s);
+  g->launches += vk::gpu::pressure_project(F.t, F.n_u, F.n_p, h->partial, h->scal + 1, s);
+  g->launches += vk::gpu::sell_residual(F.A, F.t, M.x, F.r, s);
+  g->launches += 2;
+  M.true_res = std::sqrt(device_dot(h, F.r, F.r, n, s));
+  if (M.status == VK_OK && !M.converged) M.status = VK_ERR_NOT_CONVERGED;
+  M.active = false;
+  h->in_group = false;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vk_group_create(int max_members, vk_group** out) {
+  return guard([&] {
+    if (!out || max_members < 1 || max_members > vk::gpu::kGroupMax) raise(VK_ERR_ARG, "max_members must be in 1..24");
+    *out = nullptr;
+    auto g = std::make_unique<vk_group>();
+    g->max_members = max_members;
+    g->m.resize(max_members);
+    std::lock_guard<std::mutex> lock(g_device_mu);
+    CK(cudaMalloc(&g->dflags, 2 * sizeof(int) * max_members));
+    CK(cudaMallocHost(&g->hflags, 2 * sizeof(int) * max_members));
+    *out = g.release();
+    return VK_OK;
+  });
+}
+
+void vk_group_destroy(vk_group* g) {
+  if (!g) return;
+  std::lock_guard<std::mutex> lock(g_device_mu);
+  cudaDeviceSynchronize();
+  for (GroupMember& M : g->m)
+    if (M.used && M.h) M.h->in_group = false;
+  delete g;
+}
+
+int vk_group_launches(const vk_group* g, int64_t* launches) {
+  return guard([&] {
+    if (!g || !launches) raise(VK_ERR_ARG, "null argument");
+    *launches = g->launches;
+    return VK_OK;
+  });
+}
+
+int vk_group_add(vk_group* g, vk_hierarchy* h, const double* b, double* x, double rtol, int maxit, void* stream,
+                 int* member) {
+  return guard([&] {
+    if (!g || !member) raise(VK_ERR_ARG, "null argument");
+    check_device(h);
+    if (h->in_group) raise(VK_ERR_ARG, "hierarchy is already in a group member");
+    if (!b || !x || b == x) raise(VK_ERR_ARG, "null or aliased vectors");
+    if (maxit < 1 || maxit > h->kmax) raise(VK_ERR_ARG, "maxit must be in 1..max_iterations");
+    if (!(rtol >= 0.0)) raise(VK_ERR_ARG, "rtol must be >= 0");
+    for (const GroupMember& M : g->m)
+      if (M.used && M.h && M.h->opt.factor_prec != h->opt.factor_prec)
+        raise(VK_ERR_ARG, "group members must share factor_prec");
+    int slot = -1;
+    for (int i = 0; i < g->max_members; ++i)
+      if (!g->m[i].used) {
+        slot = i;
+        break;
+      }
+    if (slot < 0) raise(VK_ERR_ARG, "group is full");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    GroupMember M;
+    M.h = h;
+    M.b = b;
+    M.x = x;
+    M.rtol = rtol;
+    M.maxit = maxit;
+    M.used = true;
+    M.t0 = std::chrono::steady_clock::now();
+    // prologue of solve_impl: b_hat = projected b, beta, v_1 = b_hat / beta
+    DevLevel& F = h->lv.back();
+    const int n = F.ndof;
+    g->launches += vk::gpu::copy(h->V, b, n, s);
+    g->launches += vk::gpu::pressure_project(h->V, F.n_u, F.n_p, h->partial, h->scal + 1, s);
+    g->launches += 2;
+    M.beta = std::sqrt(device_dot(h, h->V, h->V, n, s));
+    if (!std::isfinite(M.beta)) raise(VK_ERR_NONFINITE, "right-hand side is not finite");
+    if (M.beta == 0.0) {
+      g->launches += vk::gpu::fill(x, 0.0, n, s);
+      CK(cudaStreamSynchronize(s));
+      M.converged = true;
+      M.hist.assign(1, 0.0);
+      M.true_res = 0.0;
+    } else {
+      g->launches += vk::gpu::scale_copy(h->V, h->scal, h->V, n, s);
+      g->launches += vk::gpu::fill(h->g, 0.0, h->kmax + 1, s);
+      CK(cudaMemcpyAsync(h->g, &M.beta, sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(h->hist, &M.beta, sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(cudaGetLastError());
+      M.active = true;
+      h->in_group = true;
+    }
+    g->m[slot] = std::move(M);
+    *member = slot;
+    return VK_OK;
+  });
+}
+
+int vk_group_step(vk_group* g, void* stream, int* active) {
+  return guard([&] {
+    if (!g) raise(VK_ERR_ARG, "null group");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int> act;
+    for (int i = 0; i < g->max_members; ++i)
+      if (g->m[i].used && g->m[i].active) act.push_back(i);
+    if (!act.empty()) {
+      const int cnt = int(act.size());
+      std::vector<GLevel> fin(cnt);
+      int kmax = 0;
+      for (int c = 0; c < cnt; ++c) {
+        GroupMember& M = g->m[act[c]];
+        vk_hierarchy* h = M.h;
+        fin[c] = GLevel{h, h->prob.nlevels - 1, h->V + h->ldv * M.j, h->Z + h->ldv * M.j};
+        kmax = std::max(kmax, h->kmax);
+        h->n_vcycle++;
+      }
+      g->launches += group_vcycle(fin, s);
+      vk::gpu::GroupVecArgs pv, c1, c2, nw;
+      pv.count = c1.count = c2.count = nw.count = cnt;
+      std::vector<const double*> none(cnt, nullptr), zj(cnt);
+      std::vector<const uint8_t*> nomask(cnt, nullptr);
+      std::vector<double*> w(cnt);
+      for (int c = 0; c < cnt; ++c) {
+        GroupMember& M = g->m[act[c]];
+        vk_hierarchy* h = M.h;
+        DevLevel& F = h->lv.back();
+        const int ldh = h->kmax + 1;
+        double* z = h->Z + h->ldv * M.j;
+        double* wv = h->V + h->ldv * (M.j + 1);
+        double* hcol = h->H + int64_t(M.j) * ldh;
+        zj[c] = z;
+        w[c] = wv;
+        pv.w[c] = z;
+        pv.off[c] = F.n_u;
+        pv.len[c] = F.n_p;
+        pv.partial[c] = h->partial;
+        pv.out[c] = h->scal + 1;
+        for (vk::gpu::GroupVecArgs* a : {&c1, &c2, &nw}) {
+          a->n[c] = F.ndof;
+          a->V[c] = h->V;
+          a->ld[c] = h->ldv;
+          a->nvec[c] = M.j + 1;
+          a->w[c] = wv;
+          a->partial[c] = h->partial;
+        }
+        c1.out[c] = hcol;
+        c2.out[c] = h->t2;
+        c2.acc[c] = hcol;
+        nw.out[c] = h->scal + 2;
+      }
+      g->launches += vk::gpu::group_pressure_project(pv, s);              // project z_j
+      g->launches += group_sell(fin, 0, 1, none, nomask, zj, w, s);        // w = A z_j
+      g->launches += vk::gpu::group_multi_dot(c1, s);                       // classical Gram-Schmidt, twice
+      g->launches += vk::gpu::group_multi_axpy(c1, s);
+      g->launches += vk::gpu::group_multi_dot(c2, s);
+      g->launches += vk::gpu::group_multi_axpy(c2, s);
+      g->launches += vk::gpu::group_norm2(nw, s);
+      vk::gpu::GroupGivensArgs gv;
+      gv.count = cnt;
+      gv.kmax = kmax;
+      for (int c = 0; c < cnt; ++c) {
+        GroupMember& M = g->m[act[c]];
+        vk_hierarchy* h = M.h;
+        gv.H[c] = h->H;
+        gv.ldh[c] = h->kmax + 1;
+        gv.cs[c] = h->cs;
+        gv.sn[c] = h->sn;
+        gv.g[c] = h->g;
+        gv.hist[c] = h->hist;
+        gv.j[c] = M.j;
+        gv.rtol[c] = M.rtol;
+        gv.flag[c] = g->dflags + 2 * act[c];
+        gv.wsq[c] = h->scal + 2;
+        gv.w[c] = w[c];
+        gv.vnext[c] = w[c];
+        gv.n[c] = h->lv.back().ndof;
+      }
+      g->launches += vk::gpu::group_normalize_givens(gv, s);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(g->hflags, g->dflags, 2 * sizeof(int) * g->max_members, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int c = 0; c < cnt; ++c) {
+        GroupMember& M = g->m[act[c]];
+        M.j += 1;
+        const int* f = g->hflags + 2 * act[c];
+        if (f[1]) {
+          M.status = VK_ERR_NONFINITE;
+        } else if (f[0]) {
+          M.converged = true;
+        } else if (M.j < M.maxit) {
+          continue;
+        }
+        group_finish(g, M, s);
+      }
+    }
+    if (active) {
+      int a = 0;
+      for (const GroupMember& M : g->m) a += (M.used && M.active) ? 1 : 0;
+      *active = a;
+    }
+    return VK_OK;
+  });
+}
+
+int vk_group_add_host(vk_group* g, vk_hierarchy* h, const double* b_host, double rtol, int maxit, void* stream,
+                      int* member) {
+  return guard([&] {
+    check_device(h);
+    if (!b_host) raise(VK_ERR_ARG, "null right-hand side");
+    if (h->in_group) raise(VK_ERR_ARG, "hierarchy is already in a group member");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n = h->lv.back().ndof;
+    CK(cudaMemcpyAsync(h->bh, b_host, size_t(n) * sizeof(double), cudaMemcpyHostToDevice, s));
+    const int rc = vk_group_add(g, h, h->bh, h->xh, rtol, maxit, stream, member);
+    if (rc != VK_OK) raise(rc, vk_last_error());
+    return VK_OK;
+  });
+}
+
+int vk_group_active(const vk_group* g, int member, int* active) {
+  return guard([&] {
+    if (!g || !active || member < 0 || member >= g->max_members || !g->m[member].used) raise(VK_ERR_ARG, "bad member");
+    *active = g->m[member].active ? 1 : 0;
+    return VK_OK;
+  });
+}
+
+int vk_group_result(vk_group* g, int member, double* x_host, vk_solve_info* info) {
+  return guard([&] {
+    if (!g || member < 0 || member >= g->max_members) raise(VK_ERR_ARG, "bad member");
+    GroupMember& M = g->m[member];
+    if (!M.used || M.active) raise(VK_ERR_ARG, "member is not finished");
+    if (x_host) {
+      const int n = M.h->lv.back().ndof;
+      CK(cudaMemcpy(x_host, M.x, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    if (info) {
+      info->iterations = M.j;
+      info->converged = M.converged ? 1 : 0;
+      info->res0 = M.beta;
+      info->res_est = M.hist.empty() ? 0.0 : M.hist.back();
+      info->true_res = M.true_res;
+      if (info->history)
+        for (size_t i = 0; i < M.hist.size(); ++i) info->history[i] = M.hist[i];
+      info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - M.t0).count();
+    }
+    const int st = M.status;
+    if (st == VK_ERR_NONFINITE) g_err = "FGMRES residual estimate is not finite";
+    if (st == VK_ERR_NOT_CONVERGED) g_err = "FGMRES did not reach rtol in maxit iterations";
+    M = GroupMember{};
+    return st;
+  });
+}
+
+}  // extern "C"

@@ -1,14 +1,16 @@
 // Solve service on one GPU (include/vk.h, vk_server_*): a FIFO of Stokes solve requests of mixed mesh
-// size and order, served by `slots` worker threads that each own a CUDA stream, so solves that are
-// admitted together run concurrently on the device (continuous batching: a request is admitted as
-// soon as a slot and enough device memory are free).  Hierarchies are kept resident between requests
+// size and order.  `slots` worker threads find or build each request's hierarchy; then either one
+// engine thread advances all admitted requests together as members of one group solve (VK_SERVE_GROUP:
+// one launch per stage of every FGMRES iteration over all of them, requests joining and leaving between
+// iterations), or each worker solves its request alone on its own CUDA stream (VK_SERVE_STREAMS).  Hierarchies are kept resident between requests
 // in a pool keyed by the whole problem (N_coarse, nlevels, k and the bits of the viscosity nu, which
 // enters the matrix); a pool entry is used by one slot at a time.  Admission is
 // by device footprint (vk_footprint): when the budget would be exceeded, idle hierarchies are evicted
 // least-recently-used first; a request waits while the memory it needs is held by busy solves.
 //
-// Built only on the public C ABI (vk_setup / vk_solve / vk_footprint / vk_destroy): every solve runs
-// the same kernels as a direct vk_solve, so a result does not depend on what else is being served.
+// Built only on the public C ABI (vk_setup / vk_solve_host / vk_group_* / vk_footprint / vk_destroy):
+// every request runs the same deterministic arithmetic on its own hierarchy, so a result does not
+// depend on what else is being served.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -69,11 +71,23 @@ struct Done {
 
 }  // namespace
 
+// A request whose hierarchy is ready, waiting to join the group solve (VK_SERVE_GROUP).
+struct Ready {
+  Job job;
+  Instance* inst = nullptr;
+  double setup_ms = 0.0;
+  Clock::time_point t_start;
+};
+
 struct vk_server {
   vk_server_config cfg{};
   std::mutex mu;
   std::condition_variable cv_work;   // workers: new job or freed memory
   std::condition_variable cv_done;   // waiters: a result arrived
+  std::condition_variable cv_engine; // group engine: a request became ready, or stop
+  std::deque<Ready> ready;           // VK_SERVE_GROUP: requests with a hierarchy, not yet members
+  int inflight = 0;                  // VK_SERVE_GROUP: requests taken by workers and not finished
+  std::thread engine;
   std::deque<Job> queue;
   std::map<Key, std::vector<std::unique_ptr<Instance>>> pool;
   std::map<uint64_t, Done> done;
@@ -173,18 +187,34 @@ Instance* acquire(vk_server* s, std::unique_lock<std::mutex>& lk, const vk_probl
   return raw;
 }
 
+// Records a finished request (called with s->mu held).
+void complete(vk_server* s, uint64_t ticket, Done&& out) {
+  s->st.completed++;
+  if (out.res.status != VK_OK && out.res.status != VK_ERR_NOT_CONVERGED) s->st.failed++;
+  s->done[ticket] = std::move(out);
+  s->cv_done.notify_all();
+}
+
+// Builder / solver threads.  Each takes the next request, finds or builds its hierarchy (acquire),
+// then either solves it alone on its own stream (VK_SERVE_STREAMS) or hands it to the group engine
+// (VK_SERVE_GROUP, at most `slots` requests in flight).
 void worker(vk_server* s, int id) {
   cudaSetDevice(s->cfg.device);
   cudaStream_t stream = nullptr;
   const bool stream_ok = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess;
+  const bool group = s->cfg.mode == VK_SERVE_GROUP;
   // host staging is pageable: pinned allocations or frees at run time would synchronise the device
   std::vector<double> hx;
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
-    s->cv_work.wait(lk, [&] { return s->stopping || !s->queue.empty(); });
+    s->cv_work.wait(lk, [&] {
+      return s->stopping || (!s->queue.empty() && (!group || s->inflight < s->cfg.slots));
+    });
     if (s->stopping && s->queue.empty()) break;
+    if (s->queue.empty() || (group && s->inflight >= s->cfg.slots)) continue;
     Job job = std::move(s->queue.front());
     s->queue.pop_front();
+    if (group) s->inflight++;
     const auto t_start = Clock::now();
     double setup_ms = 0.0;
     int status = VK_OK;
@@ -198,6 +228,16 @@ void worker(vk_server* s, int id) {
         break;
       }
       s->cv_work.wait(lk);  // memory held by busy solves: wait for a release
+    }
+    if (inst && group) {
+      Ready r;
+      r.job = std::move(job);
+      r.inst = inst;
+      r.setup_ms = setup_ms;
+      r.t_start = t_start;
+      s->ready.push_back(std::move(r));
+      s->cv_engine.notify_one();
+      continue;
     }
     Done out;
     out.res.queue_ms = ms_since(job.submitted, t_start);
@@ -221,12 +261,107 @@ void worker(vk_server* s, int id) {
     }
     out.res.status = status;
     out.res.latency_ms = ms_since(job.submitted, Clock::now());
-    s->st.completed++;
-    if (status != VK_OK && status != VK_ERR_NOT_CONVERGED) s->st.failed++;
-    s->done[job.ticket] = std::move(out);
-    s->cv_done.notify_all();
+    if (group) {
+      s->inflight--;
+      s->cv_work.notify_all();
+      s->cv_engine.notify_all();
+    }
+    complete(s, job.ticket, std::move(out));
   }
   lk.unlock();
+  if (stream_ok) cudaStreamDestroy(stream);
+}
+
+// VK_SERVE_GROUP engine: admits ready requests as members of one group solve between iterations,
+// advances all members by one FGMRES iteration per step (one launch per stage), and retires the
+// members that finish.
+void engine(vk_server* s) {
+  cudaSetDevice(s->cfg.device);
+  cudaStream_t stream = nullptr;
+  const bool stream_ok = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess;
+  const int maxm = std::min(s->cfg.slots, 24);
+  vk_group* g = nullptr;
+  const bool group_ok = stream_ok && vk_group_create(maxm, &g) == VK_OK;
+  struct Active {
+    Job job;
+    Instance* inst;
+    double setup_ms, queue_ms;
+    Clock::time_point t_admit;
+  };
+  std::map<int, Active> act;
+  auto finish = [&](Active& a, int status, Done&& out) {
+    out.res.status = status;
+    out.res.setup_ms = a.setup_ms;
+    out.res.queue_ms = a.queue_ms;
+    out.res.solve_ms = ms_since(a.t_admit, Clock::now());
+    out.res.latency_ms = ms_since(a.job.submitted, Clock::now());
+    std::lock_guard<std::mutex> lk(s->mu);
+    a.inst->busy = false;
+    a.inst->last_used = Clock::now();
+    s->inflight--;
+    s->cv_work.notify_all();
+    complete(s, a.job.ticket, std::move(out));
+  };
+  while (true) {
+    std::vector<Ready> adm;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_engine.wait(lk, [&] {
+        return !act.empty() || !s->ready.empty() || (s->stopping && s->inflight == 0 && s->queue.empty());
+      });
+      if (act.empty() && s->ready.empty() && s->stopping && s->inflight == 0 && s->queue.empty()) break;
+      while (!s->ready.empty() && int(act.size() + adm.size()) < maxm) {
+        adm.push_back(std::move(s->ready.front()));
+        s->ready.pop_front();
+      }
+    }
+    for (Ready& r : adm) {
+      Active a{std::move(r.job), r.inst, r.setup_ms, 0.0, Clock::now()};
+      a.queue_ms = ms_since(a.job.submitted, a.t_admit);   // submission -> joining the group
+      int mid = -1;
+      const int rc = group_ok ? vk_group_add_host(g, a.inst->h, a.job.b.data(), a.job.rtol, a.job.maxit, stream, &mid)
+                              : VK_ERR_CUDA;
+      if (rc != VK_OK) {
+        finish(a, rc, Done{});
+        continue;
+      }
+      act.emplace(mid, std::move(a));
+    }
+    if (act.empty()) continue;
+    int nact = 0;
+    const int rc = vk_group_step(g, stream, &nact);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->st.group_steps++;
+      s->st.member_steps += int64_t(act.size());
+    }
+    std::vector<int> gone;
+    for (auto& kv : act) {
+      int still = 1;
+      if (rc == VK_OK && vk_group_active(g, kv.first, &still) == VK_OK && still) continue;
+      Done out;
+      vk_solve_info info{};
+      int st = rc;
+      if (rc == VK_OK) {
+        out.x.assign(kv.second.job.b.size(), 0.0);
+        st = vk_group_result(g, kv.first, out.x.data(), &info);
+        out.res.iterations = info.iterations;
+        out.res.converged = info.converged;
+        out.res.res0 = info.res0;
+        out.res.true_res = info.true_res;
+      }
+      finish(kv.second, st, std::move(out));
+      gone.push_back(kv.first);
+    }
+    for (int m : gone) act.erase(m);
+    if (rc != VK_OK && group_ok) {
+      // a failed step leaves the group's members in an unknown state: start a fresh group
+      vk_group_destroy(g);
+      g = nullptr;
+      if (vk_group_create(maxm, &g) != VK_OK) g = nullptr;
+    }
+  }
+  if (g) vk_group_destroy(g);
   if (stream_ok) cudaStreamDestroy(stream);
 }
 
@@ -241,12 +376,14 @@ void vk_default_server_config(vk_server_config* c) {
   c->max_per_key = 2;
   c->memory_budget = 0;
   c->device = 0;
+  c->mode = VK_SERVE_GROUP;
   vk_default_options(&c->options);
 }
 
 int vk_server_create(const vk_server_config* cfg, vk_server** out) {
   g_srv_err.clear();
-  if (!cfg || !out || cfg->slots < 1 || cfg->slots > 64) {
+  if (!cfg || !out || cfg->slots < 1 || cfg->slots > 64 || (cfg->mode != VK_SERVE_GROUP && cfg->mode != VK_SERVE_STREAMS) ||
+      (cfg->mode == VK_SERVE_GROUP && cfg->slots > 24)) {
     g_srv_err = "bad server configuration";
     return VK_ERR_ARG;
   }
@@ -271,6 +408,7 @@ int vk_server_create(const vk_server_config* cfg, vk_server** out) {
   }
   vk_server* raw = s.get();
   for (int i = 0; i < cfg->slots; ++i) raw->workers.emplace_back(worker, raw, i);
+  if (raw->cfg.mode == VK_SERVE_GROUP) raw->engine = std::thread(engine, raw);
   *out = s.release();
   return VK_OK;
 }
@@ -363,6 +501,11 @@ void vk_server_destroy(vk_server* s) {
   }
   s->cv_work.notify_all();
   for (auto& t : s->workers) t.join();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->cv_engine.notify_all();
+  }
+  if (s->engine.joinable()) s->engine.join();
   for (auto& kv : s->pool)
     for (auto& inst : kv.second)
       if (inst->h) vk_destroy(inst->h);

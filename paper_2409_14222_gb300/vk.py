@@ -22,6 +22,7 @@ VK_ERR_CUDA = 7
 VK_ERR_INTERNAL = 8
 VK_ERR_CANCELLED = 9
 VK_BC_DIRICHLET_ALL = 0
+VK_SERVE_GROUP, VK_SERVE_STREAMS = 0, 1
 
 VK_WEIGHTS_PLAIN = 0
 VK_WEIGHTS_MULTIPLICITY = 1
@@ -44,6 +45,8 @@ SYMBOLS = [
     "vk_export_patches", "vk_export_dirichlet", "vk_hessenberg_eigenvalues", "vk_stats_reset", "vk_stats_read",
     "vk_vanka_noalloc", "vk_solve_batch", "vk_apply_schedule", "vk_ndof", "vk_export_dof_coords", "vk_default_server_config", "vk_server_create", "vk_server_submit", "vk_server_wait",
     "vk_server_get_stats", "vk_server_destroy", "vk_check_problem", "vk_server_cancel", "vk_measure_fma_rate",
+    "vk_group_create", "vk_group_add", "vk_group_step", "vk_group_result", "vk_group_launches", "vk_group_destroy",
+    "vk_group_add_host", "vk_group_active",
 ]
 
 
@@ -98,7 +101,7 @@ class vk_stats(ctypes.Structure):
 
 class vk_server_config(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("max_per_key", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("memory_budget", ctypes.c_size_t), ("options", vk_options)]
+                ("memory_budget", ctypes.c_size_t), ("options", vk_options), ("mode", ctypes.c_int32)]
 
 
 class vk_request(ctypes.Structure):
@@ -115,7 +118,8 @@ class vk_result(ctypes.Structure):
 class vk_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("builds", ctypes.c_int64), ("evictions", ctypes.c_int64), ("resident", ctypes.c_int32),
-                ("queued", ctypes.c_int32), ("bytes_used", ctypes.c_size_t), ("memory_budget", ctypes.c_size_t)]
+                ("queued", ctypes.c_int32), ("bytes_used", ctypes.c_size_t), ("memory_budget", ctypes.c_size_t),
+                ("group_steps", ctypes.c_int64), ("member_steps", ctypes.c_int64)]
 
 
 _lib = None
@@ -167,6 +171,14 @@ def lib():
             "vk_server_cancel": (I, [VP, ctypes.c_uint64]),
             "vk_check_problem": (I, [P(vk_problem), P(vk_options)]),
             "vk_measure_fma_rate": (I, [I, VP, P(D)]),
+            "vk_group_create": (I, [I, P(VP)]),
+            "vk_group_add": (I, [VP, H, VP, VP, D, I, VP, P(I)]),
+            "vk_group_step": (I, [VP, VP, P(I)]),
+            "vk_group_result": (I, [VP, I, VP, P(vk_solve_info)]),
+            "vk_group_add_host": (I, [VP, H, VP, D, I, VP, P(I)]),
+            "vk_group_active": (I, [VP, I, P(I)]),
+            "vk_group_launches": (I, [VP, P(I64)]),
+            "vk_group_destroy": (None, [VP]),
             "vk_stats_read": (I, [H, P(vk_stats)]),
             "vk_apply_schedule": (I, [H, I, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32),
                                       P(ctypes.c_int32), VP, P(ctypes.c_int32)]),
@@ -428,6 +440,61 @@ class Hierarchy:
         return out
 
 
+class Group:
+    """Several independent solves advanced together, one launch per stage over all members (vk_group_*)."""
+
+    def __init__(self, max_members=8):
+        self.handle = ctypes.c_void_p()
+        check(lib().vk_group_create(int(max_members), ctypes.byref(self.handle)))
+        self._keep = {}
+
+    def add(self, hier, b, x, rtol=1e-8, maxit=100, stream=None):
+        """Adds a solve of hier's finest system (b, x: contiguous FP64 device tensors); returns its member id."""
+        m = ctypes.c_int()
+        check(lib().vk_group_add(self.handle, hier.handle, _ptr(b), _ptr(x), float(rtol), int(maxit),
+                                 _stream_handle(stream), ctypes.byref(m)))
+        self._keep[m.value] = (hier, b, x, maxit)
+        return m.value
+
+    def step(self, stream=None):
+        """One FGMRES iteration of every active member; returns the number still active."""
+        a = ctypes.c_int()
+        check(lib().vk_group_step(self.handle, _stream_handle(stream), ctypes.byref(a)))
+        return a.value
+
+    def run(self, stream=None):
+        while self.step(stream) > 0:
+            pass
+
+    def result(self, member):
+        import numpy as np
+        maxit = self._keep[member][3]
+        info = vk_solve_info()
+        hist = np.zeros(maxit + 1)
+        info.history = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        code = lib().vk_group_result(self.handle, int(member), None, ctypes.byref(info))
+        if code not in (VK_OK, VK_ERR_NOT_CONVERGED):
+            check(code)
+        del self._keep[member]
+        return Hierarchy._result(info, hist, code)
+
+    def launches(self):
+        v = ctypes.c_int64()
+        check(lib().vk_group_launches(self.handle, ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().vk_group_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def footprint(N_coarse, nlevels, k, nu=1.0, options=None):
     p = make_problem(N_coarse, nlevels, k, nu)
     o = options if options is not None else default_options()
@@ -461,10 +528,11 @@ def ndof_of(N_coarse, nlevels, k):
 class Server:
     """The solve service of include/vk.h (vk_server_*): submit host right-hand sides, wait for results."""
 
-    def __init__(self, slots=4, memory_budget=0, device=0, options=None, max_per_key=None):
+    def __init__(self, slots=4, memory_budget=0, device=0, options=None, max_per_key=None, mode=VK_SERVE_GROUP):
         c = vk_server_config()
         lib().vk_default_server_config(ctypes.byref(c))
         c.slots = slots
+        c.mode = mode
         if max_per_key is not None:
             c.max_per_key = max_per_key
         c.memory_budget = int(memory_budget)

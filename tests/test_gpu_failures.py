@@ -128,7 +128,7 @@ def test_server_keys_hierarchies_by_viscosity(vk):
     finally:
         srv.close()
     for nu, x in ((1.0, xa), (0.25, xb)):
-        G = vk.Hierarchy(*key, nu=nu)
+        G = vk.Hierarchy(*key, nu=nu, options=vk.default_options(use_graph=0))   # the group mode's loop
         xd = torch.zeros(n, dtype=torch.float64, device="cuda")
         G.solve(torch.from_numpy(b).cuda(), xd, rtol=1e-10)
         torch.cuda.synchronize()
