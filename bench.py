@@ -555,6 +555,12 @@ def run_vk(args, config, cfg):
         torch.cuda.empty_cache()
         nested["batch16"] = batch_record(vk, torch, si, cfg, args, flush, hbm, peaks, peak_kind, G64=main["G"],
                                          fp64_value=main["value"])
+        main["G"] = None
+        torch.cuda.empty_cache()
+        if not args.no_serving:
+            srv = serving_record(vk, si, args, args.serve_requests, (1.0,), 8, per_key=1)
+            srv["workload"] = CONFIGS["cfg5"][5]
+            nested["serving"] = srv
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline else oracle_cpu_baseline(config, cfg)
@@ -681,15 +687,12 @@ def serve_pass(vk, srv, reqs, arrivals):
             "mean_iterations": float(np.mean(iters))}
 
 
-def run_serving(args):
-    """cfg5: continuous batching of a Poisson request stream (vk_server, C++ runtime)."""
-    import torch
-    from __graft_entry__ import build
-    build()
-    import paper_2409_14222_gb300 as vk
-    import synthetic_inputs as si
-    torch.cuda.set_device(0)
-    mix = si.request_mix(args.requests, seed=42)
+def serving_record(vk, si, args, n_req, rate_mults, slots, per_key=2, baseline=True, clk=None):
+    """The request stream of the serving workload through vk_server in its two modes on the same arrival
+    traces: the group engine (every admitted request shares each FGMRES iteration's launches) and one
+    CUDA stream per slot; plus plain FP64 one at a time (one slot).  Arrival rates are multiples of the
+    group mode's measured capacity; every hierarchy is resident before the timed passes."""
+    mix = si.request_mix(n_req, seed=42)
     keys = lambda N, k: (8, int(np.log2(N // 8)) + 1, k)
     reqs = [(keys(N, k), seed) for N, k, seed in mix]
     uniq = sorted(set(k for k, _ in reqs))
@@ -699,57 +702,77 @@ def run_serving(args):
     elif args.prec == "f64e":
         opts.factor_prec = vk.VK_PREC_F64E
 
-    def warm(srv, per_key):
-        # every hierarchy resident (per_key instances of each key) before any timed request
+    def warm(srv, n):
+        # every hierarchy resident (n instances of each key) before any timed request
         for key in uniq:
-            ts = [srv.submit(*key, si.rhs_normal(vk.ndof_of(*key), 7), rtol=1e-8) for _ in range(per_key)]
+            ts = [srv.submit(*key, si.rhs_normal(vk.ndof_of(*key), 7), rtol=1e-8) for _ in range(n)]
             for t in ts:
                 _, res = srv.wait(t)
                 if res["status"] not in (0, 5):
                     raise RuntimeError(f"warm-up solve of {key} failed: {res}")
 
-    out_rates = {}
-    per_key = min(args.slots, 2)
-    srv = vk.Server(slots=args.slots, options=opts, max_per_key=per_key)
-    t0 = time.perf_counter()
-    warm(srv, per_key)
-    warm_s = time.perf_counter() - t0
-    ncap = min(len(reqs), 300)
-    cap = serve_pass(vk, srv, reqs[:ncap], [0.0] * ncap)
-    capacity = cap["solves_per_s"]
-    with ClockSampler(0) as clk:
-        for mult in (0.5, 1.0, 2.0):
-            n = len(reqs) if mult == 1.0 else min(len(reqs), 300)
-            arr = si.poisson_arrivals(n, mult * capacity, seed=42 + int(10 * mult))
-            out_rates[f"{mult}x"] = serve_pass(vk, srv, reqs[:n], arr)
-    st = srv.stats()
-    srv.close()
-    # plain FP64, one request at a time, same stream at the measured 1x rate
-    base = {}
-    if not args.no_baseline:
-        srv1 = vk.Server(slots=1, options=vk.default_options())
-        warm(srv1, 1)
-        n1 = min(len(reqs), 300)
-        base_cap = serve_pass(vk, srv1, reqs[:n1], [0.0] * n1)
-        base_rate = serve_pass(vk, srv1, reqs[:n1], si.poisson_arrivals(n1, capacity, seed=52))
-        base = {"capacity_solves_per_s": base_cap["solves_per_s"], "at_1x_rate": base_rate}
-        srv1.close()
-    one = out_rates["1.0x"]
+    out = {"requests": len(reqs), "distinct_hierarchies": len(uniq), "slots": slots,
+           "rhs": "N(0,1) per request, rtol 1e-8", "arrivals": "Poisson, seed 42 + 10 x rate multiple"}
+    capacity = None
+    passes = [("group", vk.vk.VK_SERVE_GROUP, slots, per_key), ("streams", vk.vk.VK_SERVE_STREAMS, slots, per_key)]
+    if baseline:
+        passes.append(("one_at_a_time_plain_fp64", vk.vk.VK_SERVE_STREAMS, 1, 1))
+    for name, mode, sl, pk in passes:
+        o = vk.default_options() if name.startswith("one_at") else opts
+        srv = vk.Server(slots=sl, options=o, max_per_key=pk, mode=mode)
+        t0 = time.perf_counter()
+        warm(srv, pk)
+        warm_s = time.perf_counter() - t0
+        st0 = srv.stats()
+        cap = serve_pass(vk, srv, reqs, [0.0] * len(reqs))
+        if capacity is None:
+            capacity = cap["solves_per_s"]
+        rates = {}
+        if clk is not None and name == "group":
+            clk.__enter__()
+        for mult in rate_mults:
+            arr = si.poisson_arrivals(len(reqs), mult * capacity, seed=42 + int(10 * mult))
+            rates[f"{mult}x"] = serve_pass(vk, srv, reqs, arr)
+        if clk is not None and name == "group":
+            clk.__exit__(None, None, None)
+        st = srv.stats()
+        srv.close()
+        rec = {"capacity_solves_per_s": cap["solves_per_s"], "capacity_pass": cap, "rates": rates,
+               "warm_s": warm_s, "builds": st["builds"]}
+        if mode == vk.vk.VK_SERVE_GROUP:
+            steps = st["group_steps"] - st0["group_steps"]
+            rec["requests_per_launch_mean"] = (st["member_steps"] - st0["member_steps"]) / max(steps, 1)
+        out[name] = rec
+    out["capacity_solves_per_s"] = capacity
+    return out
+
+
+def run_serving(args):
+    """cfg5: continuous batching of a Poisson request stream (vk_server, C++ runtime)."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    import paper_2409_14222_gb300 as vk
+    import synthetic_inputs as si
+    torch.cuda.set_device(0)
+    clk = ClockSampler(0)
+    rec = serving_record(vk, si, args, args.requests, (0.5, 1.0, 2.0), args.slots, baseline=not args.no_baseline,
+                         clk=clk)
+    g = rec["group"]
+    one = g["rates"]["1.0x"]
     print(json.dumps({
-        "metric": METRIC, "value": capacity, "unit": "solves/s", "n_gpus": 1, "steps": len(reqs),
-        "warmup": len(uniq) * per_key, "ms_per_step": 1e3 / capacity, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": rec["capacity_solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+        "steps": rec["requests"], "warmup": rec["distinct_hierarchies"] * 2,
+        "ms_per_step": 1e3 / rec["capacity_solves_per_s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
         "dtype": {"f64": "f64", "f64e": "f64 vectors; FP32-pair patch inverses", "f32": "f64 vectors, f32 patch inverses"}[args.prec],
         "data": "synthetic",
-        "config": {"workload": CONFIGS["cfg5"][5], "requests": len(reqs), "slots": args.slots,
-                   "distinct_hierarchies": len(uniq), "factor_prec": args.prec, "arrivals": "Poisson, seed 42",
-                   "warm_s": warm_s},
+        "config": {"workload": CONFIGS["cfg5"][5], "requests": rec["requests"], "slots": args.slots,
+                   "distinct_hierarchies": rec["distinct_hierarchies"], "factor_prec": args.prec,
+                   "server_mode": "group (one launch per stage over all admitted requests)"},
         "latency_ms": {"p50": one["p50_ms"], "p99": one["p99_ms"]},
-        "rates": out_rates, "capacity": cap, "one_at_a_time_plain_fp64": base,
-        "server": st, "clocks": clk.summary(),
+        "serving": rec, "clocks": clk.summary(),
     }), flush=True)
-
-
 
 
 def main():
@@ -764,7 +787,9 @@ def main():
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven FGMRES loop instead of the whole-solve CUDA graph (for kernel profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-nested", action="store_true", help="cfg4: skip the nested cfg2 and 16-RHS records")
+    ap.add_argument("--no-nested", action="store_true", help="cfg4: skip the nested records")
+    ap.add_argument("--no-serving", action="store_true", help="cfg4: skip the nested serving record")
+    ap.add_argument("--serve-requests", type=int, default=100, help="cfg4: requests of the nested serving record")
     ap.add_argument("--requests", type=int, default=1000, help="cfg5: requests in the 1x stream")
     ap.add_argument("--slots", type=int, default=4, help="cfg5: concurrent solves")
     ap.add_argument("--no-baseline", action="store_true", help="cfg5: skip the one-at-a-time FP64 pass")

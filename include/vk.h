@@ -64,6 +64,9 @@ extern "C" {
 #define VK_ENGINE_TCGEN05 0   /* vk_solve_batch patch solves: tcgen05.mma, TMEM accumulators, TMA loads   */
 #define VK_ENGINE_MMA_SYNC 1  /* the same contraction with warp-level mma.sync m16n8k16 (for comparison) */
 
+#define VK_ASSEMBLY_MATRIX_FULL 0  /* patch matrices gathered from the assembled CSR matrix (ASMPatchPC, Sec. 3.1) */
+#define VK_ASSEMBLY_MATRIX_FREE 1  /* patch matrices assembled from element matrices per patch (PCPATCH, Sec. 3.1) */
+
 #define VK_CSR_A 0  /* level matrix script-A_l with Dirichlet identity rows and zeroed columns      */
 #define VK_CSR_P 1  /* prolongation from level l-1 to level l (ndof_l x ndof_{l-1})                 */
 #define VK_CSR_R 2  /* restriction R = P^T (ndof_{l-1} x ndof_l)                                     */
@@ -128,6 +131,14 @@ typedef struct vk_options {
                              last DoF of that (canonical) finest-level patch, so its patch matrix is
                              singular and vk_setup returns VK_ERR_SINGULAR naming that patch; -1
                              (default) in normal use                                                */
+  int32_t patch_assembly;  /* VK_ASSEMBLY_*: how the patch matrices are formed before they are factored.
+                             MATRIX_FULL (default) extracts them from the global CSR matrix by the
+                             patches' DoF lists; MATRIX_FREE assembles each one from the element
+                             matrices of every cell containing one of its DoFs (redundant work on
+                             overlapping patches, as the paper notes for PCPATCH).  Both sum each entry
+                             over the same cells in the same order, so the patch matrices, inverses
+                             and solves are bit-identical; only the setup cost differs
+                             (vk_stats.setup_factor_ms)                                             */
 } vk_options;
 
 /* Device memory provider.  alloc returns device memory of at least `bytes` (256-byte aligned) or
@@ -329,6 +340,9 @@ typedef struct vk_stats {
                               12*nnz (value, column) + 28*ndof (row index, b, x, r)                 */
   double batch_spmv_bytes; /* the same for the 16-right-hand-side FP32 residual of vk_solve_batch:
                               8*nnz + 4*ndof (row pointer) + 192*ndof (16 x b, x, r)               */
+  double setup_factor_ms;  /* setup: summed CUDA-event time of the patch-matrix formation and
+                              factorisation launches of every smoothed level (not reset)            */
+  double setup_ms;         /* setup: host wall time of vk_setup (not reset)                         */
 } vk_stats;
 
 /* Zeroes the counters; time_kernels = 1 also brackets every finest-level patch-apply launch and

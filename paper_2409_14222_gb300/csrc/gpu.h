@@ -91,8 +91,21 @@ int divide(double a, double* x, int n, cudaStream_t s);                  // x /=
 // Gather every patch matrix from the CSR matrix, invert it by Gauss-Jordan with partial pivoting,
 // and store it in the warp-packed layout.  status[0] receives 1 + the first singular patch id.
 // Returns -1 (nothing launched) when the level has a patch larger than 128 DoFs.
-int patch_factor(const Csr& A, const Patches& P, int prec, void* factors, int* status, cudaStream_t s);
 // (the layout written is P.sym's)
+// Matrix-free source of the patch matrices (PCPATCH-style, Sec. 3.1): each patch matrix is assembled
+// from the element matrices of every cell containing one of its DoFs, restricted to the patch's DoFs,
+// without the global matrix.  Entries are summed over the cells in ascending order, the order of the
+// global assembly, so the assembled patch matrix equals the gathered one bit for bit.
+struct PatchElems {
+  int nloc = 0;                  // element DoFs per cell
+  int ncell_lower = 0;           // cells below this index have the lower shape
+  const int* cell_dofs = nullptr;    // [cell][nloc] global DoF of each element DoF
+  const double* kel = nullptr;       // [2][nloc][nloc] element matrices of the two cell shapes
+  const int* cell_ptr = nullptr;     // per patch: range of its cells in `cells`
+  const int* cells = nullptr;
+};
+int patch_factor(const Csr& A, const Patches& P, int prec, void* factors, int* status, cudaStream_t s,
+                 const PatchElems* elems = nullptr);
 // delta[slot] = (A_i^{-1} r[idx_i]) for every patch (one launch for all patches of a level).  With
 // FP32-pair inverses r is first split into r2 (ndof float2) and delta holds FP32 pairs.
 int patch_apply(const Patches& P, const double* r, float2* r2, double* delta, cudaStream_t s);

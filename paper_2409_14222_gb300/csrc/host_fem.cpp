@@ -184,7 +184,7 @@ void element_matrices(int k, int e1x, int e1y, int e2x, int e2y, double h, doubl
     }
 }
 
-void build_level(int N, int k, double nu, bool with_patches, int nthreads, HostLevel& L) {
+void build_level(int N, int k, double nu, bool with_patches, int nthreads, HostLevel& L, bool element_data) {
   if (k < 2 || k > 6) throw std::runtime_error("order k must be in 2..6");
   L.N = N;
   L.k = k;
@@ -420,6 +420,55 @@ void build_level(int N, int k, double nu, bool with_patches, int nthreads, HostL
           emit(2, cl, 1, pn);
         }
   }
+  if (!element_data) return;
+  // ---- element data of the matrix-free patch assembly -------------------------------------------
+  const int nloc = nvl + nq;
+  L.nloc = nloc;
+  L.cell_dofs.resize(size_t(ncell) * nloc);
+  for (int c = 0; c < ncell; ++c) {
+    int* cd = L.cell_dofs.data() + size_t(c) * nloc;
+    for (int a = 0; a < nb; ++a)
+      for (int d = 0; d < 2; ++d) cd[2 * a + d] = 2 * cv[size_t(c) * nb + a] + d;
+    for (int p = 0; p < nq; ++p) cd[nvl + p] = n_u + cp[size_t(c) * nq + p];
+  }
+  L.kel.assign(size_t(2) * nloc * nloc, 0.0);
+  for (int sh = 0; sh < 2; ++sh) {
+    const Element& E = sh == 0 ? EL : EU;
+    double* K = L.kel.data() + size_t(sh) * nloc * nloc;
+    for (int a = 0; a < nvl; ++a)
+      for (int b = 0; b < nvl; ++b) K[size_t(a) * nloc + b] = E.A[size_t(a) * nvl + b];
+    for (int p = 0; p < nq; ++p)
+      for (int a = 0; a < nvl; ++a) {
+        K[size_t(nvl + p) * nloc + a] = E.B[size_t(p) * nvl + a];
+        K[size_t(a) * nloc + nvl + p] = E.B[size_t(p) * nvl + a];
+      }
+  }
+  // cells of each patch's assembly: every cell containing one of the patch's DoFs, ascending
+  const int np = int(L.patch_ptr.size()) - 1;
+  std::vector<std::vector<int>> pc(np);
+  parallel_for(np, nthreads, [&](int lo, int hi) {
+    std::vector<int> cs;
+    for (int p = lo; p < hi; ++p) {
+      cs.clear();
+      for (int e = L.patch_ptr[p]; e < L.patch_ptr[p + 1]; ++e) {
+        const int g = L.patch_dofs[e];
+        if (g < n_u) {
+          const int node = g / 2;
+          for (int t = vptr[node]; t < vptr[node + 1]; ++t) cs.push_back(vent[t] / nb);
+        } else {
+          const int node = g - n_u;
+          for (int t = pptr[node]; t < pptr[node + 1]; ++t) cs.push_back(pent[t] / nq);
+        }
+      }
+      std::sort(cs.begin(), cs.end());
+      cs.erase(std::unique(cs.begin(), cs.end()), cs.end());
+      pc[p] = cs;
+    }
+  });
+  L.patch_cell_ptr.assign(np + 1, 0);
+  for (int p = 0; p < np; ++p) L.patch_cell_ptr[p + 1] = L.patch_cell_ptr[p] + int(pc[p].size());
+  L.patch_cells.resize(L.patch_cell_ptr.back());
+  for (int p = 0; p < np; ++p) std::copy(pc[p].begin(), pc[p].end(), L.patch_cells.begin() + L.patch_cell_ptr[p]);
 }
 
 void build_transfer(const HostLevel& c, HostLevel& f) {

@@ -37,8 +37,8 @@ __device__ __forceinline__ float2 store_entry<float2>(double v) {
   return make_float2(hi, lo);
 }
 
-template <typename FT>
-__global__ void __launch_bounds__(kFactorThreads) k_patch_factor(Csr A, const int* __restrict__ slot_ptr,
+template <typename FT, bool kMF>
+__global__ void __launch_bounds__(kFactorThreads) k_patch_factor(Csr A, PatchElems E, const int* __restrict__ slot_ptr,
                                                                  const int* __restrict__ slot_dofs,
                                                                  const int64_t* __restrict__ foff,
                                                                  FT* __restrict__ F, int* status, int sym) {
@@ -54,17 +54,45 @@ __global__ void __launch_bounds__(kFactorThreads) k_patch_factor(Csr A, const in
   int* perm = reinterpret_cast<int*>(fcol + n);  // n
   for (int i = tid; i < n * n; i += kFactorThreads) M[i] = 0.0;
   __syncthreads();
-  // gather: row i of the patch scans CSR row dofs[i]; each column is located in the sorted list
-  for (int i = tid; i < n; i += kFactorThreads) {
-    const int g = dofs[i];
-    for (int e = A.ptr[g]; e < A.ptr[g + 1]; ++e) {
-      const int c = A.col[e];
-      int lo = 0, hi = n;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (dofs[mid] < c) lo = mid + 1; else hi = mid;
+  auto find = [&](int c) {   // position of global DoF c in the sorted patch list, or -1
+    int lo = 0, hi = n;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (dofs[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    return (lo < n && dofs[lo] == c) ? lo : -1;
+  };
+  if (!kMF) {
+    // matrix-full gather: row i of the patch scans CSR row dofs[i]; each column is located in the
+    // sorted list
+    for (int i = tid; i < n; i += kFactorThreads) {
+      const int g = dofs[i];
+      for (int e = A.ptr[g]; e < A.ptr[g + 1]; ++e) {
+        const int j = find(A.col[e]);
+        if (j >= 0) M[i * n + j] = A.val[e];
       }
-      if (lo < n && dofs[lo] == c) M[i * n + lo] = A.val[e];
+    }
+  } else {
+    // matrix-free assembly: row i sums, over the patch's cells in ascending order, the element-matrix
+    // row of its DoF into the patch columns (each cell is visited again by every patch it serves)
+    for (int i = tid; i < n; i += kFactorThreads) {
+      const int g = dofs[i];
+      for (int t = E.cell_ptr[p]; t < E.cell_ptr[p + 1]; ++t) {
+        const int c = E.cells[t];
+        const int* cd = E.cell_dofs + int64_t(c) * E.nloc;
+        int la = -1;
+        for (int q = 0; q < E.nloc; ++q)
+          if (cd[q] == g) {
+            la = q;
+            break;
+          }
+        if (la < 0) continue;
+        const double* K = E.kel + (int64_t(c < E.ncell_lower ? 0 : 1) * E.nloc + la) * E.nloc;
+        for (int q = 0; q < E.nloc; ++q) {
+          const int j = find(cd[q]);
+          if (j >= 0) M[i * n + j] += K[q];
+        }
+      }
     }
   }
   __syncthreads();
@@ -656,7 +684,27 @@ int apply_prec(const Patches& P, const ApplySched& sc, const double* r, const fl
 
 }  // namespace
 
-int patch_factor(const Csr& A, const Patches& P, int prec, void* factors, int* status, cudaStream_t s) {
+namespace {
+
+template <typename FT>
+void launch_factor(const Csr& A, const PatchElems* elems, const Patches& P, void* factors, int* status, size_t smem,
+                   int smem_cap, cudaStream_t s) {
+  if (elems) {
+    cudaFuncSetAttribute(k_patch_factor<FT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);
+    k_patch_factor<FT, true><<<P.npatch, kFactorThreads, smem, s>>>(A, *elems, P.slot_ptr, P.slot_dofs, P.foff,
+                                                                     static_cast<FT*>(factors), status, P.sym);
+  } else {
+    cudaFuncSetAttribute(k_patch_factor<FT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);
+    k_patch_factor<FT, false><<<P.npatch, kFactorThreads, smem, s>>>(A, PatchElems{}, P.slot_ptr, P.slot_dofs,
+                                                                      P.foff, static_cast<FT*>(factors), status,
+                                                                      P.sym);
+  }
+}
+
+}  // namespace
+
+int patch_factor(const Csr& A, const Patches& P, int prec, void* factors, int* status, cudaStream_t s,
+                 const PatchElems* elems) {
   if (P.npatch == 0) return 0;
   // shared bytes n*n*8 + n*12 for the largest patch of the level (n <= 4 * nb_max <= 128).  The
   // function attribute is always set to the bound for n = 128 (the same value from every thread, so
@@ -665,19 +713,12 @@ int patch_factor(const Csr& A, const Patches& P, int prec, void* factors, int* s
   const size_t smem = size_t(nmax) * nmax * 8 + size_t(nmax) * 12;
   const int smem_cap = 128 * 128 * 8 + 128 * 12;
   if (nmax > 128) return -1;   // the caller reports VK_ERR_ARG: nothing is left unfactored silently
-  if (prec == 0) {
-    cudaFuncSetAttribute(k_patch_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);
-    k_patch_factor<double><<<P.npatch, kFactorThreads, smem, s>>>(A, P.slot_ptr, P.slot_dofs, P.foff,
-                                                                   static_cast<double*>(factors), status, P.sym);
-  } else if (prec == 1) {
-    cudaFuncSetAttribute(k_patch_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);
-    k_patch_factor<float><<<P.npatch, kFactorThreads, smem, s>>>(A, P.slot_ptr, P.slot_dofs, P.foff,
-                                                                  static_cast<float*>(factors), status, P.sym);
-  } else {
-    cudaFuncSetAttribute(k_patch_factor<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);
-    k_patch_factor<float2><<<P.npatch, kFactorThreads, smem, s>>>(A, P.slot_ptr, P.slot_dofs, P.foff,
-                                                                   static_cast<float2*>(factors), status, P.sym);
-  }
+  if (prec == 0)
+    launch_factor<double>(A, elems, P, factors, status, smem, smem_cap, s);
+  else if (prec == 1)
+    launch_factor<float>(A, elems, P, factors, status, smem, smem_cap, s);
+  else
+    launch_factor<float2>(A, elems, P, factors, status, smem, smem_cap, s);
   return 1;
 }
 

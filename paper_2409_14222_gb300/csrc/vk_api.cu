@@ -244,6 +244,7 @@ struct DevLevel {
   double lam = 0.0;
   double *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *t = nullptr, *delta = nullptr;
   float2* r2 = nullptr;  // FP32-pair residual (emulated-FP64 inverses only)
+  vk::gpu::PatchElems pe;   // element data of the matrix-free patch assembly (patch_assembly = 1)
   // multi-right-hand-side structures (batch_prec != VK_BATCH_NONE)
   vk::gpu::SellB Ab, Pb, Rb;                 // SELL-8 copies for the 16-right-hand-side products
   int64_t* foff16 = nullptr;
@@ -325,6 +326,7 @@ struct vk_hierarchy {
   double apply_bytes = 0.0, apply_flops = 0.0;
   double bapply_bytes = 0.0, bapply_flops = 0.0;
   double spmv_bytes = 0.0, bspmv_bytes = 0.0;
+  double factor_ms = 0.0, setup_ms = 0.0;
   // graph-resident FGMRES (one CUDA graph per hierarchy: prologue, WHILE node, epilogue)
   vk::gpu::FgState* st = nullptr;        // device
   vk::gpu::FgState* h_par = nullptr;     // pinned: parameters written before each launch
@@ -397,6 +399,8 @@ void validate(const vk_problem* p, const vk_options* o) {
   if (o->spmv_warps < 1 || o->spmv_warps > 4096) raise(VK_ERR_ARG, "spmv_warps must be in 1..4096");
   if (o->batch_coarse_fp32 != 0 && o->batch_coarse_fp32 != 1) raise(VK_ERR_ARG, "batch_coarse_fp32 must be 0 or 1");
   if (o->test_singular_patch < -1) raise(VK_ERR_ARG, "test_singular_patch must be -1 or a patch id");
+  if (o->patch_assembly != VK_ASSEMBLY_MATRIX_FULL && o->patch_assembly != VK_ASSEMBLY_MATRIX_FREE)
+    raise(VK_ERR_ARG, "bad patch_assembly");
   if (o->apply_schedule < -1 || o->apply_schedule >= int(apply_candidates().size()))
     raise(VK_ERR_ARG, "apply_schedule must be -1 or a candidate index");
   if (o->batch_prec != VK_BATCH_NONE) {
@@ -412,7 +416,8 @@ void build_host(vk_hierarchy* h) {
   nthreads = std::max(1, std::min(nthreads, 64));
   h->host.resize(L);
   for (int l = 0; l < L; ++l) {
-    vk::build_level(h->prob.N_coarse << l, h->prob.k, h->prob.nu, l > 0, nthreads, h->host[l]);
+    vk::build_level(h->prob.N_coarse << l, h->prob.k, h->prob.nu, l > 0, nthreads, h->host[l],
+                    l > 0 && h->opt.patch_assembly == VK_ASSEMBLY_MATRIX_FREE);
     if (l > 0) vk::build_transfer(h->host[l - 1], h->host[l]);
   }
 }
@@ -635,6 +640,14 @@ void allocate_device(vk_hierarchy* h) {
       G.slot_pos = m.upload(P.slot_pos);
       G.weight = P.weight.empty() ? nullptr : m.upload(P.weight);
       D.delta = m.get_n<double>(G.nslots);
+      if (h->opt.patch_assembly == VK_ASSEMBLY_MATRIX_FREE) {
+        D.pe.nloc = H.nloc;
+        D.pe.ncell_lower = H.N * H.N;
+        D.pe.cell_dofs = m.upload(H.cell_dofs);
+        D.pe.kel = m.upload(H.kel);
+        D.pe.cell_ptr = m.upload(H.patch_cell_ptr);
+        D.pe.cells = m.upload(H.patch_cells);
+      }
       if (h->opt.factor_prec == VK_PREC_F64E) D.r2 = m.get_n<float2>(H.ndof);
     }
   }
@@ -853,11 +866,31 @@ void setup_device(vk_hierarchy* h, cudaStream_t s) {
   CK(cudaStreamCreateWithFlags(&h->cap1, cudaStreamNonBlocking));
   CK(cudaMemsetAsync(h->iflag, 0, 16 * sizeof(int), s));
   const int L = h->prob.nlevels;
-  for (int l = 1; l < L; ++l) {
-    DevLevel& D = h->lv[l];
-    const int nl = vk::gpu::patch_factor(D.Acsr, D.pat, D.pat.prec, const_cast<void*>(D.pat.factors), h->iflag + l, s);
-    if (nl < 0) raise(VK_ERR_ARG, "level " + std::to_string(l) + " has a patch larger than the factor kernel supports");
-    h->n_launch += nl;
+  {
+    // patch matrices (gathered or assembled) and their inverses, timed with events on the setup stream
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+    for (int l = 1; l < L; ++l) {
+      DevLevel& D = h->lv[l];
+      const vk::gpu::PatchElems* pe = h->opt.patch_assembly == VK_ASSEMBLY_MATRIX_FREE ? &D.pe : nullptr;
+      const int nl = vk::gpu::patch_factor(D.Acsr, D.pat, D.pat.prec, const_cast<void*>(D.pat.factors), h->iflag + l,
+                                           s, pe);
+      if (nl < 0) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        raise(VK_ERR_ARG, "level " + std::to_string(l) + " has a patch larger than the factor kernel supports");
+      }
+      h->n_launch += nl;
+    }
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    h->factor_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     CK(cudaGetLastError());
   }
   // coarsest level: bordered inverse
@@ -1451,6 +1484,7 @@ int vk_setup(const vk_problem* p, const vk_options* o, const vk_allocator* alloc
       h->mem.user = *alloc;
       h->mem.custom = true;
     }
+    const auto t_setup = std::chrono::steady_clock::now();
     build_host(h.get());
     if (!h->host_only) {
       vk_options tmp = h->opt;
@@ -1466,6 +1500,7 @@ int vk_setup(const vk_problem* p, const vk_options* o, const vk_allocator* alloc
       }
       h->opt = tmp;
     }
+    h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_setup).count();
     *out = h.release();
     return VK_OK;
   });
@@ -1765,6 +1800,8 @@ int vk_stats_read(vk_hierarchy* h, vk_stats* out) {
     out->spmv_ms = h->tm_spmv.total_ms();
     out->spmv_bytes = h->spmv_bytes;
     out->batch_spmv_bytes = h->bspmv_bytes;
+    out->setup_factor_ms = h->factor_ms;
+    out->setup_ms = h->setup_ms;
     return VK_OK;
   });
 }

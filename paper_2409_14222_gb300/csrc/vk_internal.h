@@ -29,10 +29,18 @@ struct HostLevel {
   // Vanka patches (empty on the coarsest level): DoFs of patch p are dofs[ptr[p] .. ptr[p+1]).
   std::vector<int> patch_ptr, patch_dofs;
   std::vector<int8_t> patch_kind;  // 0 vertex, 1 edge, 2 cell
+  // Element data for assembling patch matrices from element matrices (matrix-free patches; built only
+  // on request): the element DoFs of every cell in element-local order (velocity 2a + c, then the
+  // pressure nodes), the element matrix [[A_e, B_e^T], [B_e, 0]] of the lower and of the upper cell
+  // shape (nloc x nloc each, row-major), and per patch the cells containing any of its DoFs (ascending).
+  int nloc = 0;
+  std::vector<int> cell_dofs;
+  std::vector<double> kel;
+  std::vector<int> patch_cell_ptr, patch_cells;
 };
 
 // host_fem.cpp
-void build_level(int N, int k, double nu, bool with_patches, int nthreads, HostLevel& L);
+void build_level(int N, int k, double nu, bool with_patches, int nthreads, HostLevel& L, bool element_data = false);
 void build_transfer(const HostLevel& coarse, HostLevel& fine);
 // Element matrices of one cell shape, for tests and the manufactured load (row-major).
 void element_matrices(int k, int e1x, int e1y, int e2x, int e2y, double h, double nu,

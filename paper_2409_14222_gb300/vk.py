@@ -23,6 +23,7 @@ VK_ERR_INTERNAL = 8
 VK_ERR_CANCELLED = 9
 VK_BC_DIRICHLET_ALL = 0
 VK_SERVE_GROUP, VK_SERVE_STREAMS = 0, 1
+VK_ASSEMBLY_MATRIX_FULL, VK_ASSEMBLY_MATRIX_FREE = 0, 1
 
 VK_WEIGHTS_PLAIN = 0
 VK_WEIGHTS_MULTIPLICITY = 1
@@ -74,7 +75,8 @@ class vk_options(ctypes.Structure):
                 ("batch_max_iterations", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("apply_schedule", ctypes.c_int32), ("batch_engine", ctypes.c_int32),
                 ("test_expire_wait", ctypes.c_int32), ("spmv_warps", ctypes.c_int32),
-                ("batch_coarse_fp32", ctypes.c_int32), ("test_singular_patch", ctypes.c_int32)]
+                ("batch_coarse_fp32", ctypes.c_int32), ("test_singular_patch", ctypes.c_int32),
+                ("patch_assembly", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -96,7 +98,8 @@ class vk_stats(ctypes.Structure):
                 ("apply_ms", ctypes.c_double), ("apply_bytes", ctypes.c_double), ("apply_flops", ctypes.c_double),
                 ("batch_apply_bytes", ctypes.c_double), ("batch_apply_flops", ctypes.c_double),
                 ("spmv_launches", ctypes.c_int64), ("spmv_ms", ctypes.c_double), ("spmv_bytes", ctypes.c_double),
-                ("batch_spmv_bytes", ctypes.c_double)]
+                ("batch_spmv_bytes", ctypes.c_double), ("setup_factor_ms", ctypes.c_double),
+                ("setup_ms", ctypes.c_double)]
 
 
 class vk_server_config(ctypes.Structure):

@@ -191,3 +191,13 @@ def test_problem_boundary_data_and_domain_are_checked(vk):
         vk.footprint(4, 2, 2, options=vk.default_options(test_singular_patch=10 ** 6))
     assert e.value.code == vk.vk.VK_ERR_ARG
     assert vk.default_options().test_singular_patch == -1
+
+
+def test_matrix_free_option_builds_element_data(vk):
+    # the matrix-free patch assembly keeps each cell's element DoFs and each patch's cell list on the
+    # device: a larger footprint, refused values rejected
+    base = vk.footprint(8, 3, 2)
+    mf = vk.footprint(8, 3, 2, options=vk.default_options(patch_assembly=vk.vk.VK_ASSEMBLY_MATRIX_FREE))
+    assert mf > base
+    with pytest.raises(vk.VkError):
+        vk.footprint(8, 3, 2, options=vk.default_options(patch_assembly=2))
