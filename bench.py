@@ -39,6 +39,7 @@ CONFIGS = {
     "cfg4batch": (32, 5, 2, 1, 1e-8, "2D Stokes TH P2/P1, 32x32 -> 512x512 (5 levels), FGMRES to 1e-8"),
     "cfg5": (8, 0, 0, 1, 1e-8, "Serving: Poisson stream of solve requests, N in {16..256} (coarsest 8x8), "
                                "k in {2,3,4}, FGMRES to 1e-8"),
+    "stopping": (5, 0, 0, 1, 1e-2, "Stopping-criterion study (Sec. 4.4): manufactured problem, tolerance halving"),
 }
 DEFAULT_CONFIG = "cfg4"
 
@@ -775,6 +776,64 @@ def run_serving(args):
     }), flush=True)
 
 
+def run_stopping(args):
+    """The stopping-criterion study of Sec. 4.4 on the GPU, for Taylor-Hood P_k/P_{k-1} on triangles: the
+    manufactured problem (Eq. model_problem) on 5x5 -> 5*2^l meshes is solved with relative tolerances
+    1e-2, 5e-3, 2.5e-3, ... (halved each time, down to 1e-13), and the relative H^1 velocity error and the
+    L^2 pressure error (mean removed) are measured on the device.  For each quantity the reported
+    tolerance is the largest of the sequence from which on every tighter tolerance gives an error within
+    1 % of the error at the tightest one (the discretisation error)."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    import paper_2409_14222_gb300 as vk
+    torch.cuda.set_device(0)
+    taus = []
+    t = 1e-2
+    while t >= 1e-13:
+        taus.append(t)
+        t /= 2
+    rows = []
+    t_start = time.perf_counter()
+    for k in (2, 3, 4):
+        for lev in (1, 2, 3, 4):
+            G = vk.Hierarchy(5, lev + 1, k, options=vk.default_options(sweeps=1))
+            b = torch.from_numpy(G.manufactured_rhs()).cuda()
+            x = torch.zeros_like(b)
+            errs, iters, ms = [], [], []
+            for tau in taus:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                out = G.solve(b, x, rtol=tau, history=False)
+                e1.record()
+                errs.append(G.errors(x))
+                iters.append(out["iterations"])
+                ms.append(e0.elapsed_time(e1))
+                if not out["converged"]:
+                    break
+            def needed(q):
+                final = errs[-1][q]
+                ok = [abs(e[q] - final) <= 1e-2 * final for e in errs]
+                i = len(ok) - 1
+                while i > 0 and ok[i - 1]:
+                    i -= 1
+                return i
+            iv, ip = needed(0), needed(2)
+            rows.append({"k": k, "levels_refined": lev, "mesh": f"{5 << lev}x{5 << lev}", "ndof": G.ndof(),
+                         "velocity": {"tolerance": taus[iv], "iterations": iters[iv], "h1_rel_error": errs[iv][0],
+                                      "solve_ms": ms[iv]},
+                         "pressure": {"tolerance": taus[ip], "iterations": iters[ip], "l2_error": errs[ip][2],
+                                      "solve_ms": ms[ip]},
+                         "tightest": {"tolerance": taus[len(errs) - 1], "h1_rel_error": errs[-1][0],
+                                      "l2_rel_error": errs[-1][1], "p_l2_error": errs[-1][2]}})
+            G.close()
+    print(json.dumps({"metric": "stopping tolerance needed to reach discretisation error (Sec. 4.4)",
+                      "config": {"workload": "Taylor-Hood P_k/P_{k-1} on triangles, manufactured solution, "
+                                             "5x5 coarsest grid, V(1,1), FGMRES", "tolerances": "1e-2 halved to 1e-13",
+                                 "criterion": "every tighter tolerance within 1 % of the tightest one's error"},
+                      "rows": rows, "wall_s": time.perf_counter() - t_start}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -817,6 +876,8 @@ def main():
         run_reference(args, config, cfg)
     elif args.config == "cfg5":
         run_serving(args)
+    elif args.config == "stopping":
+        run_stopping(args)
     elif args.config == "cfg4batch":
         run_batch(args, config, cfg)
     else:

@@ -469,6 +469,21 @@ int vk_server_cancel(vk_server* s, uint64_t ticket);
 /* Finishes the queued requests, stops the workers and frees every hierarchy. */
 void vk_server_destroy(vk_server* s);
 
+/* Right-hand side of the manufactured problem of Sec. 4 (Eq. model_problem: u = (sin(pi x) cos(pi y),
+ * -cos(pi x) sin(pi y)), p = 0, f = 2 pi^2 nu u) on the finest level, in the canonical order (b_host:
+ * ndof doubles): the load integrated with a collapsed Gauss-Legendre rule of k + 5 points per direction,
+ * the velocity's boundary values (their nodal interpolant) lifted, b_F = F_F - K_FB g and b_B = g.
+ * Host computation; works on host-only hierarchies. */
+int vk_manufactured_rhs(const vk_hierarchy* h, double* b_host);
+
+/* Discretisation errors of a finest-level solution x_dev (device, ndof doubles) of the manufactured
+ * problem, the quantities of the stopping-criterion study of Sec. 4.4: errs[0] = relative H^1 velocity
+ * error (||u - u_h||_{H^1} / ||u||_{H^1}), errs[1] = relative L^2 velocity error, errs[2] = absolute
+ * L^2 pressure error after removing the pressure's mean (p = 0).  Integrated on the device cell by cell
+ * with a collapsed Gauss-Legendre rule of k + 6 points per direction, summed in a fixed order.  errs is
+ * a host array of 3 doubles; the call allocates and frees its tables and synchronises `stream`. */
+int vk_errors(vk_hierarchy* h, const double* x_dev, double* errs, void* stream);
+
 /* Measurement helper (no counterpart in the paper: it measures the roofline denominator of the FP64
  * kernels).  FMA throughput of the current device in TFLOP/s (2 flops per FMA): precision 0 = FP64,
  * 1 = FP32.  Runs independent FMA chains on every SM, best of 5 launches timed with CUDA events on

@@ -272,6 +272,20 @@ inline int64_t frag_size(int n) { return 32LL * ((n + 15) / 16) * ((n + 15) / 16
 // device buffer of at least 8 * 256 * 8 * (SM count) bytes (never written in practice).
 double fma_rate_tflops(bool fp64, void* scratch, cudaStream_t s);
 
+// ---- discretisation errors (kernels_fem.cu) --------------------------------------------------------
+struct FemErrArgs {
+  int N = 0, nb = 0, nq = 0, Q = 0, n_u = 0;
+  double h = 0.0;
+  const int* cv = nullptr;      // [cell][nb] velocity nodes
+  const int* cp = nullptr;      // [cell][nq] pressure nodes
+  const double *xi = nullptr, *eta = nullptr, *w = nullptr;                  // [Q] reference rule
+  const double *phi = nullptr, *dxi = nullptr, *deta = nullptr;             // [Q][nb] P_k basis
+  const double* psi = nullptr;  // [Q][nq] P_{k-1} basis
+  const double* x = nullptr;    // solution (canonical DoF order)
+};
+// sums[0..6] = e_l2, n_l2, e_h1, n_h1 (gradient parts), int p, int p^2, area; partial: 1024 * 7 doubles
+int fem_error_sums(const FemErrArgs& a, double* partial, double* sums, cudaStream_t s);
+
 // ---- group kernels: one launch over the members of a group solve (vk_group_*) -------------------
 // Each member is an independent solve on its own hierarchy (its own mesh size, order and matrices).
 // A group launch processes the work of every member listed in its by-value argument block; item

@@ -557,3 +557,122 @@ double splitmix_uniform_pm1(uint64_t seed, uint64_t i) {
 }
 
 }  // namespace vk
+
+namespace vk {
+
+// Cell -> node maps of the structured mesh: velocity P_k nodes (cv, ncell x nb) and pressure P_{k-1}
+// nodes (cp, ncell x nq) in the element's local order (the order of build_level's assembly).
+void cell_maps(int N, int k, std::vector<int>& cv, std::vector<int>& cp) {
+  const auto av = node_indices(k), aq = node_indices(k - 1);
+  const int nb = int(av.size()), nq = int(aq.size()), nv1 = k * N + 1, np1 = (k - 1) * N + 1;
+  Cells cells{N};
+  const int ncell = cells.count();
+  cv.resize(size_t(ncell) * nb);
+  cp.resize(size_t(ncell) * nq);
+  for (int c = 0; c < ncell; ++c) {
+    int x0, y0;
+    const CellShape* s;
+    cells.vertex0(c, x0, y0, s);
+    for (int a = 0; a < nb; ++a)
+      cv[size_t(c) * nb + a] = (k * y0 + av[a][1] * s->e1y + av[a][2] * s->e2y) * nv1 +
+                               k * x0 + av[a][1] * s->e1x + av[a][2] * s->e2x;
+    for (int p = 0; p < nq; ++p)
+      cp[size_t(c) * nq + p] = ((k - 1) * y0 + aq[p][1] * s->e1y + aq[p][2] * s->e2y) * np1 +
+                               (k - 1) * x0 + aq[p][1] * s->e1x + aq[p][2] * s->e2x;
+  }
+}
+
+// Collapsed (Duffy) Gauss-Legendre rule with q points per direction on the reference triangle and the
+// P_k / P_{k-1} basis at its points: xi = u, eta = v (1 - u), weight w_u w_v (1 - u).
+void reference_tables(int k, int q, std::vector<double>& xi, std::vector<double>& eta, std::vector<double>& w,
+                      std::vector<double>& phi, std::vector<double>& dxi, std::vector<double>& deta,
+                      std::vector<double>& psi) {
+  const auto av = node_indices(k), aq = node_indices(k - 1);
+  const int nb = int(av.size()), nq = int(aq.size()), Q = q * q;
+  std::vector<double> gx, gw;
+  gauss_legendre01(q, gx, gw);
+  xi.resize(Q);
+  eta.resize(Q);
+  w.resize(Q);
+  phi.resize(size_t(Q) * nb);
+  dxi.resize(size_t(Q) * nb);
+  deta.resize(size_t(Q) * nb);
+  psi.resize(size_t(Q) * nq);
+  for (int iu = 0; iu < q; ++iu)
+    for (int iv = 0; iv < q; ++iv) {
+      const int t = iu * q + iv;
+      xi[t] = gx[iu];
+      eta[t] = gx[iv] * (1.0 - gx[iu]);
+      w[t] = gw[iu] * gw[iv] * (1.0 - gx[iu]);
+      eval_basis(k, av, xi[t], eta[t], &phi[size_t(t) * nb], &dxi[size_t(t) * nb], &deta[size_t(t) * nb]);
+      eval_basis(k - 1, aq, xi[t], eta[t], &psi[size_t(t) * nq], nullptr, nullptr);
+    }
+}
+
+// Right-hand side of the manufactured problem (Eq. model_problem): u = (sin(pi x) cos(pi y),
+// -cos(pi x) sin(pi y)), p = 0, so f = -div(2 nu eps(u)) + grad p = 2 pi^2 nu u.  The load <f, v> is
+// integrated with the collapsed rule of k + 5 points per direction; the velocity's Dirichlet data g (its
+// nodal interpolant on the boundary) is lifted: b_F = F_F - K_FB g, b_B = g, with K the element
+// matrices before boundary conditions.
+void manufactured_rhs(const HostLevel& L, double nu, std::vector<double>& b) {
+  const int N = L.N, k = L.k, nv1 = L.nv1, n_u = L.n_u;
+  const double h = 1.0 / N, pi = M_PI;
+  std::vector<int> cv, cp;
+  cell_maps(N, k, cv, cp);
+  const int nb = (k + 1) * (k + 2) / 2, nq = k * (k + 1) / 2, nvl = 2 * nb;
+  std::vector<double> xi, eta, w, phi, dxi, deta, psi;
+  reference_tables(k, k + 5, xi, eta, w, phi, dxi, deta, psi);
+  const int Q = int(w.size());
+  const Element EL = make_element(k, kLower, h, nu), EU = make_element(k, kUpper, h, nu);
+  Cells cells{N};
+  b.assign(L.ndof, 0.0);
+  std::vector<double> g(L.ndof, 0.0);
+  for (int node = 0; node < nv1 * nv1; ++node)
+    if (L.dir[2 * node]) {
+      const double X = double(node % nv1) / (k * N), Y = double(node / nv1) / (k * N);
+      g[2 * node] = std::sin(pi * X) * std::cos(pi * Y);
+      g[2 * node + 1] = -std::cos(pi * X) * std::sin(pi * Y);
+    }
+  for (int c = 0; c < cells.count(); ++c) {
+    int x0, y0;
+    const CellShape* s;
+    cells.vertex0(c, x0, y0, s);
+    const double J00 = h * s->e1x, J01 = h * s->e2x, J10 = h * s->e1y, J11 = h * s->e2y;
+    const double adet = std::fabs(J00 * J11 - J01 * J10);
+    const int* nodes = &cv[size_t(c) * nb];
+    for (int t = 0; t < Q; ++t) {
+      const double X = h * x0 + J00 * xi[t] + J01 * eta[t], Y = h * y0 + J10 * xi[t] + J11 * eta[t];
+      const double f1 = 2 * pi * pi * nu * std::sin(pi * X) * std::cos(pi * Y);
+      const double f2 = -2 * pi * pi * nu * std::cos(pi * X) * std::sin(pi * Y);
+      const double wt = w[t] * adet;
+      for (int a = 0; a < nb; ++a) {
+        b[2 * nodes[a]] += wt * f1 * phi[size_t(t) * nb + a];
+        b[2 * nodes[a] + 1] += wt * f2 * phi[size_t(t) * nb + a];
+      }
+    }
+    // lifting: subtract K_e g_e from every row of the element
+    const Element& E = c < N * N ? EL : EU;
+    double ge[64];
+    bool any = false;
+    for (int a = 0; a < nb; ++a)
+      for (int d = 0; d < 2; ++d) {
+        ge[2 * a + d] = g[2 * nodes[a] + d];
+        any = any || ge[2 * a + d] != 0.0;
+      }
+    if (!any) continue;
+    for (int la = 0; la < nvl; ++la) {
+      double acc = 0.0;
+      for (int lb = 0; lb < nvl; ++lb) acc += E.A[size_t(la) * nvl + lb] * ge[lb];
+      b[2 * nodes[la / 2] + (la & 1)] -= acc;
+    }
+    for (int p = 0; p < nq; ++p) {
+      double acc = 0.0;
+      for (int lb = 0; lb < nvl; ++lb) acc += E.B[size_t(p) * nvl + lb] * ge[lb];
+      b[n_u + cp[size_t(c) * nq + p]] -= acc;
+    }
+  }
+  for (int i = 0; i < n_u; ++i)
+    if (L.dir[i]) b[i] = g[i];
+}
+
+}  // namespace vk

@@ -1806,6 +1806,73 @@ int vk_stats_read(vk_hierarchy* h, vk_stats* out) {
   });
 }
 
+int vk_manufactured_rhs(const vk_hierarchy* h, double* b_host) {
+  return guard([&] {
+    if (!h || !b_host) raise(VK_ERR_ARG, "null argument");
+    std::vector<double> b;
+    vk::manufactured_rhs(h->host.back(), h->prob.nu, b);
+    std::copy(b.begin(), b.end(), b_host);
+    return VK_OK;
+  });
+}
+
+int vk_errors(vk_hierarchy* h, const double* x, double* errs, void* stream) {
+  return guard([&] {
+    check_device(h);
+    if (!x || !errs) raise(VK_ERR_ARG, "null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const vk::HostLevel& F = h->host.back();
+    std::vector<int> cv, cp;
+    vk::cell_maps(F.N, F.k, cv, cp);
+    std::vector<double> xi, eta, w, phi, dxi, deta, psi;
+    vk::reference_tables(F.k, F.k + 6, xi, eta, w, phi, dxi, deta, psi);
+    std::vector<void*> bufs;
+    auto up = [&](const auto& v) {
+      using T = typename std::decay_t<decltype(v)>::value_type;
+      void* p = nullptr;
+      CK(cudaMalloc(&p, std::max<size_t>(1, v.size()) * sizeof(T)));
+      bufs.push_back(p);
+      CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+      return static_cast<const T*>(p);
+    };
+    double sums[7] = {};
+    try {
+      vk::gpu::FemErrArgs a;
+      a.N = F.N;
+      a.nb = (F.k + 1) * (F.k + 2) / 2;
+      a.nq = F.k * (F.k + 1) / 2;
+      a.Q = int(w.size());
+      a.n_u = F.n_u;
+      a.h = 1.0 / F.N;
+      a.cv = up(cv);
+      a.cp = up(cp);
+      a.xi = up(xi);
+      a.eta = up(eta);
+      a.w = up(w);
+      a.phi = up(phi);
+      a.dxi = up(dxi);
+      a.deta = up(deta);
+      a.psi = up(psi);
+      a.x = x;
+      std::vector<double> zeros(1024 * 7 + 7, 0.0);
+      double* part = const_cast<double*>(up(zeros));
+      h->n_launch += vk::gpu::fem_error_sums(a, part, part + 1024 * 7, s);
+      CK(cudaMemcpyAsync(sums, part + 1024 * 7, 7 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    } catch (...) {
+      cudaStreamSynchronize(s);
+      for (void* p : bufs) cudaFree(p);
+      throw;
+    }
+    for (void* p : bufs) cudaFree(p);
+    const double mean = sums[4] / sums[6];
+    errs[0] = std::sqrt((sums[0] + sums[2]) / (sums[1] + sums[3]));
+    errs[1] = std::sqrt(sums[0] / sums[1]);
+    errs[2] = std::sqrt(std::max(sums[5] - 2.0 * mean * sums[4] + mean * mean * sums[6], 0.0));
+    return VK_OK;
+  });
+}
+
 int vk_measure_fma_rate(int precision, void* stream, double* tflops) {
   return guard([&] {
     if (!tflops || (precision != 0 && precision != 1)) raise(VK_ERR_ARG, "bad arguments");

@@ -47,6 +47,12 @@ void element_matrices(int k, int e1x, int e1y, int e2x, int e2y, double h, doubl
                       std::vector<double>& Aloc, std::vector<double>& Bloc);
 void gauss_legendre01(int q, std::vector<double>& x, std::vector<double>& w);
 
+void cell_maps(int N, int k, std::vector<int>& cv, std::vector<int>& cp);
+void reference_tables(int k, int q, std::vector<double>& xi, std::vector<double>& eta, std::vector<double>& w,
+                      std::vector<double>& phi, std::vector<double>& dxi, std::vector<double>& deta,
+                      std::vector<double>& psi);
+void manufactured_rhs(const HostLevel& L, double nu, std::vector<double>& b);
+
 // host_eig.cpp: eigenvalues of a small real upper-Hessenberg matrix (row-major m x m).
 int hessenberg_eigenvalues(int m, const double* H, double* re, double* im);
 

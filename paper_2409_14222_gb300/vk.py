@@ -47,7 +47,7 @@ SYMBOLS = [
     "vk_vanka_noalloc", "vk_solve_batch", "vk_apply_schedule", "vk_ndof", "vk_export_dof_coords", "vk_default_server_config", "vk_server_create", "vk_server_submit", "vk_server_wait",
     "vk_server_get_stats", "vk_server_destroy", "vk_check_problem", "vk_server_cancel", "vk_measure_fma_rate",
     "vk_group_create", "vk_group_add", "vk_group_step", "vk_group_result", "vk_group_launches", "vk_group_destroy",
-    "vk_group_add_host", "vk_group_active",
+    "vk_group_add_host", "vk_group_active", "vk_manufactured_rhs", "vk_errors",
 ]
 
 
@@ -180,6 +180,8 @@ def lib():
             "vk_group_result": (I, [VP, I, VP, P(vk_solve_info)]),
             "vk_group_add_host": (I, [VP, H, VP, D, I, VP, P(I)]),
             "vk_group_active": (I, [VP, I, P(I)]),
+            "vk_manufactured_rhs": (I, [H, VP]),
+            "vk_errors": (I, [H, VP, VP, VP]),
             "vk_group_launches": (I, [VP, P(I64)]),
             "vk_group_destroy": (None, [VP]),
             "vk_stats_read": (I, [H, P(vk_stats)]),
@@ -370,6 +372,20 @@ class Hierarchy:
         st = vk_stats()
         check(lib().vk_stats_read(self.handle, ctypes.byref(st)))
         return {name: getattr(st, name) for name, _ in vk_stats._fields_}
+
+    def manufactured_rhs(self):
+        """Right-hand side of the manufactured problem (Eq. model_problem) on the finest level (numpy)."""
+        import numpy as np
+        b = np.zeros(self.ndof())
+        check(lib().vk_manufactured_rhs(self.handle, _ptr(b)))
+        return b
+
+    def errors(self, x, stream=None):
+        """(relative H^1 velocity, relative L^2 velocity, L^2 pressure) errors of x (vk_errors)."""
+        import numpy as np
+        e = np.zeros(3)
+        check(lib().vk_errors(self.handle, _ptr(x), _ptr(e), _stream_handle(stream)))
+        return tuple(float(v) for v in e)
 
     # ---- device operations (tensors: contiguous float64 on the device) ---------------------------
     def residual(self, level, b, x, r, stream=None):

@@ -201,3 +201,17 @@ def test_matrix_free_option_builds_element_data(vk):
     assert mf > base
     with pytest.raises(vk.VkError):
         vk.footprint(8, 3, 2, options=vk.default_options(patch_assembly=2))
+
+
+@pytest.mark.parametrize("N,k", [(4, 2), (8, 2), (4, 3), (2, 4)])
+def test_manufactured_rhs_equals_the_oracle(vk, N, k):
+    # load of Eq. (model_problem) with the Dirichlet data lifted: the library (Silvester basis, its own
+    # Gauss-Legendre nodes) and the oracle (exact rational basis, NumPy's Gauss-Legendre) agree to
+    # rounding
+    h = vk.Hierarchy(N, 1, k, nu=1.0, host_only=True)
+    s = fem.Space(N, k)
+    want = fem.manufactured_rhs(s, fem.assemble_full(s, 1.0), 1.0)
+    got = h.manufactured_rhs()
+    assert np.linalg.norm(got - want) <= 1e-13 * np.linalg.norm(want)
+    mask = s.dirichlet_mask()
+    assert np.array_equal(got[mask] == 0.0, want[mask] == 0.0)

@@ -1,0 +1,75 @@
+"""Stopping-criterion study of Sec. 4.4 on the GPU: discretisation errors of the manufactured problem
+(Eq. model_problem) as the FGMRES tolerance is halved from 1e-2.
+
+* vk_errors (relative H^1 / L^2 velocity errors, L^2 pressure error after removing the mean, integrated
+  on the device) equals the oracle's fem.errors on the same vectors.
+* The study itself: for each tolerance of the sequence 1e-2 / 2^i the GPU solve's iteration count and
+  errors equal the oracle's, so the tolerance at which the errors reach the discretisation error is the
+  same on both sides.
+"""
+import numpy as np
+import pytest
+
+from oracle import fem, solver
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_14222_gb300 import build
+    build.build()
+    import paper_2409_14222_gb300 as vk
+    return vk
+
+
+@pytest.mark.parametrize("N,k", [(4, 2), (8, 2), (4, 3), (2, 4)])
+def test_error_norms_equal_the_oracle(vk, N, k):
+    G = vk.Hierarchy(N, 1, k)
+    s = fem.Space(N, k)
+    K = fem.assemble_full(s)
+    A = fem.apply_dirichlet(K, s.dirichlet_mask())
+    b = solver.project(s, fem.manufactured_rhs(s, K))
+    xd = solver.project(s, solver.direct_solve(A, s.nullspace(), b))
+    rng = np.random.default_rng(81)
+    for x in (xd, xd + 1e-3 * rng.standard_normal(len(xd))):
+        got = G.errors(torch.from_numpy(x).cuda())
+        want = fem.errors(s, x)
+        for g, w in zip(got, want):
+            assert abs(g - w) <= 1e-10 * w, (got, want)
+
+
+def tolerances(floor=1e-12):
+    t, out = 1e-2, []
+    while t >= floor:
+        out.append(t)
+        t /= 2
+    return out
+
+
+def test_stopping_study_matches_the_oracle(vk):
+    # P3/P2 on 4x4 -> 8x8 (two levels): every tolerance of the halving sequence, both sides
+    Nc, L, k = 4, 2, 3
+    G = vk.Hierarchy(Nc, L, k)
+    H = solver.Hierarchy(Nc, L, k)
+    s = H.finest.space
+    b = fem.manufactured_rhs(s, H.finest.K)
+    assert np.linalg.norm(G.manufactured_rhs() - b) <= 1e-13 * np.linalg.norm(b)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    errs_g, errs_o = [], []
+    for tau in tolerances(1e-10)[::4]:
+        out = G.solve(bd, x, rtol=tau)
+        ref = solver.solve(H, b, tau, 100)
+        assert out["iterations"] == ref.iters, tau
+        eg, eo = G.errors(x), fem.errors(s, ref.x)
+        for a_, b_ in zip(eg, eo):
+            assert abs(a_ - b_) <= 1e-6 * b_ + 1e-12, (tau, eg, eo)   # x agrees to ~1e-12
+        errs_g.append(eg)
+        errs_o.append(eo)
+    # the velocity error settles at the discretisation error as the tolerance falls
+    h1 = [e[0] for e in errs_g]
+    assert h1[-1] <= h1[0] and abs(h1[-1] - h1[-2]) <= 1e-2 * h1[-1]
