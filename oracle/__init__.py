@@ -17,6 +17,8 @@ equations"):
                  no-slip rows (Eq. StokesDirichletNoSlip), canonical transfers (Sec. 3, "grid
                  transfer operations"), manufactured solution (Eq. model_problem), error norms (Sec. 4.4).
 * ``patches`` -- vertex / edge / cell ("composite", "topological") Vanka patches of Sec. 3.1.
+* ``quad``    -- Taylor-Hood (Q_k, Q_{k-1}) on quadrilaterals (Case 2 of Sec. 3): exact tensor-product
+                 element matrices, transfers, composite patches, manufactured data and error norms.
 * ``solver``  -- additive subspace correction (Algorithm 1), Chebyshev acceleration with the
                  [lambda/4, 1.1 lambda] interval (Sec. 3, "Relaxation"), Arnoldi eigenvalue estimate,
                  multiplicative V-cycle, bordered coarse solve, FGMRES (Sec. 3 and Sec. 4).

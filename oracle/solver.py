@@ -28,7 +28,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from . import fem, patches as patches_mod, splitmix
+from . import fem, patches as patches_mod, quad, splitmix
 
 CHEB_LO = 0.25
 CHEB_HI = 1.1
@@ -159,22 +159,28 @@ def estimate_lambda(level, level_index, seed=EIG_SEED, steps=EIG_STEPS):
 
 
 class Hierarchy:
-    """Levels 0 (coarsest, N_coarse) ... L-1 (finest, N_coarse * 2^(L-1)) for one order k."""
+    """Levels 0 (coarsest, N_coarse) ... L-1 (finest, N_coarse * 2^(L-1)) for one order k.
+
+    cell = "tri": Taylor-Hood (P_k, P_{k-1}) on triangles (Case 1 of Sec. 3); cell = "quad":
+    (Q_k, Q_{k-1}) on quadrilaterals (Case 2), with the same relaxation, cycle and Krylov method."""
 
     def __init__(self, N_coarse, nlevels, k, nu=1.0, sweeps=1, weights="plain", lambdas=None,
-                 eig_seed=EIG_SEED):
-        self.k, self.nu_visc, self.sweeps = k, nu, sweeps
+                 eig_seed=EIG_SEED, cell="tri"):
+        self.k, self.nu_visc, self.sweeps, self.cell = k, nu, sweeps, cell
+        disc = {"tri": (fem.Space, fem.assemble_full, patches_mod.build_patches, fem.prolongation),
+                "quad": (quad.QSpace, quad.assemble_full, quad.build_patches, quad.prolongation)}[cell]
+        make_space, assemble, build_patches, prolong = disc
         self.levels = []
         for l in range(nlevels):
-            space = fem.Space(N_coarse * 2 ** l, k)
-            K = fem.assemble_full(space, nu)
+            space = make_space(N_coarse * 2 ** l, k)
+            K = assemble(space, nu)
             mask = space.dirichlet_mask()
             A = fem.apply_dirichlet(K, mask)
-            plist = patches_mod.build_patches(space) if l > 0 else None
+            plist = build_patches(space) if l > 0 else None
             lev = Level(space, A, mask, plist, weights)
             lev.K = K
             if l > 0:
-                lev.P = fem.prolongation(self.levels[l - 1].space, space)
+                lev.P = prolong(self.levels[l - 1].space, space)
                 lev.R = lev.P.T.tocsr()
             self.levels.append(lev)
         c = self.levels[0]
