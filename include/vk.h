@@ -73,6 +73,11 @@ extern "C" {
 
 #define VK_BC_DIRICHLET_ALL 0  /* velocity Dirichlet condition on the whole boundary (Eq. StokesDirichletNoSlip) */
 
+#define VK_CELL_TRIANGLE 0  /* Taylor-Hood (P_k, P_{k-1}) on triangles (Case 1 of Sec. 3), 2 <= k <= 4       */
+#define VK_CELL_QUAD 1      /* Taylor-Hood (Q_k, Q_{k-1}) on quadrilaterals (Case 2 of Sec. 3), 2 <= k <= 3:
+                               the same lattice DoF layout; vertex patches, and for k = 3 edge and cell
+                               patches (Sec. 3.1); the N x N squares of the unit square           */
+
 /* Mesh hierarchy: the unit square cut into N_coarse x N_coarse squares, each split from its top-left
  * to its bottom-right corner (Sec. 4), refined uniformly nlevels-1 times (Sec. 3).  Velocity is
  * continuous P_k, pressure continuous P_{k-1} (Case 1 of Sec. 3), 2 <= k <= 4; nu is the viscosity of
@@ -94,6 +99,7 @@ typedef struct vk_problem {
   double nu;
   int32_t bc;
   double domain[4];
+  int32_t cell;        /* VK_CELL_TRIANGLE (0, the default of a zeroed struct) or VK_CELL_QUAD       */
 } vk_problem;
 
 typedef struct vk_options {

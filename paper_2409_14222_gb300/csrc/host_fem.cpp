@@ -184,10 +184,94 @@ void element_matrices(int k, int e1x, int e1y, int e2x, int e2y, double h, doubl
     }
 }
 
-void build_level(int N, int k, double nu, bool with_patches, int nthreads, HostLevel& L, bool element_data) {
+namespace {
+
+// 1-D Lagrange basis on the equispaced nodes i/deg of [0, 1] and its derivative at x.
+void lagrange_1d(int deg, double x, double* val, double* der) {
+  for (int i = 0; i <= deg; ++i) {
+    double v = 1.0, d = 0.0;
+    for (int j = 0; j <= deg; ++j) {
+      if (j == i) continue;
+      const double den = double(i - j) / deg;
+      const double f = (x - double(j) / deg) / den;
+      d = d * f + v / den;   // product rule, accumulated factor by factor
+      v *= f;
+    }
+    val[i] = v;
+    if (der) der[i] = d;
+  }
+}
+
+// Q_k / Q_{k-1} element of an axis-aligned square of side h (Case 2 of Sec. 3): local velocity node
+// (s, t) has index t (k+1) + s and basis l_s(x) l_t(y); local DoF 2a + c; Gauss-Legendre rule of k + 1
+// points per direction (exact for the degree-2k products of the bilinear forms).
+Element make_quad_element(int k, double h, double nu) {
+  Element E;
+  const int n1 = k + 1, nb = n1 * n1, nq = k * k, nv = 2 * nb;
+  E.nb = nb;
+  E.nq = nq;
+  E.A.assign(size_t(nv) * nv, 0.0);
+  E.B.assign(size_t(nq) * nv, 0.0);
+  std::vector<double> gx, gw;
+  const int q = k + 1;
+  gauss_legendre01(q, gx, gw);
+  std::vector<double> lx(n1), dx(n1), ly(n1), dy(n1), mx(k), my(k), phi(nb), gxp(nb), gyp(nb), psi(nq);
+  for (int iy = 0; iy < q; ++iy)
+    for (int ix = 0; ix < q; ++ix) {
+      lagrange_1d(k, gx[ix], lx.data(), dx.data());
+      lagrange_1d(k, gx[iy], ly.data(), dy.data());
+      lagrange_1d(k - 1, gx[ix], mx.data(), nullptr);
+      lagrange_1d(k - 1, gx[iy], my.data(), nullptr);
+      const double w = gw[ix] * gw[iy] * h * h;
+      for (int t = 0; t < n1; ++t)
+        for (int s2 = 0; s2 < n1; ++s2) {
+          phi[t * n1 + s2] = lx[s2] * ly[t];
+          gxp[t * n1 + s2] = dx[s2] * ly[t] / h;
+          gyp[t * n1 + s2] = lx[s2] * dy[t] / h;
+        }
+      for (int u = 0; u < k; ++u)
+        for (int r = 0; r < k; ++r) psi[u * k + r] = mx[r] * my[u];
+      for (int a = 0; a < nb; ++a)
+        for (int c = 0; c < 2; ++c) {
+          const double ga[2] = {gxp[a], gyp[a]};
+          for (int b = 0; b < nb; ++b)
+            for (int d = 0; d < 2; ++d) {
+              const double gb[2] = {gxp[b], gyp[b]};
+              double v2 = ga[d] * gb[c];
+              if (c == d) v2 += ga[0] * gb[0] + ga[1] * gb[1];
+              E.A[size_t(2 * a + c) * nv + 2 * b + d] += nu * w * v2;
+            }
+          for (int p = 0; p < nq; ++p) E.B[size_t(p) * nv + 2 * a + c] -= w * psi[p] * ga[c];
+        }
+    }
+  return E;
+}
+
+}  // namespace
+
+// Cell -> node maps of the structured quadrilateral mesh: cell (i, j) = j N + i; local node (s, t) of
+// Q_deg at lattice point (deg i + s, deg j + t), index t (deg+1) + s.
+void cell_maps_quad(int N, int k, std::vector<int>& cv, std::vector<int>& cp) {
+  const int n1 = k + 1, nv1 = k * N + 1, np1 = (k - 1) * N + 1, nb = n1 * n1, nq = k * k;
+  cv.resize(size_t(N) * N * nb);
+  cp.resize(size_t(N) * N * nq);
+  for (int j = 0; j < N; ++j)
+    for (int i = 0; i < N; ++i) {
+      const int c = j * N + i;
+      for (int t = 0; t < n1; ++t)
+        for (int s = 0; s < n1; ++s) cv[size_t(c) * nb + t * n1 + s] = (k * j + t) * nv1 + k * i + s;
+      for (int u = 0; u < k; ++u)
+        for (int r = 0; r < k; ++r) cp[size_t(c) * nq + u * k + r] = ((k - 1) * j + u) * np1 + (k - 1) * i + r;
+    }
+}
+
+void build_level(int N, int k, double nu, bool with_patches, int nthreads, HostLevel& L, bool element_data,
+                 int cell) {
   if (k < 2 || k > 6) throw std::runtime_error("order k must be in 2..6");
+  const bool quadc = cell == 1;
   L.N = N;
   L.k = k;
+  L.cell = cell;
   L.nv1 = k * N + 1;
   L.np1 = (k - 1) * N + 1;
   L.n_u = 2 * L.nv1 * L.nv1;
@@ -195,30 +279,22 @@ void build_level(int N, int k, double nu, bool with_patches, int nthreads, HostL
   L.ndof = L.n_u + L.n_p;
   const int nv1 = L.nv1, np1 = L.np1, n_u = L.n_u;
   const double h = 1.0 / N;
-  const auto av = node_indices(k);
-  const auto aq = node_indices(k - 1);
-  const int nb = int(av.size()), nq = int(aq.size()), nvl = 2 * nb;
-  const Element EL = make_element(k, kLower, h, nu), EU = make_element(k, kUpper, h, nu);
-  Cells cells{N};
-  const int ncell = cells.count();
+  // triangles: lower cells (index < N^2) and upper cells have their own element matrices; squares
+  // all share one
+  const int nb = quadc ? (k + 1) * (k + 1) : (k + 1) * (k + 2) / 2;
+  const int nq = quadc ? k * k : k * (k + 1) / 2, nvl = 2 * nb;
+  const Element EL = quadc ? make_quad_element(k, h, nu) : make_element(k, kLower, h, nu);
+  const Element EU = quadc ? EL : make_element(k, kUpper, h, nu);
+  const int ncell = quadc ? N * N : 2 * N * N;
+  const int nlow = quadc ? ncell : N * N;
+  L.ncell_lower = nlow;
 
   // local -> global node maps
-  std::vector<int> cv(size_t(ncell) * nb), cp(size_t(ncell) * nq);
-  for (int c = 0; c < ncell; ++c) {
-    int x0, y0;
-    const CellShape* s;
-    cells.vertex0(c, x0, y0, s);
-    for (int a = 0; a < nb; ++a) {
-      int sa = av[a][1], ta = av[a][2];
-      int xa = k * x0 + sa * s->e1x + ta * s->e2x, ya = k * y0 + sa * s->e1y + ta * s->e2y;
-      cv[size_t(c) * nb + a] = ya * nv1 + xa;
-    }
-    for (int p = 0; p < nq; ++p) {
-      int sp = aq[p][1], tp = aq[p][2];
-      int xp = (k - 1) * x0 + sp * s->e1x + tp * s->e2x, yp = (k - 1) * y0 + sp * s->e1y + tp * s->e2y;
-      cp[size_t(c) * nq + p] = yp * np1 + xp;
-    }
-  }
+  std::vector<int> cv, cp;
+  if (quadc)
+    cell_maps_quad(N, k, cv, cp);
+  else
+    cell_maps(N, k, cv, cp);
   // Dirichlet flags
   L.dir.assign(L.ndof, 0);
   for (int b = 0; b < nv1; ++b)
@@ -311,7 +387,7 @@ void build_level(int N, int k, double nu, bool with_patches, int nthreads, HostL
         const int comp = row & 1;
         for (int e : inc) {
           int c = e / nb, a = e % nb;
-          const Element& E = c < N * N ? EL : EU;
+          const Element& E = c < nlow ? EL : EU;
           const int la = 2 * a + comp;
           for (int b = 0; b < nb; ++b)
             for (int d = 0; d < 2; ++d) {
@@ -323,7 +399,7 @@ void build_level(int N, int k, double nu, bool with_patches, int nthreads, HostL
       } else {
         for (int e : inc) {
           int c = e / nq, p = e % nq;
-          const Element& E = c < N * N ? EL : EU;
+          const Element& E = c < nlow ? EL : EU;
           for (int b = 0; b < nb; ++b)
             for (int d = 0; d < 2; ++d) {
               int g = 2 * cv[size_t(c) * nb + b] + d;
@@ -364,6 +440,50 @@ void build_level(int N, int k, double nu, bool with_patches, int nthreads, HostL
   const int k1 = k - 1;
   std::vector<int> pn;
   int cl[6];
+  if (quadc) {
+    // squares (Case 2): vertex patches (star = the up-to-four cells around the vertex), then for k >= 3
+    // horizontal edges, vertical edges (the one or two adjacent cells; the k - 2 edge pressures) and
+    // cells (the (k - 2)^2 interior pressures); each family y outer, x inner
+    auto sq = [&](int i, int j) { return j * N + i; };
+    for (int j = 0; j <= N; ++j)
+      for (int i = 0; i <= N; ++i) {
+        int n = 0;
+        if (i > 0 && j > 0) cl[n++] = sq(i - 1, j - 1);
+        if (i < N && j > 0) cl[n++] = sq(i, j - 1);
+        if (i > 0 && j < N) cl[n++] = sq(i - 1, j);
+        if (i < N && j < N) cl[n++] = sq(i, j);
+        pn.assign(1, (k1 * j) * np1 + k1 * i);
+        emit(0, cl, n, pn);
+      }
+    if (k >= 3) {
+      for (int j = 0; j <= N; ++j)
+        for (int i = 0; i < N; ++i) {
+          int n = 0;
+          if (j > 0) cl[n++] = sq(i, j - 1);
+          if (j < N) cl[n++] = sq(i, j);
+          pn.clear();
+          for (int t = 1; t <= k - 2; ++t) pn.push_back((k1 * j) * np1 + k1 * i + t);
+          emit(1, cl, n, pn);
+        }
+      for (int j = 0; j < N; ++j)
+        for (int i = 0; i <= N; ++i) {
+          int n = 0;
+          if (i > 0) cl[n++] = sq(i - 1, j);
+          if (i < N) cl[n++] = sq(i, j);
+          pn.clear();
+          for (int t = 1; t <= k - 2; ++t) pn.push_back((k1 * j + t) * np1 + k1 * i);
+          emit(1, cl, n, pn);
+        }
+      for (int j = 0; j < N; ++j)
+        for (int i = 0; i < N; ++i) {
+          cl[0] = sq(i, j);
+          pn.clear();
+          for (int u = 1; u <= k - 2; ++u)
+            for (int r = 1; r <= k - 2; ++r) pn.push_back((k1 * j + u) * np1 + k1 * i + r);
+          emit(2, cl, 1, pn);
+        }
+    }
+  } else {
   // vertices: star = the up-to-six incident cells
   for (int j = 0; j <= N; ++j)
     for (int i = 0; i <= N; ++i) {
@@ -420,6 +540,7 @@ void build_level(int N, int k, double nu, bool with_patches, int nthreads, HostL
           emit(2, cl, 1, pn);
         }
   }
+  }  // triangles
   if (!element_data) return;
   // ---- element data of the matrix-free patch assembly -------------------------------------------
   const int nloc = nvl + nq;
@@ -475,14 +596,44 @@ void build_transfer(const HostLevel& c, HostLevel& f) {
   // P = diag(P^V, P^Q): each fine node is located in a coarse cell; coarse basis functions are
   // evaluated there exactly: barycentric coordinates are m_i / (2 deg) with integer m_i, so
   // phi_alpha = prod_i prod_{j < alpha_i} (m_i - 2j) / (2 (j + 1)), an exact ratio of integers.
-  if (f.N != 2 * c.N || f.k != c.k) throw std::runtime_error("transfer: levels not nested");
+  // Squares: the basis is a tensor product, so P^V and P^Q are tensor products of the 1-D
+  // interpolations l_s(m / (2 deg)) = prod_{j != s} (m - 2 j) / (2 (s - j)), also exact ratios.
+  if (f.N != 2 * c.N || f.k != c.k || f.cell != c.cell) throw std::runtime_error("transfer: levels not nested");
   const int Nc = c.N;
   struct Trip {
     int r, c;
     double v;
   };
   std::vector<Trip> t;
+  auto block_quad = [&](int deg, int nf1, int nc1, int offf, int offc, int stride) {
+    const int two = 2 * deg;
+    std::vector<std::vector<std::pair<int, double>>> w1(nf1);   // 1-D weights of fine node a
+    for (int a = 0; a < nf1; ++a) {
+      const int i = std::min(a / two, Nc - 1), m = a - two * i;
+      for (int s2 = 0; s2 <= deg; ++s2) {
+        int64_t num = 1, den = 1;
+        for (int j = 0; j <= deg; ++j)
+          if (j != s2) {
+            num *= (m - 2 * j);
+            den *= 2 * (s2 - j);
+          }
+        if (num != 0) w1[a].push_back({deg * i + s2, double(num) / double(den)});
+      }
+    }
+    for (int b = 0; b < nf1; ++b)
+      for (int a = 0; a < nf1; ++a)
+        for (const auto& wy : w1[b])
+          for (const auto& wx : w1[a]) {
+            const double v = wx.second * wy.second;
+            const int cn = wy.first * nc1 + wx.first, fn = b * nf1 + a;
+            for (int d = 0; d < stride; ++d) t.push_back({offf + stride * fn + d, offc + stride * cn + d, v});
+          }
+  };
   auto block = [&](int deg, int nf1, int nc1, int offf, int offc, int stride) {
+    if (f.cell == 1) {
+      block_quad(deg, nf1, nc1, offf, offc, stride);
+      return;
+    }
     const auto al = node_indices(deg);
     const int two = 2 * deg;
     for (int b = 0; b < nf1; ++b)

@@ -374,7 +374,9 @@ std::vector<vk::gpu::ApplySched> apply_candidates() {
 
 void validate(const vk_problem* p, const vk_options* o) {
   if (!p || !o) raise(VK_ERR_ARG, "null problem or options");
-  if (p->k < 2 || p->k > 4) raise(VK_ERR_ARG, "order k must be 2, 3 or 4");
+  if (p->cell != VK_CELL_TRIANGLE && p->cell != VK_CELL_QUAD) raise(VK_ERR_ARG, "cell must be VK_CELL_TRIANGLE or VK_CELL_QUAD");
+  if (p->k < 2 || p->k > (p->cell == VK_CELL_QUAD ? 3 : 4))
+    raise(VK_ERR_ARG, p->cell == VK_CELL_QUAD ? "order k must be 2 or 3 on quadrilaterals" : "order k must be 2, 3 or 4");
   if (p->N_coarse < 1 || p->nlevels < 1 || p->nlevels > 12) raise(VK_ERR_ARG, "bad mesh hierarchy");
   const int64_t Nf = int64_t(p->N_coarse) << (p->nlevels - 1);
   if (Nf * p->k > 8192) raise(VK_ERR_ARG, "finest mesh too large for 32-bit indices");
@@ -417,7 +419,7 @@ void build_host(vk_hierarchy* h) {
   h->host.resize(L);
   for (int l = 0; l < L; ++l) {
     vk::build_level(h->prob.N_coarse << l, h->prob.k, h->prob.nu, l > 0, nthreads, h->host[l],
-                    l > 0 && h->opt.patch_assembly == VK_ASSEMBLY_MATRIX_FREE);
+                    l > 0 && h->opt.patch_assembly == VK_ASSEMBLY_MATRIX_FREE, h->prob.cell);
     if (l > 0) vk::build_transfer(h->host[l - 1], h->host[l]);
   }
 }
@@ -642,7 +644,7 @@ void allocate_device(vk_hierarchy* h) {
       D.delta = m.get_n<double>(G.nslots);
       if (h->opt.patch_assembly == VK_ASSEMBLY_MATRIX_FREE) {
         D.pe.nloc = H.nloc;
-        D.pe.ncell_lower = H.N * H.N;
+        D.pe.ncell_lower = H.ncell_lower;
         D.pe.cell_dofs = m.upload(H.cell_dofs);
         D.pe.kel = m.upload(H.kel);
         D.pe.cell_ptr = m.upload(H.patch_cell_ptr);
@@ -1809,6 +1811,7 @@ int vk_stats_read(vk_hierarchy* h, vk_stats* out) {
 int vk_manufactured_rhs(const vk_hierarchy* h, double* b_host) {
   return guard([&] {
     if (!h || !b_host) raise(VK_ERR_ARG, "null argument");
+    if (h->prob.cell != VK_CELL_TRIANGLE) raise(VK_ERR_ARG, "the manufactured data is built for triangles only");
     std::vector<double> b;
     vk::manufactured_rhs(h->host.back(), h->prob.nu, b);
     std::copy(b.begin(), b.end(), b_host);
@@ -1820,6 +1823,7 @@ int vk_errors(vk_hierarchy* h, const double* x, double* errs, void* stream) {
   return guard([&] {
     check_device(h);
     if (!x || !errs) raise(VK_ERR_ARG, "null argument");
+    if (h->prob.cell != VK_CELL_TRIANGLE) raise(VK_ERR_ARG, "the error norms are integrated on triangles only");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const vk::HostLevel& F = h->host.back();
     std::vector<int> cv, cp;

@@ -21,6 +21,8 @@ struct HostCsr {
 // One mesh level of the Taylor-Hood (P_k, P_{k-1}) discretization on the structured triangle mesh.
 struct HostLevel {
   int N = 0, k = 0;
+  int cell = 0;             // 0: triangles (P_k, P_{k-1}); 1: squares (Q_k, Q_{k-1})
+  int ncell_lower = 0;      // cells below this index use the first element matrix (all squares do)
   int nv1 = 0, np1 = 0;     // lattice sizes per side: k*N+1 (velocity), (k-1)*N+1 (pressure)
   int n_u = 0, n_p = 0, ndof = 0;
   HostCsr A;                // saddle-point matrix with Dirichlet identity rows / zero columns
@@ -40,7 +42,8 @@ struct HostLevel {
 };
 
 // host_fem.cpp
-void build_level(int N, int k, double nu, bool with_patches, int nthreads, HostLevel& L, bool element_data = false);
+void build_level(int N, int k, double nu, bool with_patches, int nthreads, HostLevel& L, bool element_data = false,
+                 int cell = 0);
 void build_transfer(const HostLevel& coarse, HostLevel& fine);
 // Element matrices of one cell shape, for tests and the manufactured load (row-major).
 void element_matrices(int k, int e1x, int e1y, int e2x, int e2y, double h, double nu,
@@ -48,6 +51,7 @@ void element_matrices(int k, int e1x, int e1y, int e2x, int e2y, double h, doubl
 void gauss_legendre01(int q, std::vector<double>& x, std::vector<double>& w);
 
 void cell_maps(int N, int k, std::vector<int>& cv, std::vector<int>& cp);
+void cell_maps_quad(int N, int k, std::vector<int>& cv, std::vector<int>& cp);
 void reference_tables(int k, int q, std::vector<double>& xi, std::vector<double>& eta, std::vector<double>& w,
                       std::vector<double>& phi, std::vector<double>& dxi, std::vector<double>& deta,
                       std::vector<double>& psi);

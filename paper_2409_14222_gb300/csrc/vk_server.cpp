@@ -37,15 +37,15 @@ double ms_since(Clock::time_point t0, Clock::time_point t1) {
   return std::chrono::duration<double, std::milli>(t1 - t0).count();
 }
 
-// N_coarse, nlevels, k, bit pattern of nu (two requests share a hierarchy only if their matrices are
-// the same; bc and domain have a single accepted value each, checked at submission)
-using Key = std::tuple<int, int, int, uint64_t>;
+// N_coarse, nlevels, k, cell type, bit pattern of nu (two requests share a hierarchy only if their
+// matrices are the same; bc and domain have a single accepted value each, checked at submission)
+using Key = std::tuple<int, int, int, int, uint64_t>;
 
 Key key_of(const vk_problem& p) {
   uint64_t bits = 0;
   static_assert(sizeof(bits) == sizeof(p.nu), "nu is a double");
   std::memcpy(&bits, &p.nu, sizeof(bits));
-  return Key{p.N_coarse, p.nlevels, p.k, bits};
+  return Key{p.N_coarse, p.nlevels, p.k, p.cell, bits};
 }
 
 struct Instance {

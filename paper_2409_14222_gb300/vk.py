@@ -22,6 +22,7 @@ VK_ERR_CUDA = 7
 VK_ERR_INTERNAL = 8
 VK_ERR_CANCELLED = 9
 VK_BC_DIRICHLET_ALL = 0
+VK_CELL_TRIANGLE, VK_CELL_QUAD = 0, 1
 VK_SERVE_GROUP, VK_SERVE_STREAMS = 0, 1
 VK_ASSEMBLY_MATRIX_FULL, VK_ASSEMBLY_MATRIX_FREE = 0, 1
 
@@ -59,11 +60,12 @@ class VkError(RuntimeError):
 
 class vk_problem(ctypes.Structure):
     _fields_ = [("N_coarse", ctypes.c_int32), ("nlevels", ctypes.c_int32), ("k", ctypes.c_int32),
-                ("nu", ctypes.c_double), ("bc", ctypes.c_int32), ("domain", ctypes.c_double * 4)]
+                ("nu", ctypes.c_double), ("bc", ctypes.c_int32), ("domain", ctypes.c_double * 4),
+                ("cell", ctypes.c_int32)]
 
 
-def make_problem(N_coarse, nlevels, k, nu=1.0, bc=VK_BC_DIRICHLET_ALL, domain=(0.0, 1.0, 0.0, 1.0)):
-    return vk_problem(N_coarse, nlevels, k, nu, bc, (ctypes.c_double * 4)(*domain))
+def make_problem(N_coarse, nlevels, k, nu=1.0, bc=VK_BC_DIRICHLET_ALL, domain=(0.0, 1.0, 0.0, 1.0), cell=0):
+    return vk_problem(N_coarse, nlevels, k, nu, bc, (ctypes.c_double * 4)(*domain), cell)
 
 
 class vk_options(ctypes.Structure):
@@ -259,8 +261,8 @@ class Hierarchy:
     """A set-up multigrid hierarchy (vk_setup).  Methods mirror the C ABI names."""
 
     def __init__(self, N_coarse, nlevels, k, nu=1.0, options=None, device="cuda", host_only=False,
-                 lambdas=None, stream=None, allocator="torch"):
-        self.problem = make_problem(N_coarse, nlevels, k, nu)
+                 lambdas=None, stream=None, allocator="torch", cell=VK_CELL_TRIANGLE):
+        self.problem = make_problem(N_coarse, nlevels, k, nu, cell=cell)
         self.options = options if options is not None else default_options()
         if host_only:
             self.options.host_only = 1
@@ -514,8 +516,8 @@ class Group:
             pass
 
 
-def footprint(N_coarse, nlevels, k, nu=1.0, options=None):
-    p = make_problem(N_coarse, nlevels, k, nu)
+def footprint(N_coarse, nlevels, k, nu=1.0, options=None, cell=VK_CELL_TRIANGLE):
+    p = make_problem(N_coarse, nlevels, k, nu, cell=cell)
     o = options if options is not None else default_options()
     b = ctypes.c_size_t()
     check(lib().vk_footprint(ctypes.byref(p), ctypes.byref(o), ctypes.byref(b)))

@@ -215,3 +215,35 @@ def test_manufactured_rhs_equals_the_oracle(vk, N, k):
     assert np.linalg.norm(got - want) <= 1e-13 * np.linalg.norm(want)
     mask = s.dirichlet_mask()
     assert np.array_equal(got[mask] == 0.0, want[mask] == 0.0)
+
+
+@pytest.mark.parametrize("Nc,L,k", [(2, 2, 2), (2, 3, 2), (2, 2, 3), (1, 3, 3)])
+def test_quad_host_setup_equals_oracle(vk, Nc, L, k):
+    # Taylor-Hood Q_k / Q_{k-1} (Case 2 of Sec. 3): the library's element matrices (FP64 Gauss-Legendre),
+    # assembly, tensor-product transfers and quadrilateral patches against the oracle's exact ones
+    from oracle import quad
+    h = vk.Hierarchy(Nc, L, k, nu=0.7, host_only=True, cell=vk.vk.VK_CELL_QUAD)
+    for l in range(L):
+        s = quad.QSpace(Nc * 2 ** l, k)
+        Ao = fem.apply_dirichlet(quad.assemble_full(s, 0.7), s.dirichlet_mask())
+        A = _csr(vk, h, l, vk.VK_CSR_A)
+        assert A.shape == Ao.shape
+        assert abs(A - Ao).max() <= 1e-14 * abs(Ao).max()
+        assert np.array_equal(h.export_dirichlet(l), s.dirichlet_mask())
+        if l > 0:
+            Po = quad.prolongation(quad.QSpace(Nc * 2 ** (l - 1), k), s)
+            assert abs(_csr(vk, h, l, vk.VK_CSR_P) - Po).max() == 0.0
+            assert abs(_csr(vk, h, l, vk.VK_CSR_R) - Po.T).max() == 0.0
+            ptr, dofs, kind = h.export_patches(l)
+            op = quad.build_patches(s)
+            assert len(ptr) - 1 == len(op)
+            for i, (knd, ent, d) in enumerate(op):
+                assert np.array_equal(dofs[ptr[i]:ptr[i + 1]], d), (l, i)
+                assert kind[i] == {"vertex": 0, "edge": 1, "cell": 2}[knd]
+
+
+def test_quad_order_bound(vk):
+    with pytest.raises(vk.VkError):
+        vk.Hierarchy(2, 2, 4, host_only=True, cell=vk.vk.VK_CELL_QUAD)
+    with pytest.raises(vk.VkError):
+        vk.Hierarchy(2, 2, 2, host_only=True, cell=2)
