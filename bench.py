@@ -675,7 +675,7 @@ def serve_pass(vk, srv, reqs, arrivals):
     for i in range(len(reqs)):
         while tickets[i] is None:
             time.sleep(1e-4)
-        x, res = srv.wait(tickets[i])
+        x, res = srv.wait(tickets[i], timeout_ms=600000)
         if res["status"] not in (0, 5):
             raise RuntimeError(f"request {i} failed: {res}")
         lat.append(res["latency_ms"])

@@ -101,9 +101,9 @@ def test_server_cancels_a_queued_request(vk):
         t1 = srv.submit(*key, si.rhs_normal(n, 0))
         t2 = srv.submit(*key, si.rhs_normal(n, 1))
         srv.cancel(t2)
-        x2, r2 = srv.wait(t2)
+        x2, r2 = srv.wait(t2, timeout_ms=300000)
         assert r2["status"] == vk.vk.VK_ERR_CANCELLED and r2["iterations"] == 0
-        x1, r1 = srv.wait(t1)
+        x1, r1 = srv.wait(t1, timeout_ms=300000)
         assert r1["status"] == 0 and r1["converged"]
         with pytest.raises(vk.VkError):
             srv.cancel(t1)                         # finished: not cancellable
@@ -122,8 +122,8 @@ def test_server_keys_hierarchies_by_viscosity(vk):
     try:
         ta = srv.submit(*key, b, rtol=1e-10, nu=1.0)
         tb = srv.submit(*key, b, rtol=1e-10, nu=0.25)
-        xa, ra = srv.wait(ta)
-        xb, rb = srv.wait(tb)
+        xa, ra = srv.wait(ta, timeout_ms=300000)
+        xb, rb = srv.wait(tb, timeout_ms=300000)
         assert srv.stats()["builds"] == 2
     finally:
         srv.close()
