@@ -486,7 +486,8 @@ int vk_manufactured_rhs(const vk_hierarchy* h, double* b_host);
  * problem, the quantities of the stopping-criterion study of Sec. 4.4: errs[0] = relative H^1 velocity
  * error (||u - u_h||_{H^1} / ||u||_{H^1}), errs[1] = relative L^2 velocity error, errs[2] = absolute
  * L^2 pressure error after removing the pressure's mean (p = 0).  Integrated on the device cell by cell
- * with a collapsed Gauss-Legendre rule of k + 6 points per direction, summed in a fixed order.  errs is
+ * with a collapsed (triangles) or tensor (squares) Gauss-Legendre rule of k + 6 points per direction,
+ * summed in a fixed order.  errs is
  * a host array of 3 doubles; the call allocates and frees its tables and synchronises `stream`. */
 int vk_errors(vk_hierarchy* h, const double* x_dev, double* errs, void* stream);
 

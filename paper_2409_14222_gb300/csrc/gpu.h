@@ -275,6 +275,7 @@ double fma_rate_tflops(bool fp64, void* scratch, cudaStream_t s);
 // ---- discretisation errors (kernels_fem.cu) --------------------------------------------------------
 struct FemErrArgs {
   int N = 0, nb = 0, nq = 0, Q = 0, n_u = 0;
+  int quad = 0;                 // 1: the N x N squares (Q_k), 0: the 2 N^2 triangles (P_k)
   double h = 0.0;
   const int* cv = nullptr;      // [cell][nb] velocity nodes
   const int* cp = nullptr;      // [cell][nq] pressure nodes

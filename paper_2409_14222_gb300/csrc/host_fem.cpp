@@ -827,3 +827,100 @@ void manufactured_rhs(const HostLevel& L, double nu, std::vector<double>& b) {
 }
 
 }  // namespace vk
+
+namespace vk {
+
+// Tensor Gauss-Legendre rule of q points per direction on the unit reference square and the Q_k /
+// Q_{k-1} basis at its points (local node (s, t) -> index t (k+1) + s; pressure (r, u) -> u k + r).
+void reference_tables_quad(int k, int q, std::vector<double>& xi, std::vector<double>& eta, std::vector<double>& w,
+                           std::vector<double>& phi, std::vector<double>& dxi, std::vector<double>& deta,
+                           std::vector<double>& psi) {
+  const int n1 = k + 1, nb = n1 * n1, nq = k * k, Q = q * q;
+  std::vector<double> gx, gw;
+  gauss_legendre01(q, gx, gw);
+  xi.resize(Q);
+  eta.resize(Q);
+  w.resize(Q);
+  phi.resize(size_t(Q) * nb);
+  dxi.resize(size_t(Q) * nb);
+  deta.resize(size_t(Q) * nb);
+  psi.resize(size_t(Q) * nq);
+  std::vector<double> lx(n1), dx(n1), ly(n1), dy(n1), mx(k), my(k);
+  for (int iy = 0; iy < q; ++iy)
+    for (int ix = 0; ix < q; ++ix) {
+      const int t = iy * q + ix;
+      xi[t] = gx[ix];
+      eta[t] = gx[iy];
+      w[t] = gw[ix] * gw[iy];
+      lagrange_1d(k, gx[ix], lx.data(), dx.data());
+      lagrange_1d(k, gx[iy], ly.data(), dy.data());
+      lagrange_1d(k - 1, gx[ix], mx.data(), nullptr);
+      lagrange_1d(k - 1, gx[iy], my.data(), nullptr);
+      for (int b = 0; b < n1; ++b)
+        for (int a = 0; a < n1; ++a) {
+          phi[size_t(t) * nb + b * n1 + a] = lx[a] * ly[b];
+          dxi[size_t(t) * nb + b * n1 + a] = dx[a] * ly[b];
+          deta[size_t(t) * nb + b * n1 + a] = lx[a] * dy[b];
+        }
+      for (int u = 0; u < k; ++u)
+        for (int r = 0; r < k; ++r) psi[size_t(t) * nq + u * k + r] = mx[r] * my[u];
+    }
+}
+
+// The manufactured right-hand side (Eq. model_problem) for Q_k / Q_{k-1} on the N x N squares: tensor
+// Gauss-Legendre rule of k + 5 points per direction, boundary data lifted as for the triangles.
+void manufactured_rhs_quad(const HostLevel& L, double nu, std::vector<double>& b) {
+  const int N = L.N, k = L.k, nv1 = L.nv1, n_u = L.n_u;
+  const double h = 1.0 / N, pi = M_PI;
+  std::vector<int> cv, cp;
+  cell_maps_quad(N, k, cv, cp);
+  const int nb = (k + 1) * (k + 1), nq = k * k, nvl = 2 * nb;
+  std::vector<double> xi, eta, w, phi, dxi, deta, psi;
+  reference_tables_quad(k, k + 5, xi, eta, w, phi, dxi, deta, psi);
+  const int Q = int(w.size());
+  const Element E = make_quad_element(k, h, nu);
+  b.assign(L.ndof, 0.0);
+  std::vector<double> g(L.ndof, 0.0);
+  for (int node = 0; node < nv1 * nv1; ++node)
+    if (L.dir[2 * node]) {
+      const double X = double(node % nv1) / (k * N), Y = double(node / nv1) / (k * N);
+      g[2 * node] = std::sin(pi * X) * std::cos(pi * Y);
+      g[2 * node + 1] = -std::cos(pi * X) * std::sin(pi * Y);
+    }
+  for (int c = 0; c < N * N; ++c) {
+    const int i = c % N, j = c / N;
+    const int* nodes = &cv[size_t(c) * nb];
+    for (int t = 0; t < Q; ++t) {
+      const double X = h * (i + xi[t]), Y = h * (j + eta[t]);
+      const double f1 = 2 * pi * pi * nu * std::sin(pi * X) * std::cos(pi * Y);
+      const double f2 = -2 * pi * pi * nu * std::cos(pi * X) * std::sin(pi * Y);
+      const double wt = w[t] * h * h;
+      for (int a = 0; a < nb; ++a) {
+        b[2 * nodes[a]] += wt * f1 * phi[size_t(t) * nb + a];
+        b[2 * nodes[a] + 1] += wt * f2 * phi[size_t(t) * nb + a];
+      }
+    }
+    double ge[64];
+    bool any = false;
+    for (int a = 0; a < nb; ++a)
+      for (int d = 0; d < 2; ++d) {
+        ge[2 * a + d] = g[2 * nodes[a] + d];
+        any = any || ge[2 * a + d] != 0.0;
+      }
+    if (!any) continue;
+    for (int la = 0; la < nvl; ++la) {
+      double acc = 0.0;
+      for (int lb = 0; lb < nvl; ++lb) acc += E.A[size_t(la) * nvl + lb] * ge[lb];
+      b[2 * nodes[la / 2] + (la & 1)] -= acc;
+    }
+    for (int p = 0; p < nq; ++p) {
+      double acc = 0.0;
+      for (int lb = 0; lb < nvl; ++lb) acc += E.B[size_t(p) * nvl + lb] * ge[lb];
+      b[n_u + cp[size_t(c) * nq + p]] -= acc;
+    }
+  }
+  for (int i = 0; i < n_u; ++i)
+    if (L.dir[i]) b[i] = g[i];
+}
+
+}  // namespace vk

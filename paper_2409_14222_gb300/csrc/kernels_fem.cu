@@ -1,6 +1,7 @@
 // Discretisation errors of a solution of the manufactured problem (Eq. model_problem, Sec. 4.4):
 // relative H^1 and L^2 errors of the velocity and the L^2 error of the pressure after removing its
-// mean, integrated cell by cell with a collapsed Gauss-Legendre rule on the reference triangle.
+// mean, integrated cell by cell with a collapsed Gauss-Legendre rule on the reference triangle or a
+// tensor Gauss-Legendre rule on the reference square.
 // One thread per cell over a fixed grid, fixed reduction tree: the sums do not depend on scheduling.
 #include "gpu.h"
 
@@ -17,13 +18,14 @@ __global__ void __launch_bounds__(kFemThreads) k_errors(FemErrArgs a, double* __
   double acc[kFemSums];
 #pragma unroll
   for (int i = 0; i < kFemSums; ++i) acc[i] = 0.0;
-  const int ncell = 2 * a.N * a.N;
+  const int ncell = (a.quad ? 1 : 2) * a.N * a.N;
   const double pi = 3.14159265358979323846;
   for (int c = blockIdx.x * kFemThreads + threadIdx.x; c < ncell; c += kFemBlocks * kFemThreads) {
     // vertex v0 and edge vectors of the cell (units of h): lower (i,j),(i+1,j),(i,j+1);
     // upper (i+1,j),(i+1,j+1),(i,j+1)
+    // squares: cell (i, j) = j N + i, x = h (i + xi), y = h (j + eta)
     const int q = c % (a.N * a.N), i = q % a.N, j = q / a.N;
-    const bool up = c >= a.N * a.N;
+    const bool up = !a.quad && c >= a.N * a.N;
     const double x0 = a.h * (up ? i + 1 : i), y0 = a.h * j;
     const double J00 = up ? 0.0 : a.h, J01 = up ? -a.h : 0.0, J10 = up ? a.h : 0.0, J11 = a.h;
     const double det = J00 * J11 - J01 * J10, adet = fabs(det);

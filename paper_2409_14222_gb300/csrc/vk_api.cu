@@ -1811,9 +1811,11 @@ int vk_stats_read(vk_hierarchy* h, vk_stats* out) {
 int vk_manufactured_rhs(const vk_hierarchy* h, double* b_host) {
   return guard([&] {
     if (!h || !b_host) raise(VK_ERR_ARG, "null argument");
-    if (h->prob.cell != VK_CELL_TRIANGLE) raise(VK_ERR_ARG, "the manufactured data is built for triangles only");
     std::vector<double> b;
-    vk::manufactured_rhs(h->host.back(), h->prob.nu, b);
+    if (h->prob.cell == VK_CELL_QUAD)
+      vk::manufactured_rhs_quad(h->host.back(), h->prob.nu, b);
+    else
+      vk::manufactured_rhs(h->host.back(), h->prob.nu, b);
     std::copy(b.begin(), b.end(), b_host);
     return VK_OK;
   });
@@ -1823,13 +1825,18 @@ int vk_errors(vk_hierarchy* h, const double* x, double* errs, void* stream) {
   return guard([&] {
     check_device(h);
     if (!x || !errs) raise(VK_ERR_ARG, "null argument");
-    if (h->prob.cell != VK_CELL_TRIANGLE) raise(VK_ERR_ARG, "the error norms are integrated on triangles only");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const vk::HostLevel& F = h->host.back();
+    const bool quadc = h->prob.cell == VK_CELL_QUAD;
     std::vector<int> cv, cp;
-    vk::cell_maps(F.N, F.k, cv, cp);
     std::vector<double> xi, eta, w, phi, dxi, deta, psi;
-    vk::reference_tables(F.k, F.k + 6, xi, eta, w, phi, dxi, deta, psi);
+    if (quadc) {
+      vk::cell_maps_quad(F.N, F.k, cv, cp);
+      vk::reference_tables_quad(F.k, F.k + 6, xi, eta, w, phi, dxi, deta, psi);
+    } else {
+      vk::cell_maps(F.N, F.k, cv, cp);
+      vk::reference_tables(F.k, F.k + 6, xi, eta, w, phi, dxi, deta, psi);
+    }
     std::vector<void*> bufs;
     auto up = [&](const auto& v) {
       using T = typename std::decay_t<decltype(v)>::value_type;
@@ -1843,8 +1850,9 @@ int vk_errors(vk_hierarchy* h, const double* x, double* errs, void* stream) {
     try {
       vk::gpu::FemErrArgs a;
       a.N = F.N;
-      a.nb = (F.k + 1) * (F.k + 2) / 2;
-      a.nq = F.k * (F.k + 1) / 2;
+      a.quad = quadc ? 1 : 0;
+      a.nb = quadc ? (F.k + 1) * (F.k + 1) : (F.k + 1) * (F.k + 2) / 2;
+      a.nq = quadc ? F.k * F.k : F.k * (F.k + 1) / 2;
       a.Q = int(w.size());
       a.n_u = F.n_u;
       a.h = 1.0 / F.N;

@@ -56,6 +56,10 @@ void reference_tables(int k, int q, std::vector<double>& xi, std::vector<double>
                       std::vector<double>& phi, std::vector<double>& dxi, std::vector<double>& deta,
                       std::vector<double>& psi);
 void manufactured_rhs(const HostLevel& L, double nu, std::vector<double>& b);
+void reference_tables_quad(int k, int q, std::vector<double>& xi, std::vector<double>& eta, std::vector<double>& w,
+                           std::vector<double>& phi, std::vector<double>& dxi, std::vector<double>& deta,
+                           std::vector<double>& psi);
+void manufactured_rhs_quad(const HostLevel& L, double nu, std::vector<double>& b);
 
 // host_eig.cpp: eigenvalues of a small real upper-Hessenberg matrix (row-major m x m).
 int hessenberg_eigenvalues(int m, const double* H, double* re, double* im);

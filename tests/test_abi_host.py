@@ -247,3 +247,12 @@ def test_quad_order_bound(vk):
         vk.Hierarchy(2, 2, 4, host_only=True, cell=vk.vk.VK_CELL_QUAD)
     with pytest.raises(vk.VkError):
         vk.Hierarchy(2, 2, 2, host_only=True, cell=2)
+
+
+@pytest.mark.parametrize("N,k", [(4, 2), (2, 3)])
+def test_quad_manufactured_rhs_equals_the_oracle(vk, N, k):
+    from oracle import quad
+    h = vk.Hierarchy(N, 1, k, host_only=True, cell=vk.vk.VK_CELL_QUAD)
+    s = quad.QSpace(N, k)
+    want = quad.manufactured_rhs(s, quad.assemble_full(s))
+    assert np.linalg.norm(h.manufactured_rhs() - want) <= 1e-13 * np.linalg.norm(want)

@@ -26,18 +26,21 @@ def vk():
     return vk
 
 
-@pytest.mark.parametrize("N,k", [(4, 2), (8, 2), (4, 3), (2, 4)])
-def test_error_norms_equal_the_oracle(vk, N, k):
-    G = vk.Hierarchy(N, 1, k)
-    s = fem.Space(N, k)
-    K = fem.assemble_full(s)
+@pytest.mark.parametrize("N,k,cell", [(4, 2, "tri"), (8, 2, "tri"), (4, 3, "tri"), (2, 4, "tri"), (4, 2, "quad"),
+                                       (2, 3, "quad")])
+def test_error_norms_equal_the_oracle(vk, N, k, cell):
+    from oracle import quad
+    G = vk.Hierarchy(N, 1, k, cell=vk.vk.VK_CELL_QUAD if cell == "quad" else vk.vk.VK_CELL_TRIANGLE)
+    mod = quad if cell == "quad" else fem
+    s = quad.QSpace(N, k) if cell == "quad" else fem.Space(N, k)
+    K = mod.assemble_full(s)
     A = fem.apply_dirichlet(K, s.dirichlet_mask())
-    b = solver.project(s, fem.manufactured_rhs(s, K))
+    b = solver.project(s, mod.manufactured_rhs(s, K))
     xd = solver.project(s, solver.direct_solve(A, s.nullspace(), b))
     rng = np.random.default_rng(81)
     for x in (xd, xd + 1e-3 * rng.standard_normal(len(xd))):
         got = G.errors(torch.from_numpy(x).cuda())
-        want = fem.errors(s, x)
+        want = mod.errors(s, x)
         for g, w in zip(got, want):
             assert abs(g - w) <= 1e-10 * w, (got, want)
 
