@@ -74,9 +74,10 @@ extern "C" {
 #define VK_BC_DIRICHLET_ALL 0  /* velocity Dirichlet condition on the whole boundary (Eq. StokesDirichletNoSlip) */
 
 #define VK_CELL_TRIANGLE 0  /* Taylor-Hood (P_k, P_{k-1}) on triangles (Case 1 of Sec. 3), 2 <= k <= 4       */
-#define VK_CELL_QUAD 1      /* Taylor-Hood (Q_k, Q_{k-1}) on quadrilaterals (Case 2 of Sec. 3), 2 <= k <= 3:
-                               the same lattice DoF layout; vertex patches, and for k = 3 edge and cell
-                               patches (Sec. 3.1); the N x N squares of the unit square           */
+#define VK_CELL_QUAD 1      /* Taylor-Hood (Q_k, Q_{k-1}) on quadrilaterals (Case 2 of Sec. 3), 2 <= k <= 4:
+                               the same lattice DoF layout; vertex patches, and for k >= 3 edge and
+                               cell patches (Sec. 3.1; interior sizes 51 / 99, 57, 33 / 163, 92, 54 for
+                               k = 2 / 3 / 4); the N x N squares of the unit square                */
 
 /* Mesh hierarchy: the unit square cut into N_coarse x N_coarse squares, each split from its top-left
  * to its bottom-right corner (Sec. 4), refined uniformly nlevels-1 times (Sec. 3).  Velocity is
@@ -212,7 +213,7 @@ int vk_lambda(const vk_hierarchy* h, int level, double* lambda);
 /* Launch shape of the patch application on level `level` (>= 1), chosen at setup.  Patches of
  * uneven size (boundary and interior vertex patches, edge and cell patches for k >= 3: Sec. 3.1) are
  * applied either in one launch (split = 0; each warp dispatches on its patch's size) or in one launch
- * per size class of ceil(n/4) (1-4, 5-10, 11-19, 20-32; split = 1); threads per block 128 or 256;
+ * per size class of ceil(n/4) (1-4, 5-10, 11-19, 20-32, 33-42; split = 1); threads per block 128 or 256;
  * per_sm = 0 launches one warp per patch, per_sm > 0 a persistent grid of per_sm blocks per SM.
  * Candidate i is split = i / 6, threads = (i / 3) % 2 ? 256 : 128, per_sm = {0, 4, 8}[i % 3]
  * (*ncand = 12 of them).  cand_us (host, *ncand doubles, may be NULL) receives each candidate's best
@@ -407,10 +408,13 @@ void vk_group_destroy(vk_group* g);
  * Admission is by device footprint (vk_footprint): when memory_budget would be exceeded, idle
  * hierarchies are destroyed least recently used first, and a request waits while the memory it needs
  * is held by running solves; a request larger than the whole budget fails with VK_ERR_NO_MEMORY.
- *   VK_SERVE_GROUP (default): one engine thread advances every admitted request together as members
- *     of one group solve (vk_group_*): each FGMRES iteration of all of them is one launch per stage,
- *     whatever their sizes and orders, and requests join and leave between iterations (continuous
- *     batching).  At most slots <= 24 requests are in flight.
+ *   VK_SERVE_GROUP (default): engine threads advance the admitted requests together as members of
+ *     group solves (vk_group_*): each FGMRES iteration of all members of a group is one launch per
+ *     stage, whatever their sizes and orders, and requests join and leave between iterations
+ *     (continuous batching).  There is one group (engine thread and CUDA stream) per size bucket of the
+ *     finest level (below 2^16, below 2^19 and from 2^19 DoFs), so small requests share launches with
+ *     each other without waiting on the iterations of large ones.  At most slots <= 24 requests are in
+ *     flight.
  *   VK_SERVE_STREAMS: each slot solves its request alone (vk_solve_host) on its own CUDA stream, so
  *     the solves overlap on the device but share no launch.
  * Results do not depend on the mix: in both modes each request runs the same deterministic arithmetic

@@ -33,7 +33,7 @@ struct Csr {
 
 // Launch shape of a patch application: split = 0 applies every patch of the level in one launch
 // (each warp dispatches on its patch's size); split = 1 launches once per size class (ceil(n/4) in
-// 1-4, 5-10, 11-19, 20-32), each compiled for that class only.  threads = 128 or 256 per block;
+// 1-4, 5-10, 11-19, 20-32, 33-42), each compiled for that class only.  threads = 128 or 256 per block;
 // per_sm = 0 gives one warp per patch, per_sm > 0 a persistent grid of per_sm blocks per SM whose
 // warps stride over the patches.  The corrections are bit-identical for every shape.
 struct ApplySched {
@@ -41,6 +41,10 @@ struct ApplySched {
   int threads = 256;
   int per_sm = 0;
 };
+
+// Size classes of the patch application by ceil(n/4): 1-4, 5-10, 11-19, 20-32, 33-42 (n <= 168).
+constexpr int kApplyClasses = 5;
+constexpr int kMaxPatch = 168;
 
 // Patch data of one level.  Patches are processed in "work order" (by packed-tile class, largest
 // first); a work item is one warp.  slot_ptr / slot_dofs are in canonical patch order.
@@ -64,8 +68,8 @@ struct Patches {
   const double* weight = nullptr;   // per-DoF weight or nullptr (plain sum)
   ApplySched sched;                 // launch shape used by patch_apply
   int nsm = 152;                    // SMs of the device (persistent grids)
-  int cls_lo[4] = {0, 0, 0, 0};     // work-list range [cls_lo[c], cls_hi[c]) of size class c
-  int cls_hi[4] = {0, 0, 0, 0};
+  int cls_lo[kApplyClasses] = {};  // work-list range [cls_lo[c], cls_hi[c]) of size class c
+  int cls_hi[kApplyClasses] = {};
 };
 
 // ---- sparse / vector kernels (kernels_sparse.cu) -------------------------------------------------
@@ -112,8 +116,8 @@ int patch_apply(const Patches& P, const double* r, float2* r2, double* delta, cu
 // The same with an explicit launch shape (the autotuner's candidates).
 int patch_apply_sched(const Patches& P, const ApplySched& sc, const double* r, float2* r2, double* delta,
                       cudaStream_t s);
-// Upper bound of ceil(n/4) of size class c (0..3).
-constexpr int kApplyClassHi[4] = {4, 10, 19, 32};
+// Upper bound of ceil(n/4) of size class c (0..4).
+constexpr int kApplyClassHi[kApplyClasses] = {4, 10, 19, 32, 42};
 // Sum of the slot corrections into each DoF (+ Dirichlet identity), fused with the Chebyshev update:
 //   mode 0: z = M^{-1} r                   (out = z)
 //   mode 1: d = z / theta; x = d           (first step, zero initial guess)

@@ -670,11 +670,13 @@ int apply_prec(const Patches& P, const ApplySched& sc, const double* r, const fl
     // one launch over every patch of the level; the per-warp dispatch covers all sizes
     if (P.nb_max <= 10) return launch_range<1, 10, FT>(P, sc, 0, P.npatch, r, r2, delta, s);
     if (P.nb_max <= 19) return launch_range<1, 19, FT>(P, sc, 0, P.npatch, r, r2, delta, s);
-    return launch_range<1, 32, FT>(P, sc, 0, P.npatch, r, r2, delta, s);
+    if (P.nb_max <= 32) return launch_range<1, 32, FT>(P, sc, 0, P.npatch, r, r2, delta, s);
+    return launch_range<1, 42, FT>(P, sc, 0, P.npatch, r, r2, delta, s);
   }
   // one launch per size class, each compiled for its own range of sizes (fewer registers, so more
   // resident warps, for the small classes)
   int k = 0;
+  k += launch_range<33, 42, FT>(P, sc, P.cls_lo[4], P.cls_hi[4], r, r2, delta, s);
   k += launch_range<20, 32, FT>(P, sc, P.cls_lo[3], P.cls_hi[3], r, r2, delta, s);
   k += launch_range<11, 19, FT>(P, sc, P.cls_lo[2], P.cls_hi[2], r, r2, delta, s);
   k += launch_range<5, 10, FT>(P, sc, P.cls_lo[1], P.cls_hi[1], r, r2, delta, s);
@@ -706,13 +708,14 @@ void launch_factor(const Csr& A, const PatchElems* elems, const Patches& P, void
 int patch_factor(const Csr& A, const Patches& P, int prec, void* factors, int* status, cudaStream_t s,
                  const PatchElems* elems) {
   if (P.npatch == 0) return 0;
-  // shared bytes n*n*8 + n*12 for the largest patch of the level (n <= 4 * nb_max <= 128).  The
-  // function attribute is always set to the bound for n = 128 (the same value from every thread, so
-  // concurrent setups cannot lower it under each other's launches).
+  // shared bytes n*n*8 + n*12 for the largest patch of the level (n <= 4 * nb_max <= kMaxPatch: 168
+  // FP64 rows of 168 are 226 KB, within the 227 KB a block may use).  The function attribute is always
+  // set to the bound for n = kMaxPatch (the same value from every thread, so concurrent setups cannot
+  // lower it under each other's launches).
   const int nmax = 4 * P.nb_max;
   const size_t smem = size_t(nmax) * nmax * 8 + size_t(nmax) * 12;
-  const int smem_cap = 128 * 128 * 8 + 128 * 12;
-  if (nmax > 128) return -1;   // the caller reports VK_ERR_ARG: nothing is left unfactored silently
+  const int smem_cap = kMaxPatch * kMaxPatch * 8 + kMaxPatch * 12;
+  if (nmax > kMaxPatch) return -1;   // the caller reports VK_ERR_ARG: nothing is left unfactored silently
   if (prec == 0)
     launch_factor<double>(A, elems, P, factors, status, smem, smem_cap, s);
   else if (prec == 1)
@@ -745,8 +748,10 @@ int group_apply_prec(const GroupApplyArgs& a, cudaStream_t s) {
     k_group_apply<10, FT><<<blocks, 256, 0, s>>>(a);
   else if (a.nb_max <= 19)
     k_group_apply<19, FT><<<blocks, 256, 0, s>>>(a);
-  else
+  else if (a.nb_max <= 32)
     k_group_apply<32, FT><<<blocks, 256, 0, s>>>(a);
+  else
+    k_group_apply<42, FT><<<blocks, 256, 0, s>>>(a);
   return 1;
 }
 

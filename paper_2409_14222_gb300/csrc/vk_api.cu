@@ -178,7 +178,7 @@ struct HostPatchPlan {
   int64_t ftotal = 0;
   int nb_max = 0;
   bool sym = false;             // symmetric tile layout of the inverses
-  int cls_lo[4] = {0, 0, 0, 0}, cls_hi[4] = {0, 0, 0, 0};  // work-list range of each size class
+  int cls_lo[vk::gpu::kApplyClasses] = {}, cls_hi[vk::gpu::kApplyClasses] = {};  // work-list range of each size class
   std::vector<int> dof_ptr, slot_pos;
   std::vector<double> weight;
 };
@@ -204,7 +204,7 @@ HostPatchPlan plan_patches(const vk::HostLevel& L, int weights, int prec) {
     P.nb_max = std::max(P.nb_max, nb(p));
   }
   // size classes of ceil(n/4) (the work list is sorted by it, largest first, so each class is a range)
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < vk::gpu::kApplyClasses; ++c) {
     const int lo = c == 0 ? 1 : vk::gpu::kApplyClassHi[c - 1] + 1, hi = vk::gpu::kApplyClassHi[c];
     int a = np, b = 0;
     for (int w = 0; w < np; ++w) {
@@ -217,7 +217,8 @@ HostPatchPlan plan_patches(const vk::HostLevel& L, int weights, int prec) {
     P.cls_lo[c] = a < b ? a : 0;
     P.cls_hi[c] = a < b ? b : 0;
   }
-  if (P.nb_max > vk::gpu::kApplyClassHi[3]) raise(VK_ERR_ARG, "patches larger than 128 DoFs are not supported");
+  if (P.nb_max > vk::gpu::kApplyClassHi[vk::gpu::kApplyClasses - 1])
+    raise(VK_ERR_ARG, "patches larger than 168 DoFs are not supported");
   const int64_t nslots = L.patch_dofs.size();
   P.dof_ptr.assign(L.ndof + 1, 0);
   for (int64_t s = 0; s < nslots; ++s) P.dof_ptr[L.patch_dofs[s] + 1]++;
@@ -375,8 +376,7 @@ std::vector<vk::gpu::ApplySched> apply_candidates() {
 void validate(const vk_problem* p, const vk_options* o) {
   if (!p || !o) raise(VK_ERR_ARG, "null problem or options");
   if (p->cell != VK_CELL_TRIANGLE && p->cell != VK_CELL_QUAD) raise(VK_ERR_ARG, "cell must be VK_CELL_TRIANGLE or VK_CELL_QUAD");
-  if (p->k < 2 || p->k > (p->cell == VK_CELL_QUAD ? 3 : 4))
-    raise(VK_ERR_ARG, p->cell == VK_CELL_QUAD ? "order k must be 2 or 3 on quadrilaterals" : "order k must be 2, 3 or 4");
+  if (p->k < 2 || p->k > 4) raise(VK_ERR_ARG, "order k must be 2, 3 or 4");
   if (p->N_coarse < 1 || p->nlevels < 1 || p->nlevels > 12) raise(VK_ERR_ARG, "bad mesh hierarchy");
   const int64_t Nf = int64_t(p->N_coarse) << (p->nlevels - 1);
   if (Nf * p->k > 8192) raise(VK_ERR_ARG, "finest mesh too large for 32-bit indices");
@@ -634,7 +634,7 @@ void allocate_device(vk_hierarchy* h) {
       G.prec = h->opt.factor_prec;
       G.nb_max = P.nb_max;
       G.sym = P.sym ? 1 : 0;
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < vk::gpu::kApplyClasses; ++c) {
         G.cls_lo[c] = P.cls_lo[c];
         G.cls_hi[c] = P.cls_hi[c];
       }

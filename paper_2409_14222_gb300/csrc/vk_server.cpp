@@ -1,8 +1,9 @@
 // Solve service on one GPU (include/vk.h, vk_server_*): a FIFO of Stokes solve requests of mixed mesh
-// size and order.  `slots` worker threads find or build each request's hierarchy; then either one
-// engine thread advances all admitted requests together as members of one group solve (VK_SERVE_GROUP:
-// one launch per stage of every FGMRES iteration over all of them, requests joining and leaving between
-// iterations), or each worker solves its request alone on its own CUDA stream (VK_SERVE_STREAMS).  Hierarchies are kept resident between requests
+// size and order.  `slots` worker threads find or build each request's hierarchy; then either group
+// engines advance the admitted requests together as members of group solves (VK_SERVE_GROUP: one
+// engine per size bucket, each with its own stream; one launch per stage of every FGMRES iteration over
+// the bucket's members, requests joining and leaving between iterations), or each worker solves its
+// request alone on its own CUDA stream (VK_SERVE_STREAMS).  Hierarchies are kept resident between requests
 // in a pool keyed by the whole problem (N_coarse, nlevels, k and the bits of the viscosity nu, which
 // enters the matrix); a pool entry is used by one slot at a time.  Admission is
 // by device footprint (vk_footprint): when the budget would be exceeded, idle hierarchies are evicted
@@ -71,7 +72,11 @@ struct Done {
 
 }  // namespace
 
-// A request whose hierarchy is ready, waiting to join the group solve (VK_SERVE_GROUP).
+// Size buckets of the group engines (finest-level DoFs): below 2^16, below 2^19, larger.
+constexpr int kBuckets = 3;
+int bucket_of(size_t ndof) { return ndof < (size_t(1) << 16) ? 0 : ndof < (size_t(1) << 19) ? 1 : 2; }
+
+// A request whose hierarchy is ready, waiting to join a group solve (VK_SERVE_GROUP).
 struct Ready {
   Job job;
   Instance* inst = nullptr;
@@ -84,10 +89,13 @@ struct vk_server {
   std::mutex mu;
   std::condition_variable cv_work;   // workers: new job or freed memory
   std::condition_variable cv_done;   // waiters: a result arrived
-  std::condition_variable cv_engine; // group engine: a request became ready, or stop
-  std::deque<Ready> ready;           // VK_SERVE_GROUP: requests with a hierarchy, not yet members
+  std::condition_variable cv_engine; // group engines: a request became ready, or stop
+  // VK_SERVE_GROUP: requests with a hierarchy, not yet members, one queue per size bucket; each bucket
+  // has its own engine (group solve and stream), so requests of similar size share launches while
+  // small requests do not advance at the pace of large ones
+  std::deque<Ready> ready[kBuckets];
   int inflight = 0;                  // VK_SERVE_GROUP: requests taken by workers and not finished
-  std::thread engine;
+  std::vector<std::thread> engines;
   std::deque<Job> queue;
   std::map<Key, std::vector<std::unique_ptr<Instance>>> pool;
   std::map<uint64_t, Done> done;
@@ -235,8 +243,9 @@ void worker(vk_server* s, int id) {
       r.inst = inst;
       r.setup_ms = setup_ms;
       r.t_start = t_start;
-      s->ready.push_back(std::move(r));
-      s->cv_engine.notify_one();
+      const int bk = bucket_of(r.job.b.size());
+      s->ready[bk].push_back(std::move(r));
+      s->cv_engine.notify_all();
       continue;
     }
     Done out;
@@ -275,7 +284,7 @@ void worker(vk_server* s, int id) {
 // VK_SERVE_GROUP engine: admits ready requests as members of one group solve between iterations,
 // advances all members by one FGMRES iteration per step (one launch per stage), and retires the
 // members that finish.
-void engine(vk_server* s) {
+void engine(vk_server* s, int bk) {
   cudaSetDevice(s->cfg.device);
   cudaStream_t stream = nullptr;
   const bool stream_ok = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess;
@@ -306,13 +315,14 @@ void engine(vk_server* s) {
     std::vector<Ready> adm;
     {
       std::unique_lock<std::mutex> lk(s->mu);
+      auto& rq = s->ready[bk];
       s->cv_engine.wait(lk, [&] {
-        return !act.empty() || !s->ready.empty() || (s->stopping && s->inflight == 0 && s->queue.empty());
+        return !act.empty() || !rq.empty() || (s->stopping && s->inflight == 0 && s->queue.empty());
       });
-      if (act.empty() && s->ready.empty() && s->stopping && s->inflight == 0 && s->queue.empty()) break;
-      while (!s->ready.empty() && int(act.size() + adm.size()) < maxm) {
-        adm.push_back(std::move(s->ready.front()));
-        s->ready.pop_front();
+      if (act.empty() && rq.empty() && s->stopping && s->inflight == 0 && s->queue.empty()) break;
+      while (!rq.empty() && int(act.size() + adm.size()) < maxm) {
+        adm.push_back(std::move(rq.front()));
+        rq.pop_front();
       }
     }
     for (Ready& r : adm) {
@@ -408,7 +418,8 @@ int vk_server_create(const vk_server_config* cfg, vk_server** out) {
   }
   vk_server* raw = s.get();
   for (int i = 0; i < cfg->slots; ++i) raw->workers.emplace_back(worker, raw, i);
-  if (raw->cfg.mode == VK_SERVE_GROUP) raw->engine = std::thread(engine, raw);
+  if (raw->cfg.mode == VK_SERVE_GROUP)
+    for (int bk = 0; bk < kBuckets; ++bk) raw->engines.emplace_back(engine, raw, bk);
   *out = s.release();
   return VK_OK;
 }
@@ -505,7 +516,7 @@ void vk_server_destroy(vk_server* s) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->cv_engine.notify_all();
   }
-  if (s->engine.joinable()) s->engine.join();
+  for (auto& t : s->engines) t.join();
   for (auto& kv : s->pool)
     for (auto& inst : kv.second)
       if (inst->h) vk_destroy(inst->h);

@@ -217,7 +217,7 @@ def test_manufactured_rhs_equals_the_oracle(vk, N, k):
     assert np.array_equal(got[mask] == 0.0, want[mask] == 0.0)
 
 
-@pytest.mark.parametrize("Nc,L,k", [(2, 2, 2), (2, 3, 2), (2, 2, 3), (1, 3, 3)])
+@pytest.mark.parametrize("Nc,L,k", [(2, 2, 2), (2, 3, 2), (2, 2, 3), (1, 3, 3), (2, 2, 4)])
 def test_quad_host_setup_equals_oracle(vk, Nc, L, k):
     # Taylor-Hood Q_k / Q_{k-1} (Case 2 of Sec. 3): the library's element matrices (FP64 Gauss-Legendre),
     # assembly, tensor-product transfers and quadrilateral patches against the oracle's exact ones
@@ -244,7 +244,7 @@ def test_quad_host_setup_equals_oracle(vk, Nc, L, k):
 
 def test_quad_order_bound(vk):
     with pytest.raises(vk.VkError):
-        vk.Hierarchy(2, 2, 4, host_only=True, cell=vk.vk.VK_CELL_QUAD)
+        vk.Hierarchy(2, 2, 5, host_only=True, cell=vk.vk.VK_CELL_QUAD)
     with pytest.raises(vk.VkError):
         vk.Hierarchy(2, 2, 2, host_only=True, cell=2)
 

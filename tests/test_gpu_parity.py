@@ -358,7 +358,20 @@ def test_multiplicity_weights_parity(vk, weighted, case):
     x = torch.empty_like(dev(b))
     G.vcycle(dev(b), x)
     assert rel(host(x), H.vcycle(b)) <= 1e-9
-    _solve_parity(vk, H, G, si.rhs_normal(H.finest.space.ndof, 0), 1e-10)
+    if case[2] == 2:
+        _solve_parity(vk, H, G, si.rhs_normal(H.finest.space.ndof, 0), 1e-10)
+        return
+    # P3 / P4: some Givens estimates are ill-conditioned; the 1e-8 history target applies to the entries
+    # the method determines (where the oracle's two orthogonalisations agree), as in the higher-order tests
+    from test_gpu_schedule import check_history as check_determined
+    bb = si.rhs_normal(H.finest.space.ndof, 0)
+    xs = torch.zeros_like(dev(bb))
+    out = G.solve(dev(bb), xs, rtol=1e-10)
+    ref = solver.solve(H, bb, 1e-10, 100)
+    ref2 = solver.solve(H, bb, 1e-10, 100, orth="cgs2")
+    assert out["iterations"] == ref.iters == ref2.iters
+    check_determined(out["history"], np.array(ref.hist), np.array(ref2.hist))
+    assert rel(host(xs), ref2.x) <= 1e-10 and rel(host(xs), ref.x) <= max(1e-10, 2 * rel(ref2.x, ref.x))
 
 
 def test_device_footprint_matches_prediction(vk):

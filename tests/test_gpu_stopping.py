@@ -66,11 +66,14 @@ def test_stopping_study_matches_the_oracle(vk):
     errs_g, errs_o = [], []
     for tau in tolerances(1e-10)[::4]:
         out = G.solve(bd, x, rtol=tau)
-        ref = solver.solve(H, b, tau, 100)
+        # the oracle with the library's orthogonalisation (classical Gram-Schmidt twice): at loose
+        # tolerances the iterate's error is poorly determined by the ill-conditioned Hessenberg system,
+        # so two orthogonalisations give equal residual reductions but different errors
+        ref = solver.solve(H, b, tau, 100, orth="cgs2")
         assert out["iterations"] == ref.iters, tau
         eg, eo = G.errors(x), fem.errors(s, ref.x)
         for a_, b_ in zip(eg, eo):
-            assert abs(a_ - b_) <= 1e-6 * b_ + 1e-12, (tau, eg, eo)   # x agrees to ~1e-12
+            assert abs(a_ - b_) <= 1e-6 * b_ + 1e-12, (tau, eg, eo)
         errs_g.append(eg)
         errs_o.append(eo)
     # the velocity error settles at the discretisation error as the tolerance falls
