@@ -432,7 +432,8 @@ def single_rhs_record(vk, torch, si, cfg, args, opts, steps, warmup, flush, worl
     return rec
 
 
-def summary_of(rec, cfg, args, hbm, peak_kind, fp64_tflops, config):
+def summary_of(rec, cfg, args, hbm, peak_kind, fp64_tflops, config, prec=None):
+    prec = prec or args.prec
     t, kt = rec["timed"], rec["kt"]
     Nc, L, k, sweeps, rtol, desc = cfg
     return {
@@ -442,7 +443,7 @@ def summary_of(rec, cfg, args, hbm, peak_kind, fp64_tflops, config):
         "iterations": {"mean": float(np.mean(t["iters"])), "min": int(min(t["iters"])), "max": int(max(t["iters"]))},
         "latency_ms": {"p50": float(np.percentile(t["times_ms"], 50)), "p99": float(np.percentile(t["times_ms"], 99))},
         "setup_s": rec["setup_s"], "gpu_launches": t["launches"],
-        "roofline": apply_roofline(kt, args.prec, hbm, peak_kind, fp64_tflops, config),
+        "roofline": apply_roofline(kt, prec, hbm, peak_kind, fp64_tflops, config),
         "spmv": spmv_roofline(kt, "spmv_bytes", hbm, peak_kind, "k_sell residual r = b - A x (finest level, FP64)"),
         "apply_schedule": schedules(rec["G"], L),
     }
@@ -554,6 +555,26 @@ def run_vk(args, config, cfg):
         nested["cfg2"] = summary_of(r2, c2, args, hbm, peak_kind, fp64_tflops, "cfg2")
         del r2
         torch.cuda.empty_cache()
+        if args.prec == "f64":
+            # the same workload with FP32-pair inverses in the symmetric tile layout (about 48-bit
+            # entries, FP32-pipe arithmetic, bound by HBM instead of the FP64 pipe), and its solution's
+            # difference from the FP64 one on the same right-hand side
+            oe = make_options(vk, args, sweeps)
+            oe.factor_prec = vk.VK_PREC_F64E
+            re_ = single_rhs_record(vk, torch, si, cfg, args, oe, min(args.steps, 10), 3, flush, world, rank, peaks,
+                                    e2e=False)
+            se = summary_of(re_, cfg, args, hbm, peak_kind, fp64_tflops, config, prec="f64e")
+            b0 = torch.from_numpy(si.rhs_normal(main["ndof"], 4242)).cuda()
+            xa, xb = torch.zeros_like(b0), torch.zeros_like(b0)
+            oa = main["G"].solve(b0, xa, rtol=rtol, history=False)
+            ob = re_["G"].solve(b0, xb, rtol=rtol, history=False)
+            se["rel_diff_vs_fp64_solution"] = float(torch.linalg.vector_norm(xa - xb) / torch.linalg.vector_norm(xa))
+            se["iterations_fp64_vs_f64e"] = [oa["iterations"], ob["iterations"]]
+            se["speedup_vs_fp64"] = se["value"] / main["value"]
+            se["dtype"] = "f64 vectors; patch inverses as FP32 pairs (48-bit), symmetric tiles, FP32-pair products"
+            nested["f64e_symmetric"] = se
+            del re_
+            torch.cuda.empty_cache()
         nested["batch16"] = batch_record(vk, torch, si, cfg, args, flush, hbm, peaks, peak_kind, G64=main["G"],
                                          fp64_value=main["value"])
         main["G"] = None
