@@ -19,6 +19,9 @@ equations"):
 * ``patches`` -- vertex / edge / cell ("composite", "topological") Vanka patches of Sec. 3.1.
 * ``quad``    -- Taylor-Hood (Q_k, Q_{k-1}) on quadrilaterals (Case 2 of Sec. 3): exact tensor-product
                  element matrices, transfers, composite patches, manufactured data and error norms.
+* ``bdm``     -- (BDM_k, dP_{k-1}) with the interior-penalty form of Eq. (DiscontBilinearForm) (Case 3):
+                 exact reference basis and transfers, FP64 element and edge integrals, extended cell
+                 patches (Sec. 3.1), manufactured data and broken error norms.
 * ``solver``  -- additive subspace correction (Algorithm 1), Chebyshev acceleration with the
                  [lambda/4, 1.1 lambda] interval (Sec. 3, "Relaxation"), Arnoldi eigenvalue estimate,
                  multiplicative V-cycle, bordered coarse solve, FGMRES (Sec. 3 and Sec. 4).

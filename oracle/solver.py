@@ -28,7 +28,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from . import fem, patches as patches_mod, quad, splitmix
+from . import bdm, fem, patches as patches_mod, quad, splitmix
 
 CHEB_LO = 0.25
 CHEB_HI = 1.1
@@ -162,13 +162,15 @@ class Hierarchy:
     """Levels 0 (coarsest, N_coarse) ... L-1 (finest, N_coarse * 2^(L-1)) for one order k.
 
     cell = "tri": Taylor-Hood (P_k, P_{k-1}) on triangles (Case 1 of Sec. 3); cell = "quad":
-    (Q_k, Q_{k-1}) on quadrilaterals (Case 2), with the same relaxation, cycle and Krylov method."""
+    (Q_k, Q_{k-1}) on quadrilaterals (Case 2); cell = "bdm": (BDM_k, dP_{k-1}) with the interior-penalty
+    form and extended cell patches (Case 3); the same relaxation, cycle and Krylov method for all."""
 
     def __init__(self, N_coarse, nlevels, k, nu=1.0, sweeps=1, weights="plain", lambdas=None,
                  eig_seed=EIG_SEED, cell="tri"):
         self.k, self.nu_visc, self.sweeps, self.cell = k, nu, sweeps, cell
         disc = {"tri": (fem.Space, fem.assemble_full, patches_mod.build_patches, fem.prolongation),
-                "quad": (quad.QSpace, quad.assemble_full, quad.build_patches, quad.prolongation)}[cell]
+                "quad": (quad.QSpace, quad.assemble_full, quad.build_patches, quad.prolongation),
+                "bdm": (bdm.BDMSpace, bdm.assemble_full, bdm.build_patches, bdm.prolongation)}[cell]
         make_space, assemble, build_patches, prolong = disc
         self.levels = []
         for l in range(nlevels):
