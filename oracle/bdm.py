@@ -365,7 +365,8 @@ def prolongation(coarse, fine):
             c = _cell_of_point(coarse, Xc, Yc)
         dofs, signs, _ = coarse.cell_dofs(c)
         vs = _coarse_value(coarse, c, Xc, Yc)
-        return [(d, s, v) for d, s, v in zip(dofs, signs, vs)]
+        # the signs as exact integers: a float sign would turn the moment sums below into float sums
+        return [(d, int(s), v) for d, s, v in zip(dofs, signs, vs)]
 
     # fine edge DoFs: normal flux at the fine edge points; fine units are half the coarse ones, and the
     # Piola factor 1/h doubles on the fine level while rot(x_b - x_a) halves: both in coarse units below
