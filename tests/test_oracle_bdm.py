@@ -167,3 +167,51 @@ def test_bdm_vcycle_dense_composition_and_fgmres(k):
     bp = solver.project(fin.space, b)
     xd = solver.project(fin.space, solver.direct_solve(fin.A, fin.space.nullspace(), bp))
     assert res.converged and np.linalg.norm(res.x - xd) <= 1e-9 * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_interior_moment_functions_are_orthogonal_and_span_nedelec(k):
+    # the interior DoFs' test functions: pairwise L^2-orthogonal on the reference triangle, norms in
+    # [1, 2), and the same span as the monomial-generated Nedelec space (exact ranks of the coefficient
+    # matrices over the monomials)
+    Q = bdm._ned_space(k)
+    M = bdm._ned_monomial(k)
+    assert len(Q) == len(M) == (k + 1) * (k - 1)
+    for i, a in enumerate(Q):
+        for j, b in enumerate(Q):
+            ip = bdm._ned_inner(a, b)
+            if i != j:
+                assert ip == 0
+            else:
+                assert 1 <= ip < 4
+    keys = sorted({(c, pq) for f in Q + M for c in (0, 1) for pq in f[c]})
+    mat = lambda fs: sympy.Matrix([[f[c].get(pq, 0) for (c, pq) in keys] for f in fs])
+    assert mat(Q).rank() == mat(M).rank() == mat(Q + M).rank() == len(M)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_penalty_makes_the_form_coercive_with_margin(k):
+    # alpha = (k+1)(k+2) is "sufficiently large" (Sec. 2.1): the velocity block is positive definite on
+    # the free DoFs, while a quarter of it loses coercivity (the bound is not vacuous)
+    s = bdm.BDMSpace(4, k)
+    free = ~s.dirichlet_mask()[:s.n_u]
+    mins = []
+    for scale in (1.0, 0.25):
+        old = bdm.penalty
+        bdm.penalty = lambda kk, scale=scale: scale * old(kk)
+        try:
+            K = bdm.assemble_full(s)
+        finally:
+            bdm.penalty = old
+        Au = K[:s.n_u, :s.n_u].toarray()[np.ix_(free, free)]
+        mins.append(np.linalg.eigvalsh(Au).min())
+    assert mins[0] > 0 > mins[1], mins
+
+
+@pytest.mark.parametrize("case", [(2, 2, 1), (2, 3, 1), (2, 2, 2), (2, 3, 2), (2, 2, 3)])
+def test_iteration_counts_are_h_and_p_robust(case):
+    # Sec. 4.3: with the extended cell patches the counts hardly depend on k or the level count (rtol 1e-10)
+    H = solver.Hierarchy(*case, cell="bdm")
+    b = np.random.default_rng(0).standard_normal(H.finest.space.ndof)
+    res = solver.solve(H, b, 1e-10, 100)
+    assert res.converged and 20 <= res.iters <= 40, res.iters
