@@ -798,8 +798,9 @@ def run_serving(args):
 
 
 def run_stopping(args):
-    """The stopping-criterion study of Sec. 4.4 on the GPU, for Taylor-Hood P_k/P_{k-1} on triangles and
-    Q_k/Q_{k-1} on quadrilaterals (the paper's Taylor-Hood study is on quadrilaterals): the
+    """The stopping-criterion study of Sec. 4.4 on the GPU, for Taylor-Hood P_k/P_{k-1} on triangles,
+    Q_k/Q_{k-1} on quadrilaterals (the paper's Taylor-Hood study is on quadrilaterals) and
+    (BDM_k, dP_{k-1}) on triangles (broken H^1 velocity error): the
     manufactured problem (Eq. model_problem) on 5x5 -> 5*2^l meshes is solved with relative tolerances
     1e-2, 5e-3, 2.5e-3, ... (halved each time, down to 1e-13), and the relative H^1 velocity error and the
     L^2 pressure error (mean removed) are measured on the device.  For each quantity the reported
@@ -819,10 +820,11 @@ def run_stopping(args):
     t_start = time.perf_counter()
     cases = [("triangles", k, lev) for k in (2, 3, 4) for lev in (1, 2, 3, 4)]
     cases += [("quadrilaterals", k, lev) for k in (2, 3) for lev in (1, 2, 3, 4)]
+    cases += [("bdm", k, lev) for k in (2, 3, 4, 5) for lev in (1, 2, 3, 4)]
+    cell_code = {"triangles": vk.vk.VK_CELL_TRIANGLE, "quadrilaterals": vk.vk.VK_CELL_QUAD, "bdm": vk.vk.VK_CELL_BDM}
     for cell, k, lev in cases:
         if True:
-            G = vk.Hierarchy(5, lev + 1, k, options=vk.default_options(sweeps=1),
-                             cell=vk.vk.VK_CELL_QUAD if cell == "quadrilaterals" else vk.vk.VK_CELL_TRIANGLE)
+            G = vk.Hierarchy(5, lev + 1, k, options=vk.default_options(sweeps=1), cell=cell_code[cell])
             b = torch.from_numpy(G.manufactured_rhs()).cuda()
             x = torch.zeros_like(b)
             errs, iters, ms = [], [], []
@@ -853,7 +855,8 @@ def run_stopping(args):
                                       "l2_rel_error": errs[-1][1], "p_l2_error": errs[-1][2]}})
             G.close()
     print(json.dumps({"metric": "stopping tolerance needed to reach discretisation error (Sec. 4.4)",
-                      "config": {"workload": "Taylor-Hood P_k/P_{k-1} on triangles and Q_k/Q_{k-1} on quadrilaterals, manufactured solution, "
+                      "config": {"workload": "Taylor-Hood P_k/P_{k-1} on triangles, Q_k/Q_{k-1} on quadrilaterals and "
+                                             "(BDM_k, dP_{k-1}) on triangles, manufactured solution, "
                                              "5x5 coarsest grid, V(1,1), FGMRES", "tolerances": "1e-2 halved to 1e-13",
                                  "criterion": "every tighter tolerance within 1 % of the tightest one's error"},
                       "rows": rows, "wall_s": time.perf_counter() - t_start}), flush=True)

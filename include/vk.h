@@ -78,6 +78,23 @@ extern "C" {
                                the same lattice DoF layout; vertex patches, and for k >= 3 edge and
                                cell patches (Sec. 3.1; interior sizes 51 / 99, 57, 33 / 163, 92, 54 for
                                k = 2 / 3 / 4); the N x N squares of the unit square                */
+#define VK_CELL_BDM 2       /* (BDM_k, dP_{k-1}) on triangles (Case 3 of Sec. 3), 1 <= k <= 5: H(div)-
+                               conforming velocity, discontinuous pressure, the interior-penalty form
+                               of Eq. (DiscontBilinearForm) with alpha = (k+1)(k+2), u . n = 0 imposed on
+                               the boundary-edge DoFs, extended cell patches (Sec. 3.1; interior size
+                               4 (k+1)(k+2) - 3 (k+1) + k (k+1) / 2: 19, 42, 74, 115, 165 for k = 1..5);
+                               matrix-full patches only.  DoFs: per edge (oriented from its lower to its
+                               higher vertex id, vertex id = y (N+1) + x) the normal fluxes
+                               v(x_j) . rot(x_b - x_a), rot(x, y) = (y, -x), at x_j = x_a + (j+1)/(k+2)
+                               (x_b - x_a); per cell the moments of the pulled-back field against
+                               Nedelec's first-kind space of degree k - 1 on the reference cell (its
+                               monomial basis orthogonalised in L^2 and scaled to norms in [1, 2) by
+                               powers of two); per
+                               cell the pressure at the equispaced P_{k-1} nodes.  Order: edge DoFs
+                               (horizontal, vertical, diagonal edges, each lexicographic), then each
+                               cell's interior DoFs, then each cell's pressures (lower cells, then
+                               upper).  The Dirichlet rows of this discretization are the no-flux rows:
+                               b there is the prescribed normal flux (zero for Eq. model_problem).  */
 
 /* Mesh hierarchy: the unit square cut into N_coarse x N_coarse squares, each split from its top-left
  * to its bottom-right corner (Sec. 4), refined uniformly nlevels-1 times (Sec. 3).  Velocity is
@@ -100,7 +117,8 @@ typedef struct vk_problem {
   double nu;
   int32_t bc;
   double domain[4];
-  int32_t cell;        /* VK_CELL_TRIANGLE (0, the default of a zeroed struct) or VK_CELL_QUAD       */
+  int32_t cell;        /* VK_CELL_TRIANGLE (0, the default of a zeroed struct), VK_CELL_QUAD or
+                          VK_CELL_BDM (k in 1..5 for VK_CELL_BDM)                                   */
 } vk_problem;
 
 typedef struct vk_options {
@@ -483,12 +501,14 @@ void vk_server_destroy(vk_server* s);
  * -cos(pi x) sin(pi y)), p = 0, f = 2 pi^2 nu u) on the finest level, in the canonical order (b_host:
  * ndof doubles): the load integrated with a collapsed Gauss-Legendre rule of k + 5 points per direction,
  * the velocity's boundary values (their nodal interpolant) lifted, b_F = F_F - K_FB g and b_B = g.
- * Host computation; works on host-only hierarchies. */
+ * VK_CELL_BDM: the load against the Piola-mapped basis; the exact velocity has u . n = 0 on the
+ * boundary, so the no-flux entries are zero.  Host computation; works on host-only hierarchies. */
 int vk_manufactured_rhs(const vk_hierarchy* h, double* b_host);
 
 /* Discretisation errors of a finest-level solution x_dev (device, ndof doubles) of the manufactured
  * problem, the quantities of the stopping-criterion study of Sec. 4.4: errs[0] = relative H^1 velocity
- * error (||u - u_h||_{H^1} / ||u||_{H^1}), errs[1] = relative L^2 velocity error, errs[2] = absolute
+ * error (||u - u_h||_{H^1} / ||u||_{H^1}; broken, cell by cell, for VK_CELL_BDM), errs[1] = relative
+ * L^2 velocity error, errs[2] = absolute
  * L^2 pressure error after removing the pressure's mean (p = 0).  Integrated on the device cell by cell
  * with a collapsed (triangles) or tensor (squares) Gauss-Legendre rule of k + 6 points per direction,
  * summed in a fixed order.  errs is

@@ -280,11 +280,14 @@ double fma_rate_tflops(bool fp64, void* scratch, cudaStream_t s);
 struct FemErrArgs {
   int N = 0, nb = 0, nq = 0, Q = 0, n_u = 0;
   int quad = 0;                 // 1: the N x N squares (Q_k), 0: the 2 N^2 triangles (P_k)
+  int bdm = 0;                  // 1: (BDM_k, dP_{k-1}) on the triangles: Piola-mapped vector basis
+  const double* sg = nullptr;   // BDM: [cell][nb] DoF signs
   double h = 0.0;
   const int* cv = nullptr;      // [cell][nb] velocity nodes
   const int* cp = nullptr;      // [cell][nq] pressure nodes
   const double *xi = nullptr, *eta = nullptr, *w = nullptr;                  // [Q] reference rule
   const double *phi = nullptr, *dxi = nullptr, *deta = nullptr;             // [Q][nb] P_k basis
+  // (BDM: phi = reference values [Q][nb][2], dxi = reference gradients [Q][nb][2][2])
   const double* psi = nullptr;  // [Q][nq] P_{k-1} basis
   const double* x = nullptr;    // solution (canonical DoF order)
 };

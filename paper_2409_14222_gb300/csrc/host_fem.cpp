@@ -267,6 +267,11 @@ void cell_maps_quad(int N, int k, std::vector<int>& cv, std::vector<int>& cp) {
 
 void build_level(int N, int k, double nu, bool with_patches, int nthreads, HostLevel& L, bool element_data,
                  int cell) {
+  if (cell == 2) {
+    if (element_data) throw std::runtime_error("BDM: no element data (matrix-full patches only)");
+    build_level_bdm(N, k, nu, with_patches, nthreads, L);
+    return;
+  }
   if (k < 2 || k > 6) throw std::runtime_error("order k must be in 2..6");
   const bool quadc = cell == 1;
   L.N = N;
@@ -599,6 +604,10 @@ void build_transfer(const HostLevel& c, HostLevel& f) {
   // Squares: the basis is a tensor product, so P^V and P^Q are tensor products of the 1-D
   // interpolations l_s(m / (2 deg)) = prod_{j != s} (m - 2 j) / (2 (s - j)), also exact ratios.
   if (f.N != 2 * c.N || f.k != c.k || f.cell != c.cell) throw std::runtime_error("transfer: levels not nested");
+  if (f.cell == 2) {
+    build_transfer_bdm(c, f);
+    return;
+  }
   const int Nc = c.N;
   struct Trip {
     int r, c;

@@ -375,11 +375,24 @@ std::vector<vk::gpu::ApplySched> apply_candidates() {
 
 void validate(const vk_problem* p, const vk_options* o) {
   if (!p || !o) raise(VK_ERR_ARG, "null problem or options");
-  if (p->cell != VK_CELL_TRIANGLE && p->cell != VK_CELL_QUAD) raise(VK_ERR_ARG, "cell must be VK_CELL_TRIANGLE or VK_CELL_QUAD");
-  if (p->k < 2 || p->k > 4) raise(VK_ERR_ARG, "order k must be 2, 3 or 4");
+  if (p->cell != VK_CELL_TRIANGLE && p->cell != VK_CELL_QUAD && p->cell != VK_CELL_BDM)
+    raise(VK_ERR_ARG, "cell must be VK_CELL_TRIANGLE, VK_CELL_QUAD or VK_CELL_BDM");
+  if (p->cell == VK_CELL_BDM) {
+    if (p->k < 1 || p->k > 5) raise(VK_ERR_ARG, "BDM order k must be in 1..5");
+  } else if (p->k < 2 || p->k > 4) {
+    raise(VK_ERR_ARG, "order k must be 2, 3 or 4");
+  }
   if (p->N_coarse < 1 || p->nlevels < 1 || p->nlevels > 12) raise(VK_ERR_ARG, "bad mesh hierarchy");
   const int64_t Nf = int64_t(p->N_coarse) << (p->nlevels - 1);
   if (Nf * p->k > 8192) raise(VK_ERR_ARG, "finest mesh too large for 32-bit indices");
+  if (p->cell == VK_CELL_BDM) {
+    // (k+1)(k+2) velocity functions per cell; an edge row couples at most the six cells around the two
+    // cells of its edge, plus their pressures
+    const int64_t nb = int64_t(p->k + 1) * (p->k + 2), nq = int64_t(p->k) * (p->k + 1) / 2;
+    const int64_t ncell = 2 * Nf * Nf, n_u = 3 * Nf * Nf * (p->k + 1) + ncell * (p->k + 1) * (p->k - 1);
+    if (n_u * (6 * nb + 2 * nq) + ncell * nq * nb > int64_t(INT32_MAX))
+      raise(VK_ERR_ARG, "finest BDM mesh too large for 32-bit indices");
+  }
   if (!(p->nu > 0.0) || !std::isfinite(p->nu)) raise(VK_ERR_ARG, "viscosity must be positive and finite");
   if (p->bc != VK_BC_DIRICHLET_ALL) raise(VK_ERR_ARG, "bc must be VK_BC_DIRICHLET_ALL");
   {
@@ -403,6 +416,8 @@ void validate(const vk_problem* p, const vk_options* o) {
   if (o->test_singular_patch < -1) raise(VK_ERR_ARG, "test_singular_patch must be -1 or a patch id");
   if (o->patch_assembly != VK_ASSEMBLY_MATRIX_FULL && o->patch_assembly != VK_ASSEMBLY_MATRIX_FREE)
     raise(VK_ERR_ARG, "bad patch_assembly");
+  if (p->cell == VK_CELL_BDM && o->patch_assembly != VK_ASSEMBLY_MATRIX_FULL)
+    raise(VK_ERR_ARG, "BDM patches are gathered from the assembled matrix (VK_ASSEMBLY_MATRIX_FULL)");
   if (o->apply_schedule < -1 || o->apply_schedule >= int(apply_candidates().size()))
     raise(VK_ERR_ARG, "apply_schedule must be -1 or a candidate index");
   if (o->batch_prec != VK_BATCH_NONE) {
@@ -1814,6 +1829,8 @@ int vk_manufactured_rhs(const vk_hierarchy* h, double* b_host) {
     std::vector<double> b;
     if (h->prob.cell == VK_CELL_QUAD)
       vk::manufactured_rhs_quad(h->host.back(), h->prob.nu, b);
+    else if (h->prob.cell == VK_CELL_BDM)
+      vk::manufactured_rhs_bdm(h->host.back(), h->prob.nu, b);
     else
       vk::manufactured_rhs(h->host.back(), h->prob.nu, b);
     std::copy(b.begin(), b.end(), b_host);
@@ -1827,10 +1844,13 @@ int vk_errors(vk_hierarchy* h, const double* x, double* errs, void* stream) {
     if (!x || !errs) raise(VK_ERR_ARG, "null argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const vk::HostLevel& F = h->host.back();
-    const bool quadc = h->prob.cell == VK_CELL_QUAD;
+    const bool quadc = h->prob.cell == VK_CELL_QUAD, bdmc = h->prob.cell == VK_CELL_BDM;
     std::vector<int> cv, cp;
-    std::vector<double> xi, eta, w, phi, dxi, deta, psi;
-    if (quadc) {
+    std::vector<double> xi, eta, w, phi, dxi, deta, psi, sg;
+    if (bdmc) {
+      vk::bdm_error_data(F, F.k + 6, cv, sg, cp, xi, eta, w, phi, dxi, psi);
+      deta.assign(1, 0.0);
+    } else if (quadc) {
       vk::cell_maps_quad(F.N, F.k, cv, cp);
       vk::reference_tables_quad(F.k, F.k + 6, xi, eta, w, phi, dxi, deta, psi);
     } else {
@@ -1851,7 +1871,8 @@ int vk_errors(vk_hierarchy* h, const double* x, double* errs, void* stream) {
       vk::gpu::FemErrArgs a;
       a.N = F.N;
       a.quad = quadc ? 1 : 0;
-      a.nb = quadc ? (F.k + 1) * (F.k + 1) : (F.k + 1) * (F.k + 2) / 2;
+      a.bdm = bdmc ? 1 : 0;
+      a.nb = bdmc ? (F.k + 1) * (F.k + 2) : quadc ? (F.k + 1) * (F.k + 1) : (F.k + 1) * (F.k + 2) / 2;
       a.nq = quadc ? F.k * F.k : F.k * (F.k + 1) / 2;
       a.Q = int(w.size());
       a.n_u = F.n_u;
@@ -1865,6 +1886,7 @@ int vk_errors(vk_hierarchy* h, const double* x, double* errs, void* stream) {
       a.dxi = up(dxi);
       a.deta = up(deta);
       a.psi = up(psi);
+      if (bdmc) a.sg = up(sg);
       a.x = x;
       std::vector<double> zeros(1024 * 7 + 7, 0.0);
       double* part = const_cast<double*>(up(zeros));

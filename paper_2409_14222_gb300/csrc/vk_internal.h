@@ -21,7 +21,7 @@ struct HostCsr {
 // One mesh level of the Taylor-Hood (P_k, P_{k-1}) discretization on the structured triangle mesh.
 struct HostLevel {
   int N = 0, k = 0;
-  int cell = 0;             // 0: triangles (P_k, P_{k-1}); 1: squares (Q_k, Q_{k-1})
+  int cell = 0;             // 0: triangles (P_k, P_{k-1}); 1: squares (Q_k, Q_{k-1}); 2: (BDM_k, dP_{k-1})
   int ncell_lower = 0;      // cells below this index use the first element matrix (all squares do)
   int nv1 = 0, np1 = 0;     // lattice sizes per side: k*N+1 (velocity), (k-1)*N+1 (pressure)
   int n_u = 0, n_p = 0, ndof = 0;
@@ -60,6 +60,14 @@ void reference_tables_quad(int k, int q, std::vector<double>& xi, std::vector<do
                            std::vector<double>& phi, std::vector<double>& dxi, std::vector<double>& deta,
                            std::vector<double>& psi);
 void manufactured_rhs_quad(const HostLevel& L, double nu, std::vector<double>& b);
+
+// host_bdm.cpp: (BDM_k, dP_{k-1}) with the interior-penalty form on the triangle mesh (Case 3).
+void build_level_bdm(int N, int k, double nu, bool with_patches, int nthreads, HostLevel& L);
+void build_transfer_bdm(const HostLevel& coarse, HostLevel& fine);
+void manufactured_rhs_bdm(const HostLevel& L, double nu, std::vector<double>& b);
+void bdm_error_data(const HostLevel& L, int q, std::vector<int>& cv, std::vector<double>& sg, std::vector<int>& cp,
+                    std::vector<double>& xi, std::vector<double>& eta, std::vector<double>& w,
+                    std::vector<double>& val, std::vector<double>& grad, std::vector<double>& psi);
 
 // host_eig.cpp: eigenvalues of a small real upper-Hessenberg matrix (row-major m x m).
 int hessenberg_eigenvalues(int m, const double* H, double* re, double* im);

@@ -22,7 +22,7 @@ VK_ERR_CUDA = 7
 VK_ERR_INTERNAL = 8
 VK_ERR_CANCELLED = 9
 VK_BC_DIRICHLET_ALL = 0
-VK_CELL_TRIANGLE, VK_CELL_QUAD = 0, 1
+VK_CELL_TRIANGLE, VK_CELL_QUAD, VK_CELL_BDM = 0, 1, 2
 VK_SERVE_GROUP, VK_SERVE_STREAMS = 0, 1
 VK_ASSEMBLY_MATRIX_FULL, VK_ASSEMBLY_MATRIX_FREE = 0, 1
 

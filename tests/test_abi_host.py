@@ -246,7 +246,7 @@ def test_quad_order_bound(vk):
     with pytest.raises(vk.VkError):
         vk.Hierarchy(2, 2, 5, host_only=True, cell=vk.vk.VK_CELL_QUAD)
     with pytest.raises(vk.VkError):
-        vk.Hierarchy(2, 2, 2, host_only=True, cell=2)
+        vk.Hierarchy(2, 2, 2, host_only=True, cell=3)
 
 
 @pytest.mark.parametrize("N,k", [(4, 2), (2, 3)])
@@ -255,4 +255,59 @@ def test_quad_manufactured_rhs_equals_the_oracle(vk, N, k):
     h = vk.Hierarchy(N, 1, k, host_only=True, cell=vk.vk.VK_CELL_QUAD)
     s = quad.QSpace(N, k)
     want = quad.manufactured_rhs(s, quad.assemble_full(s))
+    assert np.linalg.norm(h.manufactured_rhs() - want) <= 1e-13 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("Nc,L,k", [(1, 3, 1), (2, 2, 1), (1, 3, 2), (2, 2, 2), (1, 2, 3), (2, 2, 4)])
+def test_bdm_host_setup_equals_oracle(vk, Nc, L, k):
+    # (BDM_k, dP_{k-1}) (Case 3 of Sec. 3): the library's FP64 reference basis (Vandermonde solve), cell
+    # and interior-edge integrals, transfers and extended cell patches against the oracle's exact basis
+    # and transfers; the assembled values agree to rounding (the reference basis is solved in
+    # double-double: its Vandermonde matrix has condition 1e7 at k = 4)
+    from oracle import bdm
+    h = vk.Hierarchy(Nc, L, k, nu=0.7, host_only=True, cell=vk.vk.VK_CELL_BDM)
+    for l in range(L):
+        s = bdm.BDMSpace(Nc * 2 ** l, k)
+        Ao = fem.apply_dirichlet(bdm.assemble_full(s, 0.7), s.dirichlet_mask())
+        A = _csr(vk, h, l, vk.VK_CSR_A)
+        assert A.shape == Ao.shape
+        assert abs(A - Ao).max() <= 1e-12 * abs(Ao).max(), (l, abs(A - Ao).max() / abs(Ao).max())
+        assert abs(A - A.T).max() <= 1e-13 * abs(Ao).max()
+        assert np.array_equal(h.export_dirichlet(l), s.dirichlet_mask())
+        if l > 0:
+            Po = bdm.prolongation(bdm.BDMSpace(Nc * 2 ** (l - 1), k), s)
+            P = _csr(vk, h, l, vk.VK_CSR_P)
+            # formed in double-double and rounded once: the oracle's exact rationals to the last bit
+            # (the pressure rows in FP64 to a few units of the last place)
+            assert P.nnz == Po.nnz and abs(P - Po).max() <= 1e-15 * abs(Po).max()
+            assert abs(_csr(vk, h, l, vk.VK_CSR_R) - P.T).max() == 0.0
+            ptr, dofs, kind = h.export_patches(l)
+            op = bdm.build_patches(s)
+            assert len(ptr) - 1 == len(op)
+            for i, (knd, ent, d) in enumerate(op):
+                assert np.array_equal(dofs[ptr[i]:ptr[i + 1]], d), (l, i)
+                assert kind[i] == 2
+
+
+def test_bdm_order_and_assembly_bounds(vk):
+    for k in (0, 6):
+        with pytest.raises(vk.VkError):
+            vk.Hierarchy(2, 2, k, host_only=True, cell=vk.vk.VK_CELL_BDM)
+    with pytest.raises(vk.VkError):
+        vk.Hierarchy(2, 2, 2, host_only=True, cell=vk.vk.VK_CELL_BDM,
+                     options=vk.default_options(patch_assembly=vk.vk.VK_ASSEMBLY_MATRIX_FREE))
+    # the largest interior patch for k = 5 (165 DoFs) still fits the patch kernels
+    h = vk.Hierarchy(4, 2, 5, host_only=True, cell=vk.vk.VK_CELL_BDM)
+    ptr, _, _ = h.export_patches(1)
+    from oracle import bdm
+    assert np.diff(ptr).max() == bdm.interior_patch_size(5) == 165
+
+
+@pytest.mark.parametrize("N,k", [(4, 1), (4, 2), (2, 3)])
+def test_bdm_manufactured_rhs_equals_the_oracle(vk, N, k):
+    from oracle import bdm
+    h = vk.Hierarchy(N, 1, k, host_only=True, cell=vk.vk.VK_CELL_BDM)
+    s = bdm.BDMSpace(N, k)
+    want = bdm.load_vector(s)
+    want[s.dirichlet_mask()] = 0.0
     assert np.linalg.norm(h.manufactured_rhs() - want) <= 1e-13 * np.linalg.norm(want)
