@@ -402,11 +402,11 @@ def make_options(vk, args, sweeps):
 
 
 def single_rhs_record(vk, torch, si, cfg, args, opts, steps, warmup, flush, world, rank, peaks, clk=None,
-                      e2e=True):
+                      e2e=True, cell=0):
     """One single-right-hand-side workload: setup, timed solves, kernel times, end-to-end solves."""
     Nc, L, k, sweeps, rtol, desc = cfg
     t0 = time.perf_counter()
-    G = vk.Hierarchy(Nc, L, k, options=opts)
+    G = vk.Hierarchy(Nc, L, k, options=opts, cell=cell)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     ndof = G.ndof()
@@ -529,6 +529,54 @@ def batch_record(vk, torch, si, cfg, args, flush, hbm, peaks, peak_kind, G64=Non
     return rec
 
 
+def bdm_records(vk, torch, si, args, flush, world, rank, peaks, hbm, peak_kind, fp64_tflops):
+    """(BDM_k, dP_{k-1}) with the interior-penalty form and extended cell patches (Sec. 4.3): the paper's
+    5x5 coarsest grid refined four times (80x80, 5 levels), k = 2..5, FGMRES to a 1e-10 reduction, FP64
+    (the paper's timing study of this discretization is at four refinements)."""
+    out = {}
+    for k in (2, 3, 4, 5):
+        cfg = (5, 5, k, 1, 1e-10, f"(BDM_{k}, dP_{k - 1}) interior penalty, 5x5 -> 80x80 (5 levels), "
+                                   f"extended cell patches, FGMRES to 1e-10")
+        rec = single_rhs_record(vk, torch, si, cfg, args, make_options(vk, args, 1), min(args.steps, 5), 3, flush,
+                                world, rank, peaks, e2e=False, cell=vk.VK_CELL_BDM)
+        out[f"k{k}"] = summary_of(rec, cfg, args, hbm, peak_kind, fp64_tflops, f"bdm{k}")
+        del rec
+        torch.cuda.empty_cache()
+    return out
+
+
+def patch_assembly_records(vk, torch, si):
+    """Matrix-full (patch matrices gathered from the assembled CSR matrix, ASMPatchPC) against matrix-free
+    (each patch matrix assembled from the element matrices of the cells it touches, PCPATCH; Sec. 3.1)
+    patch setup on the device: the timed gather or assembly plus Gauss-Jordan inversion of every patch on
+    every level, the whole setup, the device footprint, and whether the first solve is bit-identical
+    (it must be: both build the same patch matrices in the same summation order)."""
+    out = {}
+    for name, cfg in (("cfg4", CONFIGS["cfg4"]), ("cfg3p4", CONFIGS["cfg3p4"])):
+        Nc, L, k, sweeps, rtol, desc = cfg
+        rec, xs = {"workload": desc}, []
+        for asm in ("matrix_full", "matrix_free"):
+            mode = vk.vk.VK_ASSEMBLY_MATRIX_FREE if asm == "matrix_free" else vk.vk.VK_ASSEMBLY_MATRIX_FULL
+            t0 = time.perf_counter()
+            G = vk.Hierarchy(Nc, L, k, options=vk.default_options(sweeps=sweeps, patch_assembly=mode))
+            torch.cuda.synchronize()
+            setup_s = time.perf_counter() - t0
+            st = G.stats()
+            b = torch.from_numpy(si.rhs_normal(G.ndof(), 99)).cuda()
+            x = torch.zeros_like(b)
+            G.solve(b, x, rtol=rtol, history=False)
+            xs.append(x.cpu())
+            rec[asm] = {"patch_setup_ms": st["setup_factor_ms"], "setup_s": setup_s,
+                        "device_bytes": G.device_bytes()}
+            G.close()
+            del G, b, x
+            torch.cuda.empty_cache()
+        rec["first_solve_bit_identical"] = bool(torch.equal(xs[0], xs[1]))
+        rec["matrix_free_over_full_patch_setup"] = rec["matrix_free"]["patch_setup_ms"] / rec["matrix_full"]["patch_setup_ms"]
+        out[name] = rec
+    return out
+
+
 def run_vk(args, config, cfg):
     import torch
     world, rank, local = dist_setup()
@@ -583,6 +631,9 @@ def run_vk(args, config, cfg):
             srv = serving_record(vk, si, args, args.serve_requests, (1.0,), 8, per_key=1)
             srv["workload"] = CONFIGS["cfg5"][5]
             nested["serving"] = srv
+        if not args.no_bdm:
+            nested["bdm"] = bdm_records(vk, torch, si, args, flush, world, rank, peaks, hbm, peak_kind, fp64_tflops)
+        nested["patch_assembly"] = patch_assembly_records(vk, torch, si)
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline else oracle_cpu_baseline(config, cfg)
@@ -876,6 +927,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-nested", action="store_true", help="cfg4: skip the nested records")
     ap.add_argument("--no-serving", action="store_true", help="cfg4: skip the nested serving record")
+    ap.add_argument("--no-bdm", action="store_true", help="cfg4: skip the nested BDM records")
     ap.add_argument("--serve-requests", type=int, default=100, help="cfg4: requests of the nested serving record")
     ap.add_argument("--requests", type=int, default=1000, help="cfg5: requests in the 1x stream")
     ap.add_argument("--slots", type=int, default=4, help="cfg5: concurrent solves")

@@ -338,7 +338,8 @@ int vk_ndof(const vk_hierarchy* h, int level, int64_t* n_u, int64_t* n_p);
 /* Coordinates of every DoF of a level in the canonical order: xy (host, 2*ndof doubles, may be NULL)
  * receives (x, y) of the DoF's Lagrange node (equispaced nodes of the structured mesh of Sec. 4);
  * kind (host, ndof bytes, may be NULL) receives 0 / 1 for the x / y velocity component and 2 for
- * pressure.  Works on host-only hierarchies. */
+ * pressure.  VK_CELL_BDM: the edge point of each normal-flux DoF (kind 3), the cell centroid for the
+ * interior moment DoFs (kind 4), the pressure node (kind 2).  Works on host-only hierarchies. */
 int vk_export_dof_coords(const vk_hierarchy* h, int level, double* xy, int8_t* kind);
 
 /* Copies the Dirichlet flags (1 = no-slip velocity DoF) of a level into a host array of ndof bytes. */

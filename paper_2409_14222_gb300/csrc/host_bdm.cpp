@@ -1078,4 +1078,41 @@ void bdm_error_data(const HostLevel& L, int q, std::vector<int>& cv, std::vector
   }
 }
 
+// DoF locations of a (BDM_k, dP_{k-1}) level: the edge point of each normal-flux DoF (kind 3), the
+// cell centroid for the interior moments (kind 4), the pressure node (kind 2).
+void bdm_dof_coords(const HostLevel& L, double* xy, int8_t* kind) {
+  const int N = L.N, k = L.k;
+  const BdmMesh M(N, k);
+  const double h = 1.0 / N;
+  auto put = [&](int d, double x, double y, int8_t c) {
+    if (xy) {
+      xy[2 * int64_t(d)] = x;
+      xy[2 * int64_t(d) + 1] = y;
+    }
+    if (kind) kind[d] = c;
+  };
+  for (int e = 0; e < M.nedge; ++e) {
+    int ax, ay, bx, by;
+    M.edge_ends(e, ax, ay, bx, by);
+    for (int j = 0; j <= k; ++j) {
+      const double t = double(j + 1) / (k + 2);
+      put(e * M.per_e + j, h * (ax + t * (bx - ax)), h * (ay + t * (by - ay)), 3);
+    }
+  }
+  const int dq = k - 1;
+  for (int c = 0; c < M.ncell; ++c) {
+    int v[3][2];
+    cell_vertices(N, c, v);
+    const double cx = h * (v[0][0] + v[1][0] + v[2][0]) / 3.0, cy = h * (v[0][1] + v[1][1] + v[2][1]) / 3.0;
+    for (int m = 0; m < M.per_c; ++m) put(M.n_edge + c * M.per_c + m, cx, cy, 4);
+    int m = 0;
+    for (int t = 0; t <= dq; ++t)
+      for (int s2 = 0; s2 + t <= dq; ++s2, ++m) {
+        const double xr = dq == 0 ? 1.0 / 3.0 : double(s2) / dq, yr = dq == 0 ? 1.0 / 3.0 : double(t) / dq;
+        put(M.pdof(c, m), h * (v[0][0] + (v[1][0] - v[0][0]) * xr + (v[2][0] - v[0][0]) * yr),
+            h * (v[0][1] + (v[1][1] - v[0][1]) * xr + (v[2][1] - v[0][1]) * yr), 2);
+      }
+  }
+}
+
 }  // namespace vk

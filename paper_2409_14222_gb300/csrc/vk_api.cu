@@ -1754,6 +1754,10 @@ int vk_export_dof_coords(const vk_hierarchy* h, int level, double* xy, int8_t* k
     check_level(h, level);
     if (!xy && !kind) raise(VK_ERR_ARG, "null outputs");
     const vk::HostLevel& L = h->host[level];
+    if (L.cell == 2) {
+      vk::bdm_dof_coords(L, xy, kind);
+      return VK_OK;
+    }
     const int nv = L.nv1, np = L.np1, kN = L.k * L.N, k1N = (L.k - 1) * L.N;
     for (int d = 0; d < L.ndof; ++d) {
       double x, y;

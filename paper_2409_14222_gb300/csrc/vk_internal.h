@@ -65,6 +65,7 @@ void manufactured_rhs_quad(const HostLevel& L, double nu, std::vector<double>& b
 void build_level_bdm(int N, int k, double nu, bool with_patches, int nthreads, HostLevel& L);
 void build_transfer_bdm(const HostLevel& coarse, HostLevel& fine);
 void manufactured_rhs_bdm(const HostLevel& L, double nu, std::vector<double>& b);
+void bdm_dof_coords(const HostLevel& L, double* xy, int8_t* kind);
 void bdm_error_data(const HostLevel& L, int q, std::vector<int>& cv, std::vector<double>& sg, std::vector<int>& cp,
                     std::vector<double>& xi, std::vector<double>& eta, std::vector<double>& w,
                     std::vector<double>& val, std::vector<double>& grad, std::vector<double>& psi);

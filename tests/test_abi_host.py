@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 import scipy.sparse as sp
 
-from oracle import fem, patches as opatches
+from oracle import exact, fem, patches as opatches
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -311,3 +311,25 @@ def test_bdm_manufactured_rhs_equals_the_oracle(vk, N, k):
     want = bdm.load_vector(s)
     want[s.dirichlet_mask()] = 0.0
     assert np.linalg.norm(h.manufactured_rhs() - want) <= 1e-13 * np.linalg.norm(want)
+
+
+def test_bdm_dof_coords_follow_the_oracle_layout(vk):
+    from oracle import bdm
+    N, k = 3, 3
+    h = vk.Hierarchy(N, 1, k, host_only=True, cell=vk.vk.VK_CELL_BDM)
+    xy, kind = h.export_dof_coords(0)
+    s = bdm.BDMSpace(N, k)
+    assert np.array_equal(kind[:s.n_edge], np.full(s.n_edge, 3))
+    assert np.array_equal(kind[s.n_edge:s.n_u], np.full(s.n_u - s.n_edge, 4))
+    assert np.array_equal(kind[s.n_u:], np.full(s.n_p, 2))
+    for e, (va, vb) in enumerate(s.edges):
+        for j in range(k + 1):
+            t = (j + 1) / (k + 2)
+            want = (np.array(va) + t * (np.array(vb) - np.array(va))) / N
+            assert np.allclose(xy[e * (k + 1) + j], want, atol=1e-15)
+    for c, cell in enumerate(s.cells):
+        _, _, pd = s.cell_dofs(c)
+        x0, J = s.geometry(c, 1.0 / N)
+        assert np.allclose(xy[s.n_edge + c * (k + 1) * (k - 1)], x0 + J @ [1 / 3, 1 / 3], atol=1e-15)
+        for m, (a, b) in enumerate(exact.lattice_nodes(k - 1)):
+            assert np.allclose(xy[pd[m]], x0 + J @ [a / (k - 1), b / (k - 1)], atol=1e-15)
