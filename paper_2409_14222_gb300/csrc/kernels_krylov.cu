@@ -170,18 +170,20 @@ __global__ void k_fg_col_put(const double* __restrict__ in, double* __restrict__
   if (r < n) Z[ld * st->j + r] = in[r];
 }
 
-// Fixed grid of kReduceBlocks blocks; block b forms the partial dots of rows {b*kT + t + k*kReduceBlocks*kT}
-// for every basis vector i <= j (same partition and order as k_multi_dot).
-// Block b's partial dots of w with V[0..j], kFgVB vectors per pass (w read once per pass).  Each
-// vector's partial is summed in the same element order and combined by the same tree as block_sum,
-// so the values equal those of k_multi_dot.
+// Grid (kReduceBlocks, ceil(kmax / kFgVB)): block (b, g) forms the partial dots of rows
+// {b*kT + t + k*kReduceBlocks*kT} (the partition of k_multi_dot) with the basis vectors
+// g*kFgVB .. g*kFgVB + kFgVB - 1 that are <= j (w read once for the group); blocks of groups beyond j
+// return at once.  Each vector's partial is summed in the same element order and combined by the same
+// tree as block_sum, so the values equal those of k_multi_dot.
 constexpr int kFgVB = 8;
 __global__ void __launch_bounds__(kT) k_fg_mdot(const double* __restrict__ V, int64_t ld,
                                                 const FgState* __restrict__ st, const double* __restrict__ w,
                                                 int n, double* __restrict__ partial) {
   __shared__ double sh[kFgVB][kT / 32];
   const int j = st->j, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i0 = 0; i0 <= j; i0 += kFgVB) {
+  {
+    const int i0 = blockIdx.y * kFgVB;
+    if (i0 > j) return;
     double s[kFgVB];
 #pragma unroll
     for (int u = 0; u < kFgVB; ++u) s[u] = 0.0;
@@ -456,7 +458,7 @@ int fg_col_put(const double* in, double* Z, int64_t ld, const FgState* st, int n
 
 int fg_cgs_pass(const double* V, int64_t ld, const FgState* st, double* w, int n, double* partial, double* H,
                 int ldh, double* t2, int kmax, int mode, cudaStream_t s) {
-  k_fg_mdot<<<kReduceBlocks, kT, 0, s>>>(V, ld, st, w, n, partial);
+  k_fg_mdot<<<dim3(kReduceBlocks, (kmax + kFgVB - 1) / kFgVB), kT, 0, s>>>(V, ld, st, w, n, partial);
   k_fg_mfin<<<kmax, kT, 0, s>>>(partial, st, H, ldh, t2, mode);
   k_fg_maxpy<<<(n + kT - 1) / kT, kT, 0, s>>>(V, ld, st, H, ldh, t2, mode, w, n);
   return 3;
