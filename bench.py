@@ -396,6 +396,8 @@ def make_options(vk, args, sweeps):
         opts.factor_prec = vk.VK_PREC_F64E
     if args.no_graph:
         opts.use_graph = 0
+    if args.no_pdl:
+        opts.graph_pdl = 0
     if args.spmv_warps:
         opts.spmv_warps = args.spmv_warps
     return opts
@@ -414,8 +416,9 @@ def single_rhs_record(vk, torch, si, cfg, args, opts, steps, warmup, flush, worl
     B = [torch.from_numpy(si.rhs_normal(ndof, s)).cuda() for s in seeds]
     x = torch.zeros(ndof, dtype=torch.float64, device="cuda")
     t = timed_solves(torch, G, B, x, rtol, steps, warmup, flush, world, clk)
+    graph_pdl = int(G.stats()["graph_pdl"])
     kt = kernel_times(torch, G, B, x, rtol, min(steps, 10), warmup, flush)
-    rec = {"G": G, "ndof": ndof, "setup_s": setup_s, "timed": t, "kt": kt,
+    rec = {"G": G, "ndof": ndof, "setup_s": setup_s, "timed": t, "kt": kt, "graph_pdl": graph_pdl,
            "value": world * steps / t["total_s"],
            "vcycle_dof_per_s": world * ndof * t["vcycles"] / t["total_s"]}
     if e2e:
@@ -647,7 +650,9 @@ def run_vk(args, config, cfg):
                   "f32": "f64 vectors, f32 patch inverses"}[args.prec],
         "data": "synthetic",
         "config": {"workload": desc, "ndof": main["ndof"], "levels": L, "k": k, "sweeps": sweeps, "rtol": rtol,
-                   "factor_prec": args.prec, "fgmres_loop": "host" if args.no_graph else "CUDA graph (WHILE node)",
+                   "factor_prec": args.prec,
+                   "fgmres_loop": "host" if args.no_graph else ("CUDA graph (WHILE node), programmatic dependent launch"
+                                                                if main["graph_pdl"] else "CUDA graph (WHILE node)"),
                    "rhs": "N(0,1), numpy default_rng(seed)",
                    "l2": "256 MiB buffer overwritten between timed solves (outside the per-solve events)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
@@ -925,6 +930,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven FGMRES loop instead of the whole-solve CUDA graph (for kernel profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-pdl", action="store_true", help="capture the solve graph with ordinary launches")
     ap.add_argument("--no-nested", action="store_true", help="cfg4: skip the nested records")
     ap.add_argument("--no-serving", action="store_true", help="cfg4: skip the nested serving record")
     ap.add_argument("--no-bdm", action="store_true", help="cfg4: skip the nested BDM records")

@@ -164,6 +164,12 @@ typedef struct vk_options {
                              over the same cells in the same order, so the patch matrices, inverses
                              and solves are bit-identical; only the setup cost differs
                              (vk_stats.setup_factor_ms)                                             */
+  int32_t graph_pdl;       /* 1 (default): the whole-solve graph's kernels are captured with
+                             programmatic dependent launch (each may be scheduled while its predecessor
+                             drains, and waits for that grid's completion before touching memory);
+                             if the driver refuses the capture, the graph is rebuilt without it
+                             (vk_stats.graph_pdl reports which).  0: ordinary launches.  Results are
+                             identical either way                                                    */
 } vk_options;
 
 /* Device memory provider.  alloc returns device memory of at least `bytes` (256-byte aligned) or
@@ -369,6 +375,7 @@ typedef struct vk_stats {
   double setup_factor_ms;  /* setup: summed CUDA-event time of the patch-matrix formation and
                               factorisation launches of every smoothed level (not reset)            */
   double setup_ms;         /* setup: host wall time of vk_setup (not reset)                         */
+  int32_t graph_pdl;       /* 1 if the whole-solve graph uses programmatic dependent launch          */
 } vk_stats;
 
 /* Zeroes the counters; time_kernels = 1 also brackets every finest-level patch-apply launch and

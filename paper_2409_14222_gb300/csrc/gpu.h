@@ -5,9 +5,44 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
 
 namespace vk {
 namespace gpu {
+
+// ---- programmatic dependent launch (inside the whole-solve graph) -------------------------------
+// While pdl_enabled() is set on the calling thread (during the capture of the FGMRES graph), the
+// solve-path launchers issue their kernels with programmatic stream serialisation: a kernel may be
+// scheduled while its predecessor drains, and every such kernel begins with pdl_wait(), which blocks
+// until the predecessor grid has completed and its writes are visible, before touching memory (so
+// read-after-write and write-after-read order is unchanged); pdl_trigger() then lets the next kernel
+// be scheduled.  Launched the ordinary way, both are no-ops.
+bool pdl_enabled();
+void set_pdl(bool on);
+
+template <typename... P, typename... A>
+inline void launch(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+  if (!pdl_enabled()) {
+    kernel<<<grid, block, smem, s>>>(std::forward<A>(args)...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#endif
 
 // Sliced ELLPACK with C = 32 / tpr rows per slice and tpr threads per row (SELL-C-sigma): rows are
 // permuted (sorted by length inside windows of 1024 rows) so the rows of a slice have similar

@@ -126,6 +126,8 @@ __device__ __forceinline__ void gemv_row(int row, const double* __restrict__ Min
 
 __global__ void __launch_bounds__(128) k_dense_gemv(const double* __restrict__ Minv, int n, int ld,
                                                     const double* __restrict__ b, double* __restrict__ x) {
+  pdl_wait();
+  pdl_trigger();
   gemv_row(blockIdx.x, Minv, n, ld, b, x);
 }
 
@@ -165,7 +167,7 @@ int group_dense_gemv(const GroupGemvArgs& a, cudaStream_t s) {
 }
 
 int dense_gemv(const double* Minv, int n, int ld, const double* b, double* x, cudaStream_t s) {
-  k_dense_gemv<<<n, 128, 0, s>>>(Minv, n, ld, b, x);
+  launch(k_dense_gemv, dim3(n), dim3(128), 0, s, Minv, n, ld, b, x);
   return 1;
 }
 

@@ -135,6 +135,8 @@ __global__ void k_scale_copy(const double* x, const double* __restrict__ sq, dou
 // ---------------- device-resident FGMRES kernels (iteration index read from FgState) -------------
 __global__ void k_fg_init(const double* __restrict__ sq, FgState* st, double* __restrict__ g,
                           double* __restrict__ hist, int kmax, cudaGraphConditionalHandle cond) {
+  pdl_wait();
+  pdl_trigger();
   const double beta = sqrt(*sq);
   for (int i = threadIdx.x; i <= kmax; i += blockDim.x) g[i] = 0.0;
   __syncthreads();
@@ -153,6 +155,8 @@ __global__ void k_fg_init(const double* __restrict__ sq, FgState* st, double* __
 }
 
 __global__ void k_fg_scale(double* v, const FgState* __restrict__ st, int n) {
+  pdl_wait();
+  pdl_trigger();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const double beta = st->beta;
   if (r < n && beta > 0.0 && isfinite(beta)) v[r] = v[r] / beta;
@@ -160,12 +164,16 @@ __global__ void k_fg_scale(double* v, const FgState* __restrict__ st, int n) {
 
 __global__ void k_fg_col_get(const double* __restrict__ V, int64_t ld, const FgState* __restrict__ st,
                              double* __restrict__ out, int n) {
+  pdl_wait();
+  pdl_trigger();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n) out[r] = V[ld * st->j + r];
 }
 
 __global__ void k_fg_col_put(const double* __restrict__ in, double* __restrict__ Z, int64_t ld,
                              const FgState* __restrict__ st, int n) {
+  pdl_wait();
+  pdl_trigger();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n) Z[ld * st->j + r] = in[r];
 }
@@ -179,6 +187,8 @@ constexpr int kFgVB = 8;
 __global__ void __launch_bounds__(kT) k_fg_mdot(const double* __restrict__ V, int64_t ld,
                                                 const FgState* __restrict__ st, const double* __restrict__ w,
                                                 int n, double* __restrict__ partial) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[kFgVB][kT / 32];
   const int j = st->j, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   {
@@ -213,6 +223,8 @@ __global__ void __launch_bounds__(kT) k_fg_mdot(const double* __restrict__ V, in
 
 __global__ void __launch_bounds__(kT) k_fg_mfin(const double* __restrict__ partial, const FgState* __restrict__ st,
                                                 double* __restrict__ H, int ldh, double* __restrict__ t2, int mode) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.x, j = st->j;
   if (i > j) return;
   double s = 0.0;
@@ -232,6 +244,8 @@ __global__ void __launch_bounds__(kT) k_fg_mfin(const double* __restrict__ parti
 __global__ void k_fg_maxpy(const double* __restrict__ V, int64_t ld, const FgState* __restrict__ st,
                            const double* __restrict__ H, int ldh, const double* __restrict__ t2, int mode,
                            double* __restrict__ w, int n) {
+  pdl_wait();
+  pdl_trigger();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int j = st->j;
@@ -244,6 +258,8 @@ __global__ void k_fg_maxpy(const double* __restrict__ V, int64_t ld, const FgSta
 
 __global__ void k_fg_normalize(const double* __restrict__ w, const double* __restrict__ sq, double* __restrict__ V,
                                int64_t ld, const FgState* __restrict__ st, double* __restrict__ H, int ldh, int n) {
+  pdl_wait();
+  pdl_trigger();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = st->j;
   const double nrm = sqrt(*sq);
@@ -254,6 +270,8 @@ __global__ void k_fg_normalize(const double* __restrict__ w, const double* __res
 __global__ void k_fg_givens(double* __restrict__ H, int ldh, double* __restrict__ cs, double* __restrict__ sn,
                             double* __restrict__ g, double* __restrict__ hist, FgState* st,
                             cudaGraphConditionalHandle cond) {
+  pdl_wait();
+  pdl_trigger();
   const int j = st->j;
   const double est = givens_column(H, ldh, cs, sn, g, hist, j);
   if (threadIdx.x == 0) {
@@ -269,6 +287,8 @@ __global__ void k_fg_givens(double* __restrict__ H, int ldh, double* __restrict_
 // Back substitution with one warp: y[i] = (g[i] - sum_{k>i} H[i][k] y[k]) / H[i][i].
 __global__ void k_fg_backsolve(const double* __restrict__ H, int ldh, const double* __restrict__ g,
                                const FgState* __restrict__ st, double* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ double ys[];
   const int m = st->j, lane = threadIdx.x;
   for (int i = m - 1; i >= 0; --i) {
@@ -283,6 +303,8 @@ __global__ void k_fg_backsolve(const double* __restrict__ H, int ldh, const doub
 
 __global__ void k_fg_combine(const double* __restrict__ Z, int64_t ldz, const FgState* __restrict__ st,
                              const double* __restrict__ y, double* __restrict__ x, int n) {
+  pdl_wait();
+  pdl_trigger();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int m = st->j;
@@ -291,7 +313,9 @@ __global__ void k_fg_combine(const double* __restrict__ Z, int64_t ldz, const Fg
   x[r] = s;
 }
 
-__global__ void k_fg_finish(FgState* st, const double* __restrict__ sq) { st->true_res = sqrt(*sq); }
+__global__ void k_fg_finish(FgState* st, const double* __restrict__ sq) {
+  pdl_wait();
+  pdl_trigger(); st->true_res = sqrt(*sq); }
 
 // ---- group forms: the same partitions, orders and trees as the single-solve kernels ------------
 // block (b, v) of the grid: member m and basis vector i of the concatenated vector list
@@ -437,55 +461,55 @@ int group_normalize_givens(const GroupGivensArgs& a, cudaStream_t s) {
 
 int fg_init(const double* sq, FgState* st, double* g, double* hist, int kmax, cudaGraphConditionalHandle cond,
             cudaStream_t s) {
-  k_fg_init<<<1, kT, 0, s>>>(sq, st, g, hist, kmax, cond);
+  launch(k_fg_init, dim3(1), dim3(kT), 0, s, sq, st, g, hist, kmax, cond);
   return 1;
 }
 
 int fg_scale(double* v, const FgState* st, int n, cudaStream_t s) {
-  k_fg_scale<<<(n + kT - 1) / kT, kT, 0, s>>>(v, st, n);
+  launch(k_fg_scale, dim3((n + kT - 1) / kT), dim3(kT), 0, s, v, st, n);
   return 1;
 }
 
 int fg_col_get(const double* V, int64_t ld, const FgState* st, double* out, int n, cudaStream_t s) {
-  k_fg_col_get<<<(n + kT - 1) / kT, kT, 0, s>>>(V, ld, st, out, n);
+  launch(k_fg_col_get, dim3((n + kT - 1) / kT), dim3(kT), 0, s, V, ld, st, out, n);
   return 1;
 }
 
 int fg_col_put(const double* in, double* Z, int64_t ld, const FgState* st, int n, cudaStream_t s) {
-  k_fg_col_put<<<(n + kT - 1) / kT, kT, 0, s>>>(in, Z, ld, st, n);
+  launch(k_fg_col_put, dim3((n + kT - 1) / kT), dim3(kT), 0, s, in, Z, ld, st, n);
   return 1;
 }
 
 int fg_cgs_pass(const double* V, int64_t ld, const FgState* st, double* w, int n, double* partial, double* H,
                 int ldh, double* t2, int kmax, int mode, cudaStream_t s) {
-  k_fg_mdot<<<dim3(kReduceBlocks, (kmax + kFgVB - 1) / kFgVB), kT, 0, s>>>(V, ld, st, w, n, partial);
-  k_fg_mfin<<<kmax, kT, 0, s>>>(partial, st, H, ldh, t2, mode);
-  k_fg_maxpy<<<(n + kT - 1) / kT, kT, 0, s>>>(V, ld, st, H, ldh, t2, mode, w, n);
+  launch(k_fg_mdot, dim3(dim3(kReduceBlocks, (kmax + kFgVB - 1) / kFgVB)), dim3(kT), 0, s, V, ld, st, w, n, partial);
+  launch(k_fg_mfin, dim3(kmax), dim3(kT), 0, s, partial, st, H, ldh, t2, mode);
+  launch(k_fg_maxpy, dim3((n + kT - 1) / kT), dim3(kT), 0, s, V, ld, st, H, ldh, t2, mode, w, n);
   return 3;
 }
 
 int fg_normalize(const double* w, const double* sq, double* V, int64_t ld, const FgState* st, double* H, int ldh,
                  int n, cudaStream_t s) {
-  k_fg_normalize<<<(n + kT - 1) / kT, kT, 0, s>>>(w, sq, V, ld, st, H, ldh, n);
+  launch(k_fg_normalize, dim3((n + kT - 1) / kT), dim3(kT), 0, s, w, sq, V, ld, st, H, ldh, n);
   return 1;
 }
 
 int fg_givens(double* H, int ldh, double* cs, double* sn, double* g, double* hist, FgState* st,
               cudaGraphConditionalHandle cond, cudaStream_t s) {
   // shared memory for the largest column: 3 * kmax + 2 doubles (ldh = kmax + 1)
-  k_fg_givens<<<1, 128, (3 * ldh + 2) * sizeof(double), s>>>(H, ldh, cs, sn, g, hist, st, cond);
+  launch(k_fg_givens, dim3(1), dim3(128), (3 * ldh + 2) * sizeof(double), s, H, ldh, cs, sn, g, hist, st, cond);
   return 1;
 }
 
 int fg_solution(const double* H, int ldh, const double* g, const double* Z, int64_t ld, const FgState* st,
                 double* y, double* x, int n, cudaStream_t s) {
-  k_fg_backsolve<<<1, 32, ldh * sizeof(double), s>>>(H, ldh, g, st, y);
-  k_fg_combine<<<(n + kT - 1) / kT, kT, 0, s>>>(Z, ld, st, y, x, n);
+  launch(k_fg_backsolve, dim3(1), dim3(32), ldh * sizeof(double), s, H, ldh, g, st, y);
+  launch(k_fg_combine, dim3((n + kT - 1) / kT), dim3(kT), 0, s, Z, ld, st, y, x, n);
   return 2;
 }
 
 int fg_finish(FgState* st, const double* sq, cudaStream_t s) {
-  k_fg_finish<<<1, 1, 0, s>>>(st, sq);
+  launch(k_fg_finish, dim3(1), dim3(1), 0, s, st, sq);
   return 1;
 }
 

@@ -333,6 +333,8 @@ __global__ void __launch_bounds__(256) k_patch_apply(int w0, int w1, const int* 
                                                      const FT* __restrict__ F, const double* __restrict__ r,
                                                      const float2* __restrict__ r2, const int* __restrict__ pos,
                                                      double* __restrict__ delta) {
+  pdl_wait();
+  pdl_trigger();
   const int nwarps = int((int64_t(gridDim.x) * blockDim.x) >> 5);
   const int lane = threadIdx.x & 31;
   for (int w = w0 + int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); w < w1; w += nwarps) {
@@ -491,6 +493,8 @@ __global__ void __launch_bounds__(256) k_patch_apply_sym(int w0, int w1, const i
                                                          const FT* __restrict__ F, const double* __restrict__ r,
                                                          const float2* __restrict__ r2, const int* __restrict__ pos,
                                                          double* __restrict__ delta) {
+  pdl_wait();
+  pdl_trigger();
   const int nwarps = int((int64_t(gridDim.x) * blockDim.x) >> 5);
   const int lane = threadIdx.x & 31;
   for (int w = w0 + int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); w < w1; w += nwarps) {
@@ -502,6 +506,8 @@ __global__ void __launch_bounds__(256) k_patch_apply_sym(int w0, int w1, const i
 
 // r = rh + rl with rh = fl32(r), rl = fl32(r - rh): the FP32-pair form of a residual, once per DoF.
 __global__ void k_split_pairs(const double* __restrict__ r, float2* __restrict__ r2, int n) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double v = r[i];
@@ -573,6 +579,8 @@ __global__ void __launch_bounds__(256) k_vanka_scatter(int ndof, const int* __re
                                                        double theta, double c1, double c2,
                                                        double* __restrict__ zout, double* __restrict__ d,
                                                        double* __restrict__ x) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ndof) return;
   scatter_dof<kPairs>(i, dptr, weight, dir, r, delta, mode, theta, c1, c2, zout, d, x);
@@ -632,7 +640,7 @@ template <int NBLO, int NBHI, typename FT>
 int launch_range(const Patches& P, const ApplySched& sc, int w0, int w1, const double* r, const float2* r2,
                  double* delta, cudaStream_t s) {
   if (w1 <= w0) return 0;
-  k_patch_apply<NBLO, NBHI, FT><<<apply_blocks(w1 - w0, sc, P.nsm), sc.threads, 0, s>>>(
+  launch(k_patch_apply<NBLO, NBHI, FT>, dim3(apply_blocks(w1 - w0, sc, P.nsm)), dim3(sc.threads), 0, s, 
       w0, w1, P.work, P.slot_ptr, P.slot_dofs, P.foff, static_cast<const FT*>(P.factors), r, r2, P.slot_pos, delta);
   return 1;
 }
@@ -641,7 +649,7 @@ template <int NTLO, int NTHI, typename FT>
 int launch_range_sym(const Patches& P, const ApplySched& sc, int w0, int w1, const double* r, const float2* r2,
                      double* delta, cudaStream_t s) {
   if (w1 <= w0) return 0;
-  k_patch_apply_sym<NTLO, NTHI, FT><<<apply_blocks(w1 - w0, sc, P.nsm), sc.threads, 0, s>>>(
+  launch(k_patch_apply_sym<NTLO, NTHI, FT>, dim3(apply_blocks(w1 - w0, sc, P.nsm)), dim3(sc.threads), 0, s, 
       w0, w1, P.work, P.slot_ptr, P.slot_dofs, P.foff, static_cast<const FT*>(P.factors), r, r2, P.slot_pos, delta);
   return 1;
 }
@@ -733,7 +741,7 @@ int patch_apply_sched(const Patches& P, const ApplySched& sc, const double* r, f
     return P.sym ? apply_sym_prec<float>(P, sc, r, nullptr, delta, s) : apply_prec<float>(P, sc, r, nullptr, delta, s);
   // FP32-pair inverses: split the residual once per DoF first
   const int n = P.ndof;
-  k_split_pairs<<<(n + 255) / 256, 256, 0, s>>>(r, r2, n);
+  launch(k_split_pairs, dim3((n + 255) / 256), dim3(256), 0, s, r, r2, n);
   return 1 + (P.sym ? apply_sym_prec<float2>(P, sc, r, r2, delta, s) : apply_prec<float2>(P, sc, r, r2, delta, s));
 }
 
@@ -777,10 +785,10 @@ int vanka_scatter(const Patches& P, int ndof, const uint8_t* dir, const double* 
                    int mode, double theta, double c1, double c2, double* out_z, double* d, double* x,
                    cudaStream_t s) {
   if (P.prec == 2)
-    k_vanka_scatter<true><<<(ndof + 255) / 256, 256, 0, s>>>(ndof, P.dof_ptr, P.weight, dir, r, delta, mode,
+    launch(k_vanka_scatter<true>, dim3((ndof + 255) / 256), dim3(256), 0, s, ndof, P.dof_ptr, P.weight, dir, r, delta, mode,
                                                              theta, c1, c2, out_z, d, x);
   else
-    k_vanka_scatter<false><<<(ndof + 255) / 256, 256, 0, s>>>(ndof, P.dof_ptr, P.weight, dir, r, delta, mode,
+    launch(k_vanka_scatter<false>, dim3((ndof + 255) / 256), dim3(256), 0, s, ndof, P.dof_ptr, P.weight, dir, r, delta, mode,
                                                               theta, c1, c2, out_z, d, x);
   return 1;
 }

@@ -67,6 +67,8 @@ __global__ void __launch_bounds__(kThreads) k_sell(int nslices, const int64_t* _
                                                    const double* __restrict__ val, const int* __restrict__ rowof,
                                                    const double* b, const uint8_t* __restrict__ mask,
                                                    const double* __restrict__ x, double* y) {
+  pdl_wait();
+  pdl_trigger();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= nslices) return;
   sell_slice<kMode, T>(warp, threadIdx.x & 31, sptr, sw, col, val, rowof, b, mask, x, y);
@@ -94,16 +96,16 @@ int launch_sell(const Sell& A, const double* b, const uint8_t* mask, const doubl
   const int g = blocks_for(int64_t(A.nslices) * 32);
   switch (A.tpr) {
     case 1:
-      k_sell<kMode, 1><<<g, kThreads, 0, s>>>(A.nslices, A.sptr, A.swidth, A.col, A.val, A.rowof, b, mask, x, y);
+      launch(k_sell<kMode, 1>, dim3(g), dim3(kThreads), 0, s, A.nslices, A.sptr, A.swidth, A.col, A.val, A.rowof, b, mask, x, y);
       break;
     case 2:
-      k_sell<kMode, 2><<<g, kThreads, 0, s>>>(A.nslices, A.sptr, A.swidth, A.col, A.val, A.rowof, b, mask, x, y);
+      launch(k_sell<kMode, 2>, dim3(g), dim3(kThreads), 0, s, A.nslices, A.sptr, A.swidth, A.col, A.val, A.rowof, b, mask, x, y);
       break;
     case 4:
-      k_sell<kMode, 4><<<g, kThreads, 0, s>>>(A.nslices, A.sptr, A.swidth, A.col, A.val, A.rowof, b, mask, x, y);
+      launch(k_sell<kMode, 4>, dim3(g), dim3(kThreads), 0, s, A.nslices, A.sptr, A.swidth, A.col, A.val, A.rowof, b, mask, x, y);
       break;
     default:
-      k_sell<kMode, 8><<<g, kThreads, 0, s>>>(A.nslices, A.sptr, A.swidth, A.col, A.val, A.rowof, b, mask, x, y);
+      launch(k_sell<kMode, 8>, dim3(g), dim3(kThreads), 0, s, A.nslices, A.sptr, A.swidth, A.col, A.val, A.rowof, b, mask, x, y);
       break;
   }
   return 1;
@@ -125,6 +127,8 @@ __device__ double block_sum(double v) {
 __global__ void __launch_bounds__(kThreads) k_dot_partials(const double* __restrict__ x,
                                                            const double* __restrict__ y, int n,
                                                            double* __restrict__ partial) {
+  pdl_wait();
+  pdl_trigger();
   double s = 0.0;
   for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += kReduceBlocks * kThreads)
     s = fma(x[i], y[i], s);
@@ -134,6 +138,8 @@ __global__ void __launch_bounds__(kThreads) k_dot_partials(const double* __restr
 
 __global__ void __launch_bounds__(kThreads) k_sum_partials(const double* __restrict__ x, int n,
                                                            double* __restrict__ partial) {
+  pdl_wait();
+  pdl_trigger();
   double s = 0.0;
   for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += kReduceBlocks * kThreads) s += x[i];
   s = block_sum<kThreads>(s);
@@ -142,6 +148,8 @@ __global__ void __launch_bounds__(kThreads) k_sum_partials(const double* __restr
 
 __global__ void __launch_bounds__(kThreads) k_finalize(const double* __restrict__ partial, int nparts,
                                                        double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   double s = 0.0;
   for (int i = threadIdx.x; i < nparts; i += kThreads) s += partial[i];
   s = block_sum<kThreads>(s);
@@ -149,17 +157,23 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const double* __restrict_
 }
 
 __global__ void k_subtract_mean(double* __restrict__ x, int len, const double* __restrict__ sum) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= len) return;
   x[i] -= *sum / double(len);
 }
 
 __global__ void k_fill(double* x, double v, int64_t n) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (i < n) x[i] = v;
 }
 
 __global__ void k_copy(double* __restrict__ d, const double* __restrict__ s, int64_t n) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (i < n) d[i] = s[i];
 }
@@ -185,6 +199,13 @@ __global__ void k_divide(double a, double* __restrict__ x, int n) {
 }
 
 }  // namespace
+
+namespace {
+thread_local bool t_pdl = false;
+}
+
+bool pdl_enabled() { return t_pdl; }
+void set_pdl(bool on) { t_pdl = on; }
 
 int divide(double a, double* x, int n, cudaStream_t s) {
   if (n <= 0) return 0;
@@ -231,33 +252,33 @@ int sell_prolong_add(const Sell& P, const double* ec, double* x, cudaStream_t s)
 
 
 int dot_partials(const double* x, const double* y, int n, double* partial, cudaStream_t s) {
-  k_dot_partials<<<kReduceBlocks, kThreads, 0, s>>>(x, y, n, partial);
+  launch(k_dot_partials, dim3(kReduceBlocks), dim3(kThreads), 0, s, x, y, n, partial);
   return 1;
 }
 
 int finalize_sum(const double* partial, int nparts, double* out, cudaStream_t s) {
-  k_finalize<<<1, kThreads, 0, s>>>(partial, nparts, out);
+  launch(k_finalize, dim3(1), dim3(kThreads), 0, s, partial, nparts, out);
   return 1;
 }
 
 int pressure_project(double* x, int off, int len, double* scratch_partial, double* scratch_sum,
                       cudaStream_t s) {
   if (len <= 0) return 0;
-  k_sum_partials<<<kReduceBlocks, kThreads, 0, s>>>(x + off, len, scratch_partial);
-  k_finalize<<<1, kThreads, 0, s>>>(scratch_partial, kReduceBlocks, scratch_sum);
-  k_subtract_mean<<<blocks_for(len), kThreads, 0, s>>>(x + off, len, scratch_sum);
+  launch(k_sum_partials, dim3(kReduceBlocks), dim3(kThreads), 0, s, x + off, len, scratch_partial);
+  launch(k_finalize, dim3(1), dim3(kThreads), 0, s, scratch_partial, kReduceBlocks, scratch_sum);
+  launch(k_subtract_mean, dim3(blocks_for(len)), dim3(kThreads), 0, s, x + off, len, scratch_sum);
   return 3;
 }
 
 int fill(double* x, double v, int64_t n, cudaStream_t s) {
   if (n <= 0) return 0;
-  k_fill<<<blocks_for(n), kThreads, 0, s>>>(x, v, n);
+  launch(k_fill, dim3(blocks_for(n)), dim3(kThreads), 0, s, x, v, n);
   return 1;
 }
 
 int copy(double* dst, const double* src, int64_t n, cudaStream_t s) {
   if (n <= 0) return 0;
-  k_copy<<<blocks_for(n), kThreads, 0, s>>>(dst, src, n);
+  launch(k_copy, dim3(blocks_for(n)), dim3(kThreads), 0, s, dst, src, n);
   return 1;
 }
 

@@ -339,6 +339,7 @@ struct vk_hierarchy {
   cudaGraphExec_t gexec = nullptr;
   cudaGraphConditionalHandle cond = 0;
   int64_t g_pro = 0, g_body = 0, g_epi = 0;   // kernels per prologue / iteration / epilogue
+  int graph_pdl = 0;                          // 1: the graph was captured with programmatic launches
   // vk_solve_batch workspace (finest level, FP64, 16 interleaved right-hand sides)
   int kb = 0;
   int64_t ldb = 0;
@@ -414,6 +415,7 @@ void validate(const vk_problem* p, const vk_options* o) {
   if (o->spmv_warps < 1 || o->spmv_warps > 4096) raise(VK_ERR_ARG, "spmv_warps must be in 1..4096");
   if (o->batch_coarse_fp32 != 0 && o->batch_coarse_fp32 != 1) raise(VK_ERR_ARG, "batch_coarse_fp32 must be 0 or 1");
   if (o->test_singular_patch < -1) raise(VK_ERR_ARG, "test_singular_patch must be -1 or a patch id");
+  if (o->graph_pdl != 0 && o->graph_pdl != 1) raise(VK_ERR_ARG, "graph_pdl must be 0 or 1");
   if (o->patch_assembly != VK_ASSEMBLY_MATRIX_FULL && o->patch_assembly != VK_ASSEMBLY_MATRIX_FREE)
     raise(VK_ERR_ARG, "bad patch_assembly");
   if (p->cell == VK_CELL_BDM && o->patch_assembly != VK_ASSEMBLY_MATRIX_FULL)
@@ -1122,11 +1124,29 @@ int solve_impl(vk_hierarchy* h, const double* b, double* x, double rtol, int max
 // history to pinned host memory).  Built once per hierarchy; only bh / xh are bound.
 void build_graph_locked(vk_hierarchy* h);
 
+void build_graph_attempt(vk_hierarchy* h, bool pdl);
+
+// Captures the graph with programmatic dependent launch when the options ask for it; a driver that
+// refuses such a capture gets the graph rebuilt with ordinary launches.
 void build_graph(vk_hierarchy* h) {
   std::lock_guard<std::mutex> lock(g_device_mu);
+  const bool want = h->opt.graph_pdl == 1;
+  try {
+    build_graph_attempt(h, want);
+  } catch (...) {
+    if (!want) throw;
+    build_graph_attempt(h, false);
+  }
+}
+
+void build_graph_attempt(vk_hierarchy* h, bool pdl) {
+  vk::gpu::set_pdl(pdl);
   try {
     build_graph_locked(h);
+    vk::gpu::set_pdl(false);
+    h->graph_pdl = pdl ? 1 : 0;
   } catch (...) {
+    vk::gpu::set_pdl(false);
     // leave no stream in capture mode and no half-built graph behind
     cudaStreamCaptureStatus st;
     for (cudaStream_t c : {h->cap1, h->cap0})
@@ -1474,6 +1494,7 @@ void vk_default_options(vk_options* o) {
   o->batch_engine = VK_ENGINE_TCGEN05;
   o->spmv_warps = 48;
   o->test_singular_patch = -1;
+  o->graph_pdl = 1;
 }
 
 int vk_check_problem(const vk_problem* p, const vk_options* o) {
@@ -1823,6 +1844,7 @@ int vk_stats_read(vk_hierarchy* h, vk_stats* out) {
     out->batch_spmv_bytes = h->bspmv_bytes;
     out->setup_factor_ms = h->factor_ms;
     out->setup_ms = h->setup_ms;
+    out->graph_pdl = h->graph_pdl;
     return VK_OK;
   });
 }

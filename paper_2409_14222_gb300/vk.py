@@ -78,7 +78,7 @@ class vk_options(ctypes.Structure):
                 ("apply_schedule", ctypes.c_int32), ("batch_engine", ctypes.c_int32),
                 ("test_expire_wait", ctypes.c_int32), ("spmv_warps", ctypes.c_int32),
                 ("batch_coarse_fp32", ctypes.c_int32), ("test_singular_patch", ctypes.c_int32),
-                ("patch_assembly", ctypes.c_int32)]
+                ("patch_assembly", ctypes.c_int32), ("graph_pdl", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -101,7 +101,7 @@ class vk_stats(ctypes.Structure):
                 ("batch_apply_bytes", ctypes.c_double), ("batch_apply_flops", ctypes.c_double),
                 ("spmv_launches", ctypes.c_int64), ("spmv_ms", ctypes.c_double), ("spmv_bytes", ctypes.c_double),
                 ("batch_spmv_bytes", ctypes.c_double), ("setup_factor_ms", ctypes.c_double),
-                ("setup_ms", ctypes.c_double)]
+                ("setup_ms", ctypes.c_double), ("graph_pdl", ctypes.c_int32)]
 
 
 class vk_server_config(ctypes.Structure):

@@ -275,6 +275,21 @@ def test_graph_and_host_loop_paths_agree(vk, case):
     assert sg["launches"] > 0 and sh["launches"] > 0
 
 
+def test_graph_with_and_without_programmatic_launch_agree(vk):
+    # programmatic dependent launch only lets a kernel be scheduled early; each kernel waits for its
+    # predecessor's completion before touching memory, so the solves are bit-identical
+    H, G = pair(vk, (2, 3, 2), inject=False)
+    G0 = vk.Hierarchy(2, 3, 2, options=vk.default_options(graph_pdl=0))
+    b = si.rhs_normal(H.finest.space.ndof, 33)
+    x1, x0 = torch.zeros_like(dev(b)), torch.zeros_like(dev(b))
+    o1 = G.solve(dev(b), x1, rtol=1e-10)
+    o0 = G0.solve(dev(b), x0, rtol=1e-10)
+    assert G.stats()["graph_pdl"] == 1 and G0.stats()["graph_pdl"] == 0
+    assert o1["iterations"] == o0["iterations"]
+    assert np.array_equal(o1["history"], o0["history"])
+    assert torch.equal(x1, x0)
+
+
 def test_host_buffer_solve_equals_device_solve(vk):
     H, G = pair(vk, (2, 3, 2), inject=False)
     n = H.finest.space.ndof
