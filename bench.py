@@ -396,8 +396,8 @@ def make_options(vk, args, sweeps):
         opts.factor_prec = vk.VK_PREC_F64E
     if args.no_graph:
         opts.use_graph = 0
-    if args.no_pdl:
-        opts.graph_pdl = 0
+    if args.pdl:
+        opts.graph_pdl = 1
     if args.spmv_warps:
         opts.spmv_warps = args.spmv_warps
     return opts
@@ -930,7 +930,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven FGMRES loop instead of the whole-solve CUDA graph (for kernel profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-pdl", action="store_true", help="capture the solve graph with ordinary launches")
+    ap.add_argument("--pdl", action="store_true", help="capture the solve graph with programmatic dependent launch")
     ap.add_argument("--no-nested", action="store_true", help="cfg4: skip the nested records")
     ap.add_argument("--no-serving", action="store_true", help="cfg4: skip the nested serving record")
     ap.add_argument("--no-bdm", action="store_true", help="cfg4: skip the nested BDM records")

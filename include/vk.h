@@ -164,12 +164,13 @@ typedef struct vk_options {
                              over the same cells in the same order, so the patch matrices, inverses
                              and solves are bit-identical; only the setup cost differs
                              (vk_stats.setup_factor_ms)                                             */
-  int32_t graph_pdl;       /* 1 (default): the whole-solve graph's kernels are captured with
-                             programmatic dependent launch (each may be scheduled while its predecessor
-                             drains, and waits for that grid's completion before touching memory);
+  int32_t graph_pdl;       /* 1: the whole-solve graph's kernels are captured with programmatic
+                             dependent launch (each may be launched before its predecessor has fully
+                             retired, and waits for that grid's completion before touching memory);
                              if the driver refuses the capture, the graph is rebuilt without it
-                             (vk_stats.graph_pdl reports which).  0: ordinary launches.  Results are
-                             identical either way                                                    */
+                             (vk_stats.graph_pdl reports which).  0 (default): ordinary launches —
+                             measured on GB300 no faster at 128x128 or 512x512.  Results are identical
+                             either way                                                              */
 } vk_options;
 
 /* Device memory provider.  alloc returns device memory of at least `bytes` (256-byte aligned) or

@@ -10,13 +10,14 @@
 namespace vk {
 namespace gpu {
 
-// ---- programmatic dependent launch (inside the whole-solve graph) -------------------------------
+// ---- programmatic dependent launch (inside the whole-solve graph, vk_options.graph_pdl) ----------
 // While pdl_enabled() is set on the calling thread (during the capture of the FGMRES graph), the
 // solve-path launchers issue their kernels with programmatic stream serialisation: a kernel may be
-// scheduled while its predecessor drains, and every such kernel begins with pdl_wait(), which blocks
-// until the predecessor grid has completed and its writes are visible, before touching memory (so
-// read-after-write and write-after-read order is unchanged); pdl_trigger() then lets the next kernel
-// be scheduled.  Launched the ordinary way, both are no-ops.
+// launched before its predecessor has fully retired, and every such kernel begins with pdl_wait(),
+// which blocks until the predecessor grid has completed and its writes are visible, before touching
+// memory (so read-after-write and write-after-read order is unchanged).  Launched the ordinary way,
+// pdl_wait() is a no-op.  (Triggering the next launch at the start of each kernel was measured slower:
+// the early grids took SM slots from the running one.)
 bool pdl_enabled();
 void set_pdl(bool on);
 
@@ -41,7 +42,6 @@ inline void launch(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cud
 
 #ifdef __CUDACC__
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 #endif
 
 // Sliced ELLPACK with C = 32 / tpr rows per slice and tpr threads per row (SELL-C-sigma): rows are

@@ -127,7 +127,6 @@ __device__ __forceinline__ void gemv_row(int row, const double* __restrict__ Min
 __global__ void __launch_bounds__(128) k_dense_gemv(const double* __restrict__ Minv, int n, int ld,
                                                     const double* __restrict__ b, double* __restrict__ x) {
   pdl_wait();
-  pdl_trigger();
   gemv_row(blockIdx.x, Minv, n, ld, b, x);
 }
 

@@ -136,7 +136,6 @@ __global__ void k_scale_copy(const double* x, const double* __restrict__ sq, dou
 __global__ void k_fg_init(const double* __restrict__ sq, FgState* st, double* __restrict__ g,
                           double* __restrict__ hist, int kmax, cudaGraphConditionalHandle cond) {
   pdl_wait();
-  pdl_trigger();
   const double beta = sqrt(*sq);
   for (int i = threadIdx.x; i <= kmax; i += blockDim.x) g[i] = 0.0;
   __syncthreads();
@@ -156,7 +155,6 @@ __global__ void k_fg_init(const double* __restrict__ sq, FgState* st, double* __
 
 __global__ void k_fg_scale(double* v, const FgState* __restrict__ st, int n) {
   pdl_wait();
-  pdl_trigger();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const double beta = st->beta;
   if (r < n && beta > 0.0 && isfinite(beta)) v[r] = v[r] / beta;
@@ -165,7 +163,6 @@ __global__ void k_fg_scale(double* v, const FgState* __restrict__ st, int n) {
 __global__ void k_fg_col_get(const double* __restrict__ V, int64_t ld, const FgState* __restrict__ st,
                              double* __restrict__ out, int n) {
   pdl_wait();
-  pdl_trigger();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n) out[r] = V[ld * st->j + r];
 }
@@ -173,7 +170,6 @@ __global__ void k_fg_col_get(const double* __restrict__ V, int64_t ld, const FgS
 __global__ void k_fg_col_put(const double* __restrict__ in, double* __restrict__ Z, int64_t ld,
                              const FgState* __restrict__ st, int n) {
   pdl_wait();
-  pdl_trigger();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n) Z[ld * st->j + r] = in[r];
 }
@@ -188,7 +184,6 @@ __global__ void __launch_bounds__(kT) k_fg_mdot(const double* __restrict__ V, in
                                                 const FgState* __restrict__ st, const double* __restrict__ w,
                                                 int n, double* __restrict__ partial) {
   pdl_wait();
-  pdl_trigger();
   __shared__ double sh[kFgVB][kT / 32];
   const int j = st->j, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   {
@@ -224,7 +219,6 @@ __global__ void __launch_bounds__(kT) k_fg_mdot(const double* __restrict__ V, in
 __global__ void __launch_bounds__(kT) k_fg_mfin(const double* __restrict__ partial, const FgState* __restrict__ st,
                                                 double* __restrict__ H, int ldh, double* __restrict__ t2, int mode) {
   pdl_wait();
-  pdl_trigger();
   const int i = blockIdx.x, j = st->j;
   if (i > j) return;
   double s = 0.0;
@@ -245,7 +239,6 @@ __global__ void k_fg_maxpy(const double* __restrict__ V, int64_t ld, const FgSta
                            const double* __restrict__ H, int ldh, const double* __restrict__ t2, int mode,
                            double* __restrict__ w, int n) {
   pdl_wait();
-  pdl_trigger();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int j = st->j;
@@ -259,7 +252,6 @@ __global__ void k_fg_maxpy(const double* __restrict__ V, int64_t ld, const FgSta
 __global__ void k_fg_normalize(const double* __restrict__ w, const double* __restrict__ sq, double* __restrict__ V,
                                int64_t ld, const FgState* __restrict__ st, double* __restrict__ H, int ldh, int n) {
   pdl_wait();
-  pdl_trigger();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = st->j;
   const double nrm = sqrt(*sq);
@@ -271,7 +263,6 @@ __global__ void k_fg_givens(double* __restrict__ H, int ldh, double* __restrict_
                             double* __restrict__ g, double* __restrict__ hist, FgState* st,
                             cudaGraphConditionalHandle cond) {
   pdl_wait();
-  pdl_trigger();
   const int j = st->j;
   const double est = givens_column(H, ldh, cs, sn, g, hist, j);
   if (threadIdx.x == 0) {
@@ -288,7 +279,6 @@ __global__ void k_fg_givens(double* __restrict__ H, int ldh, double* __restrict_
 __global__ void k_fg_backsolve(const double* __restrict__ H, int ldh, const double* __restrict__ g,
                                const FgState* __restrict__ st, double* __restrict__ y) {
   pdl_wait();
-  pdl_trigger();
   extern __shared__ double ys[];
   const int m = st->j, lane = threadIdx.x;
   for (int i = m - 1; i >= 0; --i) {
@@ -304,7 +294,6 @@ __global__ void k_fg_backsolve(const double* __restrict__ H, int ldh, const doub
 __global__ void k_fg_combine(const double* __restrict__ Z, int64_t ldz, const FgState* __restrict__ st,
                              const double* __restrict__ y, double* __restrict__ x, int n) {
   pdl_wait();
-  pdl_trigger();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int m = st->j;
@@ -315,7 +304,8 @@ __global__ void k_fg_combine(const double* __restrict__ Z, int64_t ldz, const Fg
 
 __global__ void k_fg_finish(FgState* st, const double* __restrict__ sq) {
   pdl_wait();
-  pdl_trigger(); st->true_res = sqrt(*sq); }
+  st->true_res = sqrt(*sq);
+}
 
 // ---- group forms: the same partitions, orders and trees as the single-solve kernels ------------
 // block (b, v) of the grid: member m and basis vector i of the concatenated vector list

@@ -334,7 +334,6 @@ __global__ void __launch_bounds__(256) k_patch_apply(int w0, int w1, const int* 
                                                      const float2* __restrict__ r2, const int* __restrict__ pos,
                                                      double* __restrict__ delta) {
   pdl_wait();
-  pdl_trigger();
   const int nwarps = int((int64_t(gridDim.x) * blockDim.x) >> 5);
   const int lane = threadIdx.x & 31;
   for (int w = w0 + int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); w < w1; w += nwarps) {
@@ -494,7 +493,6 @@ __global__ void __launch_bounds__(256) k_patch_apply_sym(int w0, int w1, const i
                                                          const float2* __restrict__ r2, const int* __restrict__ pos,
                                                          double* __restrict__ delta) {
   pdl_wait();
-  pdl_trigger();
   const int nwarps = int((int64_t(gridDim.x) * blockDim.x) >> 5);
   const int lane = threadIdx.x & 31;
   for (int w = w0 + int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); w < w1; w += nwarps) {
@@ -507,7 +505,6 @@ __global__ void __launch_bounds__(256) k_patch_apply_sym(int w0, int w1, const i
 // r = rh + rl with rh = fl32(r), rl = fl32(r - rh): the FP32-pair form of a residual, once per DoF.
 __global__ void k_split_pairs(const double* __restrict__ r, float2* __restrict__ r2, int n) {
   pdl_wait();
-  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double v = r[i];
@@ -580,7 +577,6 @@ __global__ void __launch_bounds__(256) k_vanka_scatter(int ndof, const int* __re
                                                        double* __restrict__ zout, double* __restrict__ d,
                                                        double* __restrict__ x) {
   pdl_wait();
-  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ndof) return;
   scatter_dof<kPairs>(i, dptr, weight, dir, r, delta, mode, theta, c1, c2, zout, d, x);

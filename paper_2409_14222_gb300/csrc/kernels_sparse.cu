@@ -68,7 +68,6 @@ __global__ void __launch_bounds__(kThreads) k_sell(int nslices, const int64_t* _
                                                    const double* b, const uint8_t* __restrict__ mask,
                                                    const double* __restrict__ x, double* y) {
   pdl_wait();
-  pdl_trigger();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= nslices) return;
   sell_slice<kMode, T>(warp, threadIdx.x & 31, sptr, sw, col, val, rowof, b, mask, x, y);
@@ -128,7 +127,6 @@ __global__ void __launch_bounds__(kThreads) k_dot_partials(const double* __restr
                                                            const double* __restrict__ y, int n,
                                                            double* __restrict__ partial) {
   pdl_wait();
-  pdl_trigger();
   double s = 0.0;
   for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += kReduceBlocks * kThreads)
     s = fma(x[i], y[i], s);
@@ -139,7 +137,6 @@ __global__ void __launch_bounds__(kThreads) k_dot_partials(const double* __restr
 __global__ void __launch_bounds__(kThreads) k_sum_partials(const double* __restrict__ x, int n,
                                                            double* __restrict__ partial) {
   pdl_wait();
-  pdl_trigger();
   double s = 0.0;
   for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += kReduceBlocks * kThreads) s += x[i];
   s = block_sum<kThreads>(s);
@@ -149,7 +146,6 @@ __global__ void __launch_bounds__(kThreads) k_sum_partials(const double* __restr
 __global__ void __launch_bounds__(kThreads) k_finalize(const double* __restrict__ partial, int nparts,
                                                        double* __restrict__ out) {
   pdl_wait();
-  pdl_trigger();
   double s = 0.0;
   for (int i = threadIdx.x; i < nparts; i += kThreads) s += partial[i];
   s = block_sum<kThreads>(s);
@@ -158,7 +154,6 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const double* __restrict_
 
 __global__ void k_subtract_mean(double* __restrict__ x, int len, const double* __restrict__ sum) {
   pdl_wait();
-  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= len) return;
   x[i] -= *sum / double(len);
@@ -166,14 +161,12 @@ __global__ void k_subtract_mean(double* __restrict__ x, int len, const double* _
 
 __global__ void k_fill(double* x, double v, int64_t n) {
   pdl_wait();
-  pdl_trigger();
   const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (i < n) x[i] = v;
 }
 
 __global__ void k_copy(double* __restrict__ d, const double* __restrict__ s, int64_t n) {
   pdl_wait();
-  pdl_trigger();
   const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (i < n) d[i] = s[i];
 }

@@ -1494,7 +1494,7 @@ void vk_default_options(vk_options* o) {
   o->batch_engine = VK_ENGINE_TCGEN05;
   o->spmv_warps = 48;
   o->test_singular_patch = -1;
-  o->graph_pdl = 1;
+  o->graph_pdl = 0;
 }
 
 int vk_check_problem(const vk_problem* p, const vk_options* o) {

@@ -278,7 +278,8 @@ def test_graph_and_host_loop_paths_agree(vk, case):
 def test_graph_with_and_without_programmatic_launch_agree(vk):
     # programmatic dependent launch only lets a kernel be scheduled early; each kernel waits for its
     # predecessor's completion before touching memory, so the solves are bit-identical
-    H, G = pair(vk, (2, 3, 2), inject=False)
+    H = solver.Hierarchy(2, 3, 2)
+    G = vk.Hierarchy(2, 3, 2, options=vk.default_options(graph_pdl=1))
     G0 = vk.Hierarchy(2, 3, 2, options=vk.default_options(graph_pdl=0))
     b = si.rhs_normal(H.finest.space.ndof, 33)
     x1, x0 = torch.zeros_like(dev(b)), torch.zeros_like(dev(b))
