@@ -16,8 +16,9 @@ from oracle import bdm, fem, solver
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# k = 1 (19-DoF interior patches), 2 (42), 3 (74), 4 (115): coarsest 2 x 2, two or three levels
-CASES = [(2, 2, 1), (2, 3, 1), (2, 2, 2), (2, 3, 2), (2, 2, 3), (2, 2, 4)]
+# k = 1 (19-DoF interior patches), 2 (42), 3 (74), 4 (115): coarsest 2 x 2, two or three levels;
+# k = 5 on 1 x 1 -> 2 x 2 (patches of up to 141 DoFs, the fifth size class of the patch kernels)
+CASES = [(2, 2, 1), (2, 3, 1), (2, 2, 2), (2, 3, 2), (2, 2, 3), (2, 2, 4), (1, 2, 5)]
 
 
 @pytest.fixture(scope="module")
