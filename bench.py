@@ -5,9 +5,11 @@ One step = one FGMRES solve to 1e-8 relative residual (zero initial guess, V(1,1
 Chebyshev-accelerated matrix-full Vanka smoothing, FP64) of a seeded N(0,1) right-hand side already
 resident in HBM.  The hierarchy (assembly, patch inverses, coarse inverse, eigenvalue estimates) is
 built once before timing and kept resident, as a solver service would.  The default line also nests
-two sub-records measured in the same run: the 16x16 -> 128x128 P2/P1 workload (148,739 DoFs) and the
-16-right-hand-side mixed-precision solve of the 512x512 workload (BF16 patch inverses on the tensor
-cores, FP32 V-cycle, FP64 FGMRES per column) with its error against the FP64 solutions.
+sub-records measured in the same run: the 16x16 -> 128x128 P2/P1 workload (148,739 DoFs); the
+512x512 workload with FP32-pair patch inverses; its 16-right-hand-side mixed-precision solve (BF16
+patch inverses on the tensor cores, FP32 V-cycle, FP64 FGMRES per column) with its error against the
+FP64 solutions; a Poisson stream of solve requests through the solve service; (BDM_k, dP_{k-1}) on
+5x5 -> 80x80 for k = 2..5; and matrix-full against matrix-free patch setup.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vk|reference] [--config cfg4]
 
@@ -453,7 +455,7 @@ def summary_of(rec, cfg, args, hbm, peak_kind, fp64_tflops, config, prec=None):
 
 
 def batch_record(vk, torch, si, cfg, args, flush, hbm, peaks, peak_kind, G64=None, fp64_value=None,
-                 engine=None, coarse_fp32=0, steps=None):
+                 engine=None, coarse_fp32=0, steps=None, profile=False):
     """16 right-hand sides per step through vk_solve_batch: FP32 V-cycle with BF16 (or FP16) scaled
     patch inverses on the tensor cores, FP64 coarsest solve, FP64 FGMRES per column.  With G64 (the
     FP64 single-right-hand-side hierarchy of the same workload) the first four columns are compared
@@ -479,6 +481,8 @@ def batch_record(vk, torch, si, cfg, args, flush, hbm, peaks, peak_kind, G64=Non
     Gb.stats_reset(time_kernels=False)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
     iters = []
+    if profile:
+        torch.cuda.profiler.start()          # a profiler started with --profile-from-start off sees only this
     for st in range(nsteps):
         flush.fill_(float(st))
         ev[st][0].record(stream)
@@ -488,6 +492,8 @@ def batch_record(vk, torch, si, cfg, args, flush, hbm, peaks, peak_kind, G64=Non
         if not all(o["converged"] for o in out):
             raise RuntimeError("a column did not converge")
     torch.cuda.synchronize()
+    if profile:
+        torch.cuda.profiler.stop()
     stt = Gb.stats()
     times_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(times_ms) / 1e3
@@ -706,7 +712,7 @@ def run_batch(args, config, cfg):
     clk = ClockSampler(0)
     with clk:
         rec = batch_record(vk, torch, si, cfg, args, flush, hbm, peaks, peak_kind, G64=G64, fp64_value=fp64_value,
-                           steps=args.steps)
+                           steps=args.steps, profile=True)
     other = "mma_sync" if args.engine == "tcgen05" else "tcgen05"
     rec_other = batch_record(vk, torch, si, cfg, args, flush, hbm, peaks, peak_kind, engine=other, steps=3)
     rec_c32 = batch_record(vk, torch, si, cfg, args, flush, hbm, peaks, peak_kind, coarse_fp32=1, steps=3)
