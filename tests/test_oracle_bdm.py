@@ -189,7 +189,7 @@ def test_interior_moment_functions_are_orthogonal_and_span_nedelec(k):
     assert mat(Q).rank() == mat(M).rank() == mat(Q + M).rank() == len(M)
 
 
-@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
 def test_penalty_makes_the_form_coercive_with_margin(k):
     # alpha = (k+1)(k+2) is "sufficiently large" (Sec. 2.1): the velocity block is positive definite on
     # the free DoFs, while a quarter of it loses coercivity (the bound is not vacuous)
