@@ -117,6 +117,8 @@ constexpr int kReduceBlocks = 256;
 int dot_partials(const double* x, const double* y, int n, double* partial, cudaStream_t s);
 int finalize_sum(const double* partial, int nparts, double* out, cudaStream_t s);
 // x[off..off+len) -= mean of that range (mean from a device scalar: sum / len)
+// scratch_sum = sum of x[off .. off+len) (the first two kernels of pressure_project)
+int pressure_sum(const double* x, int off, int len, double* scratch_partial, double* scratch_sum, cudaStream_t s);
 int pressure_project(double* x, int off, int len, double* scratch_partial, double* scratch_sum,
                       cudaStream_t s);
 int fill(double* x, double v, int64_t n, cudaStream_t s);
@@ -212,15 +214,16 @@ struct FgState {
 // beta = sqrt(*sq); g = (beta, 0, ...); hist[0] = beta; j = 0; sets the loop condition.
 int fg_init(const double* sq, FgState* st, double* g, double* hist, int kmax, cudaGraphConditionalHandle cond,
             cudaStream_t s);
-int fg_scale(double* v, const FgState* st, int n, cudaStream_t s);                       // v /= beta
-int fg_col_get(const double* V, int64_t ld, const FgState* st, double* out, int n, cudaStream_t s);  // out = V[j]
-int fg_col_put(const double* in, double* Z, int64_t ld, const FgState* st, int n, cudaStream_t s);   // Z[j] = in
+int fg_scale(double* v, const FgState* st, int n, double* copy, cudaStream_t s);  // v /= beta; copy = v
 // one classical Gram-Schmidt pass against V[0..j]: mode 0 writes H[:, j], mode 1 adds to it
 int fg_cgs_pass(const double* V, int64_t ld, const FgState* st, double* w, int n, double* partial, double* H,
                 int ldh, double* t2, int kmax, int mode, cudaStream_t s);
 // V[j+1] = w / sqrt(*sq), H[j+1][j] = sqrt(*sq)
 int fg_normalize(const double* w, const double* sq, double* V, int64_t ld, const FgState* st, double* H, int ldh,
-                 int n, cudaStream_t s);
+                 int n, double* copy, cudaStream_t s);   // also copy = V[j+1], the next V-cycle input
+// z's pressure mean removed and z stored as Z[j] (pressure sum, then one fused kernel)
+int fg_project_put(double* z, double* Z, int64_t ld, const FgState* st, int n, int n_u, double* partial,
+                   double* sum, cudaStream_t s);
 // Givens update of column j, residual history, convergence flags, j += 1, loop condition.
 int fg_givens(double* H, int ldh, double* cs, double* sn, double* g, double* hist, FgState* st,
               cudaGraphConditionalHandle cond, cudaStream_t s);

@@ -153,25 +153,18 @@ __global__ void k_fg_init(const double* __restrict__ sq, FgState* st, double* __
   }
 }
 
-__global__ void k_fg_scale(double* v, const FgState* __restrict__ st, int n) {
+// v /= beta, and the same values into copy (the V-cycle input of the first iteration)
+__global__ void k_fg_scale(double* v, const FgState* __restrict__ st, int n, double* __restrict__ copy) {
   pdl_wait();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
   const double beta = st->beta;
-  if (r < n && beta > 0.0 && isfinite(beta)) v[r] = v[r] / beta;
-}
-
-__global__ void k_fg_col_get(const double* __restrict__ V, int64_t ld, const FgState* __restrict__ st,
-                             double* __restrict__ out, int n) {
-  pdl_wait();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < n) out[r] = V[ld * st->j + r];
-}
-
-__global__ void k_fg_col_put(const double* __restrict__ in, double* __restrict__ Z, int64_t ld,
-                             const FgState* __restrict__ st, int n) {
-  pdl_wait();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < n) Z[ld * st->j + r] = in[r];
+  double x = v[r];
+  if (beta > 0.0 && isfinite(beta)) {
+    x = x / beta;
+    v[r] = x;
+  }
+  copy[r] = x;
 }
 
 // Grid (kReduceBlocks, ceil(kmax / kFgVB)): block (b, g) forms the partial dots of rows
@@ -250,13 +243,33 @@ __global__ void k_fg_maxpy(const double* __restrict__ V, int64_t ld, const FgSta
 }
 
 __global__ void k_fg_normalize(const double* __restrict__ w, const double* __restrict__ sq, double* __restrict__ V,
-                               int64_t ld, const FgState* __restrict__ st, double* __restrict__ H, int ldh, int n) {
+                               int64_t ld, const FgState* __restrict__ st, double* __restrict__ H, int ldh, int n,
+                               double* __restrict__ copy) {
   pdl_wait();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = st->j;
   const double nrm = sqrt(*sq);
   if (r == 0) H[int64_t(j) * ldh + j + 1] = nrm;
-  if (r < n) V[ld * (j + 1) + r] = nrm > 0.0 ? w[r] / nrm : w[r];
+  if (r < n) {
+    const double x = nrm > 0.0 ? w[r] / nrm : w[r];
+    V[ld * (j + 1) + r] = x;
+    copy[r] = x;   // the next iteration's V-cycle input
+  }
+}
+
+// The pressure part of z loses its mean (the same arithmetic as the projection's subtraction), and z
+// is stored as column j of Z.
+__global__ void k_fg_project_put(double* __restrict__ z, double* __restrict__ Z, int64_t ld,
+                                 const FgState* __restrict__ st, int n, int n_u, const double* __restrict__ sum) {
+  pdl_wait();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double x = z[r];
+  if (r >= n_u) {
+    x -= *sum / double(n - n_u);
+    z[r] = x;
+  }
+  Z[ld * st->j + r] = x;
 }
 
 __global__ void k_fg_givens(double* __restrict__ H, int ldh, double* __restrict__ cs, double* __restrict__ sn,
@@ -455,19 +468,16 @@ int fg_init(const double* sq, FgState* st, double* g, double* hist, int kmax, cu
   return 1;
 }
 
-int fg_scale(double* v, const FgState* st, int n, cudaStream_t s) {
-  launch(k_fg_scale, dim3((n + kT - 1) / kT), dim3(kT), 0, s, v, st, n);
+int fg_scale(double* v, const FgState* st, int n, double* copy, cudaStream_t s) {
+  launch(k_fg_scale, dim3((n + kT - 1) / kT), dim3(kT), 0, s, v, st, n, copy);
   return 1;
 }
 
-int fg_col_get(const double* V, int64_t ld, const FgState* st, double* out, int n, cudaStream_t s) {
-  launch(k_fg_col_get, dim3((n + kT - 1) / kT), dim3(kT), 0, s, V, ld, st, out, n);
-  return 1;
-}
-
-int fg_col_put(const double* in, double* Z, int64_t ld, const FgState* st, int n, cudaStream_t s) {
-  launch(k_fg_col_put, dim3((n + kT - 1) / kT), dim3(kT), 0, s, in, Z, ld, st, n);
-  return 1;
+int fg_project_put(double* z, double* Z, int64_t ld, const FgState* st, int n, int n_u, double* partial,
+                   double* sum, cudaStream_t s) {
+  int k = pressure_sum(z, n_u, n - n_u, partial, sum, s);
+  launch(k_fg_project_put, dim3((n + kT - 1) / kT), dim3(kT), 0, s, z, Z, ld, st, n, n_u, sum);
+  return k + 1;
 }
 
 int fg_cgs_pass(const double* V, int64_t ld, const FgState* st, double* w, int n, double* partial, double* H,
@@ -479,8 +489,8 @@ int fg_cgs_pass(const double* V, int64_t ld, const FgState* st, double* w, int n
 }
 
 int fg_normalize(const double* w, const double* sq, double* V, int64_t ld, const FgState* st, double* H, int ldh,
-                 int n, cudaStream_t s) {
-  launch(k_fg_normalize, dim3((n + kT - 1) / kT), dim3(kT), 0, s, w, sq, V, ld, st, H, ldh, n);
+                 int n, double* copy, cudaStream_t s) {
+  launch(k_fg_normalize, dim3((n + kT - 1) / kT), dim3(kT), 0, s, w, sq, V, ld, st, H, ldh, n, copy);
   return 1;
 }
 

@@ -254,6 +254,13 @@ int finalize_sum(const double* partial, int nparts, double* out, cudaStream_t s)
   return 1;
 }
 
+int pressure_sum(const double* x, int off, int len, double* scratch_partial, double* scratch_sum, cudaStream_t s) {
+  if (len <= 0) return 0;
+  launch(k_sum_partials, dim3(kReduceBlocks), dim3(kThreads), 0, s, x + off, len, scratch_partial);
+  launch(k_finalize, dim3(1), dim3(kThreads), 0, s, scratch_partial, kReduceBlocks, scratch_sum);
+  return 2;
+}
+
 int pressure_project(double* x, int off, int len, double* scratch_partial, double* scratch_sum,
                       cudaStream_t s) {
   if (len <= 0) return 0;

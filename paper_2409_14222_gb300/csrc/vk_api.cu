@@ -1186,7 +1186,7 @@ void build_graph_locked(vk_hierarchy* h) {
   CK(cudaStreamGetCaptureInfo(c0, &cst, nullptr, &g, &deps, nullptr, &ndeps));
   CK(cudaGraphConditionalHandleCreate(&h->cond, g, 0, 0));
   h->n_launch += vk::gpu::fg_init(h->scal, h->st, h->g, h->hist, h->kmax, h->cond, c0);
-  h->n_launch += vk::gpu::fg_scale(h->V, h->st, n, c0);
+  h->n_launch += vk::gpu::fg_scale(h->V, h->st, n, h->vin, c0);
   h->g_pro = h->n_launch - launches0;
   CK(cudaStreamGetCaptureInfo(c0, &cst, nullptr, &g, &deps, nullptr, &ndeps));
   cudaGraphNodeParams cp{};
@@ -1201,16 +1201,15 @@ void build_graph_locked(vk_hierarchy* h) {
   // loop body, captured straight into the conditional node's body graph
   const int64_t launches1 = h->n_launch;
   CK(cudaStreamBeginCaptureToGraph(c1, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  h->n_launch += vk::gpu::fg_col_get(h->V, ld, h->st, h->vin, n, c1);
+  // vin holds V[j]: written by the prologue's scaling for j = 0, by the previous normalisation after
   vcycle(h, L - 1, h->vin, h->zbuf, c1, false);
-  h->n_launch += vk::gpu::pressure_project(h->zbuf, F.n_u, F.n_p, h->partial, h->scal + 1, c1);
-  h->n_launch += vk::gpu::fg_col_put(h->zbuf, h->Z, ld, h->st, n, c1);
+  h->n_launch += vk::gpu::fg_project_put(h->zbuf, h->Z, ld, h->st, n, F.n_u, h->partial, h->scal + 1, c1);
   h->n_launch += vk::gpu::sell_residual(F.A, nullptr, h->zbuf, h->wbuf, c1);
   h->n_launch += vk::gpu::fg_cgs_pass(h->V, ld, h->st, h->wbuf, n, h->partial, h->H, ldh, h->t2, h->kmax, 0, c1);
   h->n_launch += vk::gpu::fg_cgs_pass(h->V, ld, h->st, h->wbuf, n, h->partial, h->H, ldh, h->t2, h->kmax, 1, c1);
   h->n_launch += vk::gpu::dot_partials(h->wbuf, h->wbuf, n, h->partial, c1);
   h->n_launch += vk::gpu::finalize_sum(h->partial, vk::gpu::kReduceBlocks, h->scal + 2, c1);
-  h->n_launch += vk::gpu::fg_normalize(h->wbuf, h->scal + 2, h->V, ld, h->st, h->H, ldh, n, c1);
+  h->n_launch += vk::gpu::fg_normalize(h->wbuf, h->scal + 2, h->V, ld, h->st, h->H, ldh, n, h->vin, c1);
   h->n_launch += vk::gpu::fg_givens(h->H, ldh, h->cs, h->sn, h->g, h->hist, h->st, h->cond, c1);
   cudaGraph_t body_out = nullptr;
   CK(cudaStreamEndCapture(c1, &body_out));
