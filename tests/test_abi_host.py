@@ -333,3 +333,16 @@ def test_bdm_dof_coords_follow_the_oracle_layout(vk):
         assert np.allclose(xy[s.n_edge + c * (k + 1) * (k - 1)], x0 + J @ [1 / 3, 1 / 3], atol=1e-15)
         for m, (a, b) in enumerate(exact.lattice_nodes(k - 1)):
             assert np.allclose(xy[pd[m]], x0 + J @ [a / (k - 1), b / (k - 1)], atol=1e-15)
+
+
+def test_bdm_index_bound_and_options_are_checked(vk):
+    # (BDM_k, dP_{k-1}) rows couple up to six cells: problems whose matrix would overflow 32-bit
+    # indices are refused before any host assembly, and the programmatic-launch option takes 0 or 1
+    ok = vk.vk.make_problem(8, 3, 5, cell=vk.vk.VK_CELL_BDM)
+    assert _check(vk, ok) == vk.vk.VK_OK
+    too_big = vk.vk.make_problem(256, 3, 5, cell=vk.vk.VK_CELL_BDM)    # 1024 x 1024, k = 5
+    assert _check(vk, too_big) == vk.vk.VK_ERR_ARG
+    assert _check(vk, vk.vk.make_problem(256, 3, 5)) == vk.vk.VK_ERR_ARG   # Taylor-Hood k = 5: no
+    assert vk.default_options().graph_pdl == 0
+    assert _check(vk, ok, vk.default_options(graph_pdl=1)) == vk.vk.VK_OK
+    assert _check(vk, ok, vk.default_options(graph_pdl=2)) == vk.vk.VK_ERR_ARG
