@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <exception>
 #include <map>
 #include <stdexcept>
 #include <thread>
@@ -559,9 +560,18 @@ void edge_block(const RefBDM& R, int k, const double A[2], const double B[2], co
 template <class F>
 void chunks(int n, int nthreads, F&& f) {
   std::vector<std::thread> th;
+  std::vector<std::exception_ptr> err(nthreads);   // a worker's exception goes to the caller
   for (int t = 0; t < nthreads; ++t)
-    th.emplace_back([&, t] { f(t, int(int64_t(n) * t / nthreads), int(int64_t(n) * (t + 1) / nthreads)); });
+    th.emplace_back([&, t] {
+      try {
+        f(t, int(int64_t(n) * t / nthreads), int(int64_t(n) * (t + 1) / nthreads));
+      } catch (...) {
+        err[t] = std::current_exception();
+      }
+    });
   for (auto& x : th) x.join();
+  for (auto& e : err)
+    if (e) std::rethrow_exception(e);
 }
 
 }  // namespace

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <exception>
 #include <stdexcept>
 #include <thread>
 
@@ -85,12 +86,23 @@ void parallel_for(int n, int nthreads, F&& f) {
     f(0, n);
     return;
   }
+  // an exception in a worker (out of host memory, say) is carried to the caller instead of ending
+  // the process
   std::vector<std::thread> th;
+  std::vector<std::exception_ptr> err(nthreads);
   for (int t = 0; t < nthreads; ++t) {
     int lo = int(int64_t(n) * t / nthreads), hi = int(int64_t(n) * (t + 1) / nthreads);
-    th.emplace_back([&f, lo, hi] { f(lo, hi); });
+    th.emplace_back([&f, &err, t, lo, hi] {
+      try {
+        f(lo, hi);
+      } catch (...) {
+        err[t] = std::current_exception();
+      }
+    });
   }
   for (auto& x : th) x.join();
+  for (auto& e : err)
+    if (e) std::rethrow_exception(e);
 }
 
 struct Cells {
